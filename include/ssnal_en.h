@@ -1,0 +1,188 @@
+/*
+ * ssnal_en.h -- C ABI of the GB300 (sm_103a) SsNAL-EN hot path.
+ *
+ * SsNAL-EN (Boschi, Reimherr, Chiaromonte, arXiv 2006.03970) solves the
+ * Elastic Net
+ *
+ *     min_x  1/2 ||A x - b||^2 + lambda1 ||x||_1 + lambda2/2 ||x||^2      (Sec. 1)
+ *
+ * with an augmented Lagrangian method on the dual (Algorithm 1, upper half)
+ * whose inner problem is solved by a semi-smooth Newton method
+ * (Algorithm 1, lower half; Prop. 2; eqs. grad_phy, Q_def, AJ_system,
+ * smw_formula, line_search) and stopped by the KKT residuals of eq. kkt_res.
+ *
+ * Conventions common to every entry point
+ *  - A is m x n, column-major: column j starts at element j*lda.  lda >= m and
+ *    lda * element size must be a multiple of 16 bytes.  Elements in rows
+ *    m..lda-1 are never used (they may hold anything, NaN included).
+ *  - Pointers documented "device" are CUDA device pointers owned by the caller;
+ *    the library never frees them.  A must stay alive and unchanged until
+ *    ssnal_en_destroy.  Pointers documented "host" are ordinary host memory.
+ *  - All device work is enqueued on the stream given to ssnal_en_create.  The
+ *    solve / path / op entry points return after that work has completed
+ *    (they synchronise the stream), so their outputs are ready on return.
+ *  - No C++ exception crosses this boundary; every call returns a status.
+ *  - A context is not thread-safe: use one context per host thread / stream.
+ *  - Floating-point work of the solve path is FP64 except where the options
+ *    select the mixed path (see ssnal_en_options.precision).
+ */
+#ifndef SSNAL_EN_H
+#define SSNAL_EN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssnal_en_ctx ssnal_en_ctx; /* opaque: owns the device workspaces */
+
+/* Storage type of A. */
+typedef enum {
+  SSNAL_EN_F64 = 0,      /* double */
+  SSNAL_EN_F32 = 1,      /* float */
+  SSNAL_EN_BF16 = 2,     /* bfloat16 bit patterns (uint16) */
+  SSNAL_EN_I8_GENO = 3   /* int8 codes; entry = (code - col_mean[j]) * col_scale[j] */
+} ssnal_en_dtype;
+
+typedef enum {
+  SSNAL_EN_OK = 0,
+  SSNAL_EN_EINVAL = 1,    /* bad argument: sizes, lda, null pointer, negative or non-finite lambda */
+  SSNAL_EN_ENOMEM = 2,    /* a device workspace could not be allocated */
+  SSNAL_EN_ENOCONV = 3,   /* iteration caps reached; the best iterate is still returned */
+  SSNAL_EN_ECUDA = 4,     /* a CUDA runtime call failed */
+  SSNAL_EN_ETIMEOUT = 5,  /* reserved for bounded device-side waits */
+  SSNAL_EN_ENOTSUP = 6    /* valid but unsupported request (e.g. m above the supported maximum) */
+} ssnal_en_status;
+
+/* The design matrix handed to ssnal_en_create (borrowed, never copied). */
+typedef struct {
+  int64_t m, n, lda;       /* rows (observations), columns (features), leading dimension in elements */
+  int32_t dtype;           /* ssnal_en_dtype */
+  int32_t reserved;
+  const void* data;        /* device, column-major, see the conventions above */
+  const float* col_mean;   /* I8_GENO only: device, length n */
+  const float* col_scale;  /* I8_GENO only: device, length n */
+} ssnal_en_matrix;
+
+/* Solver options.  ssnal_en_default_options fills the paper's settings. */
+typedef struct {
+  double sigma0;        /* 5e-3: initial AL penalty (Sec. 4.1) */
+  double sigma_growth;  /* 5: sigma multiplied by this after every AL iteration (Sec. 4.1) */
+  double sigma_max;     /* 1e8: cap of the increasing sigma sequence (Algorithm 1 step (2)) */
+  double mu;            /* 0.2: Armijo constant in (0, 1/2) (eq. line_search, Sec. 4.1) */
+  double beta;          /* 0.5: backtracking factor, trial steps 1, beta, beta^2, ... */
+  double tol;           /* 1e-6: tolerance on res(kkt1) and res(kkt3) (eq. kkt_res) */
+  int32_t max_al;       /* 100: AL iterations */
+  int32_t max_newton;   /* 50: SsN iterations per AL iteration */
+  int32_t max_ls;       /* 40: line-search trials per SsN iteration, at most 64 */
+  int32_t precision;    /* 0: FP64 stream arithmetic; 1: mixed (FP32 accumulation of low-precision A) */
+  int32_t refine_steps; /* 2: iterative-refinement steps of the Newton solve */
+  int32_t use_y0;       /* 0: y0 = A x0 - b; 1: take y0 from the y argument of ssnal_en_solve */
+  int32_t ls_fused;     /* 16: trial steps evaluated inside the A^T d pass (1..16); later trials
+                           are evaluated by a pass over the stored n-vectors only */
+  int32_t reserved0;
+  int64_t max_active;   /* 0: path stops after the first point with at least this many nonzeros (0 = never) */
+} ssnal_en_options;
+
+/* Per-fit report. */
+typedef struct {
+  int32_t status;        /* ssnal_en_status of this fit */
+  int32_t al_iters;      /* AL iterations performed */
+  int32_t newton_iters;  /* Newton directions computed (all AL iterations) */
+  int32_t ls_trials;     /* line-search trials (all Newton iterations) */
+  int64_t active;        /* nonzeros of the returned x */
+  double kkt1;           /* ||y + b - A x|| / (1 + ||b||)            (eq. kkt_res) */
+  double kkt3;           /* ||A^T y + z|| / (1 + ||y|| + ||z||)      (eq. kkt_res) */
+  double primal_obj;     /* 1/2||Ax-b||^2 + lambda1||x||_1 + lambda2/2||x||^2 */
+  double dual_gap;       /* primal_obj - D(y), D(y) = -h*(y) - p*(-A^T y) (lambda2 > 0) */
+  double seconds;        /* wall time of the fit on the host clock */
+  double sigma;          /* sigma of the last AL iteration */
+  double lambda1, lambda2;
+} ssnal_en_result;
+
+/* Fills *opts with the defaults listed above. */
+void ssnal_en_default_options(ssnal_en_options* opts);
+
+/* Human-readable name of a status code (static string). */
+const char* ssnal_en_status_string(int32_t status);
+
+/* Creates a context for the matrix *A.  opts may be NULL (defaults).  stream is
+ * a cudaStream_t (NULL = the legacy default stream).  Allocates the device
+ * workspaces (vectors of length n and m, the A_J panel, the Newton matrix).
+ * Errors: EINVAL (null pointers, m <= 0, n <= 0, lda < m, misaligned lda or
+ * data, unknown dtype), ENOTSUP (m above 4096), ENOMEM, ECUDA. */
+ssnal_en_status ssnal_en_create(ssnal_en_ctx** ctx, const ssnal_en_matrix* A,
+                                const ssnal_en_options* opts, void* stream);
+
+/* Releases the context's workspaces (never the caller's A). NULL is a no-op. */
+void ssnal_en_destroy(ssnal_en_ctx* ctx);
+
+/* Replaces the options of an existing context (NULL restores the defaults). */
+ssnal_en_status ssnal_en_set_options(ssnal_en_ctx* ctx, const ssnal_en_options* opts);
+
+/* One SsNAL-EN fit (Algorithm 1).
+ *  b   device, length m (FP64).
+ *  x   device, length n (FP64): on entry the warm start x0 (zeros for a cold
+ *      start), on return the solution.
+ *  y   device, length m (FP64) or NULL: on entry y0 when opts.use_y0 = 1, on
+ *      return the final dual iterate.
+ *  out host, may be NULL.
+ * Returns OK, ENOCONV (caps reached; x, y and *out hold the last iterate), or an
+ * error (EINVAL for lambda1 < 0, lambda2 < 0 or non-finite lambdas). */
+ssnal_en_status ssnal_en_solve(ssnal_en_ctx* ctx, const double* b, double lambda1, double lambda2,
+                               double* x, double* y, ssnal_en_result* out);
+
+/* Warm-started regularization path (Sec. 3.3).  lambda1_k = c_k ||A^T b||_inf,
+ * lambda2_k = (1 - alpha)/alpha * c_k ||A^T b||_inf (the parameterisation of
+ * Sec. 4.1 with lambda_max = ||A^T b||_inf / alpha), alpha in (0, 1].
+ *  b      device, length m.
+ *  c_grid host, K values, visited in the given order (descending for warm starts).
+ *  X      device, n x K column-major (column k = solution at c_k), or NULL.
+ *  out    host, K results (may be NULL).  Points after an early stop
+ *         (opts.max_active) get status EINVAL-free zeros and al_iters = 0.
+ *  n_done host, may be NULL: number of grid points solved.
+ * Each point starts from the previous solution (x0 = x_{k-1}, y0 = A x0 - b) and
+ * restarts sigma at sigma0. */
+ssnal_en_status ssnal_en_path(ssnal_en_ctx* ctx, const double* b, double alpha, const double* c_grid,
+                              int32_t K, double* X, ssnal_en_result* out, int32_t* n_done);
+
+/* Same as ssnal_en_path with b, X in HOST memory (X may be NULL): the library
+ * copies b to the device and the solutions back inside the call. */
+ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* ctx, const double* b_host, double alpha,
+                                   const double* c_grid, int32_t K, double* X_host,
+                                   ssnal_en_result* out, int32_t* n_done);
+
+/* ---------------------------------------------------------------------------
+ * Single steps of the hot path, exposed for tests and for callers that build
+ * their own loops.  Each runs the same kernels the solver uses.
+ * ------------------------------------------------------------------------- */
+
+/* u = A^T y (the dual-to-primal stream, needed by Prop. 2 and eq. Q_def).
+ * y device length m (FP64), u device length n (FP64). */
+ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* ctx, const double* y, double* u);
+
+/* Prox and active set (eqs. prox_elastic, Q_def): v = x - sigma*u,
+ * J = { j : |v_j| > sigma*lambda1 } in ascending order, w_J = prox_{sigma p}(v)_J.
+ * x, u device length n; J device int32 (capacity n); wJ device (capacity n);
+ * r host: |J|. */
+ssnal_en_status ssnal_en_op_prox_active(ssnal_en_ctx* ctx, const double* x, const double* u,
+                                        double sigma, double lambda1, double lambda2,
+                                        int32_t* J, double* wJ, int64_t* r);
+
+/* Gradient of psi (eq. grad_phy) restricted to J: g = y + b - A_J w_J, with the
+ * gather of A_J into the context's packed panel.  J device int32 (r entries),
+ * wJ device (r), y, b, g device length m. */
+ssnal_en_status ssnal_en_op_grad(ssnal_en_ctx* ctx, const int32_t* J, const double* wJ, int64_t r,
+                                 const double* y, const double* b, double* g);
+
+/* Newton direction (eqs. AJ_system, smw_formula): solves
+ * (I_m + kappa A_J A_J^T) d = -g on the panel gathered by the preceding
+ * ssnal_en_op_grad call (same J, r).  g, d device length m. */
+ssnal_en_status ssnal_en_op_newton(ssnal_en_ctx* ctx, int64_t r, double kappa, const double* g, double* d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSNAL_EN_H */

@@ -1,0 +1,303 @@
+"""GB300-native SsNAL-EN: Python binding of libssnal_en (include/ssnal_en.h).
+
+This module only marshals arguments for the C ABI: every step of the solver
+runs in the library's CUDA kernels.  PyTorch provides device memory and the
+current CUDA stream.  The functions carry the names of the C entry points
+(``ssnal_en_create``, ``ssnal_en_solve``, ``ssnal_en_path`` ...); ``Context``
+wraps them for convenience.
+
+There is no CPU fallback: if the shared library is missing or CUDA is not
+available the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "F64", "F32", "BF16", "I8_GENO", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
+    "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
+    "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
+    "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_prox_active", "ssnal_en_op_grad",
+    "ssnal_en_op_newton", "Context",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libssnal_en.so")
+
+F64, F32, BF16, I8_GENO = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ENOCONV, ECUDA, ETIMEOUT, ENOTSUP = range(7)
+_ELEM = {F64: 8, F32: 4, BF16: 2, I8_GENO: 1}
+
+
+class SsnalError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_lib_status(status)} (status {status})")
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("data", ctypes.c_void_p), ("col_mean", ctypes.c_void_p),
+                ("col_scale", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("sigma0", ctypes.c_double), ("sigma_growth", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("mu", ctypes.c_double), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_al", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("max_ls", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32), ("use_y0", ctypes.c_int32),
+                ("ls_fused", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("max_active", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("al_iters", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("ls_trials", ctypes.c_int32), ("active", ctypes.c_int64), ("kkt1", ctypes.c_double),
+                ("kkt3", ctypes.c_double), ("primal_obj", ctypes.c_double), ("dual_gap", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("sigma", ctypes.c_double), ("lambda1", ctypes.c_double),
+                ("lambda2", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
+           "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
+           "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton"]
+
+
+def load_library(path: str | None = None):
+    """Loads libssnal_en.so (built by paper_2006_03970_gb300.build) and declares the signatures."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(p)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.ssnal_en_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.ssnal_en_default_options.restype = None
+    L.ssnal_en_status_string.argtypes = [i32]
+    L.ssnal_en_status_string.restype = ctypes.c_char_p
+    L.ssnal_en_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Matrix), ctypes.POINTER(Options), vp]
+    L.ssnal_en_destroy.argtypes = [vp]
+    L.ssnal_en_destroy.restype = None
+    L.ssnal_en_set_options.argtypes = [vp, ctypes.POINTER(Options)]
+    L.ssnal_en_solve.argtypes = [vp, vp, dbl, dbl, vp, vp, ctypes.POINTER(Result)]
+    L.ssnal_en_path.argtypes = [vp, vp, dbl, ctypes.POINTER(dbl), i32, vp, ctypes.POINTER(Result),
+                                ctypes.POINTER(i32)]
+    L.ssnal_en_path_host.argtypes = [vp, ctypes.POINTER(dbl), dbl, ctypes.POINTER(dbl), i32, vp,
+                                     ctypes.POINTER(Result), ctypes.POINTER(i32)]
+    L.ssnal_en_op_at_y.argtypes = [vp, vp, vp]
+    L.ssnal_en_op_prox_active.argtypes = [vp, vp, vp, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64)]
+    L.ssnal_en_op_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    L.ssnal_en_op_newton.argtypes = [vp, i64, dbl, vp, vp]
+    for name in EXPORTS:
+        if getattr(L, name).restype is ctypes.c_int:
+            getattr(L, name).restype = i32
+    if path is None:
+        _LIB = L
+    return L
+
+
+def _lib_status(status):
+    try:
+        return load_library().ssnal_en_status_string(int(status)).decode()
+    except OSError:
+        return "unknown"
+
+
+def _check(status, where, allow=(OK,)):
+    if status not in allow:
+        raise SsnalError(status, where)
+    return status
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor, None for None."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def ssnal_en_default_options(**overrides) -> Options:
+    o = Options()
+    load_library().ssnal_en_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+default_options = ssnal_en_default_options
+
+
+def device_matrix(At: np.ndarray, dtype: int = F64, device="cuda"):
+    """Copies a feature-major (n, m) array (== column-major A) to the device with a
+    16-byte-aligned leading dimension; returns (tensor of shape (n, lda), m)."""
+    import torch
+    n, m = At.shape
+    es = _ELEM[dtype]
+    q = 16 // es
+    lda = (m + q - 1) // q * q
+    if dtype == F64:
+        host = np.zeros((n, lda), dtype=np.float64)
+        host[:, :m] = At
+        t = torch.from_numpy(host).to(device)
+    elif dtype == F32:
+        host = np.zeros((n, lda), dtype=np.float32)
+        host[:, :m] = At
+        t = torch.from_numpy(host).to(device)
+    elif dtype == BF16:
+        host = np.zeros((n, lda), dtype=np.uint16)
+        host[:, :m] = At  # bf16 bit patterns
+        t = torch.from_numpy(host.view(np.int16)).to(device)
+    else:
+        host = np.zeros((n, lda), dtype=np.int8)
+        host[:, :m] = At
+        t = torch.from_numpy(host).to(device)
+    return t, m
+
+
+def ssnal_en_create(A, m: int, dtype: int = F64, options: Options | None = None, stream=None,
+                    col_mean=None, col_scale=None):
+    """A: device tensor (n, lda) holding column-major A.  Returns an opaque context handle."""
+    mat = Matrix(m=m, n=A.shape[0], lda=A.shape[1], dtype=dtype, reserved=0, data=A.data_ptr(),
+                 col_mean=col_mean.data_ptr() if col_mean is not None else None,
+                 col_scale=col_scale.data_ptr() if col_scale is not None else None)
+    ctx = ctypes.c_void_p()
+    st = load_library().ssnal_en_create(ctypes.byref(ctx), ctypes.byref(mat),
+                                        ctypes.byref(options) if options is not None else None,
+                                        _stream_handle(stream))
+    _check(st, "ssnal_en_create")
+    return ctx
+
+
+def ssnal_en_destroy(ctx):
+    load_library().ssnal_en_destroy(ctx)
+
+
+def ssnal_en_set_options(ctx, options: Options | None):
+    _check(load_library().ssnal_en_set_options(ctx, ctypes.byref(options) if options is not None else None),
+           "ssnal_en_set_options")
+
+
+def ssnal_en_solve(ctx, b, lambda1, lambda2, x, y=None):
+    """b, x (in/out), y (optional in/out): FP64 device tensors.  Returns (status, Result)."""
+    res = Result()
+    st = load_library().ssnal_en_solve(ctx, _ptr(b), float(lambda1), float(lambda2), _ptr(x), _ptr(y),
+                                       ctypes.byref(res))
+    _check(st, "ssnal_en_solve", allow=(OK, ENOCONV))
+    return st, res
+
+
+def ssnal_en_path(ctx, b, alpha, c_grid, X=None):
+    """b: device FP64 (m); c_grid: host sequence; X: device FP64 (K, n) or None.
+    Returns (status, [Result], n_done)."""
+    K = len(c_grid)
+    cg = (ctypes.c_double * K)(*[float(c) for c in c_grid])
+    out = (Result * K)()
+    done = ctypes.c_int32(0)
+    st = load_library().ssnal_en_path(ctx, _ptr(b), float(alpha), cg, K, _ptr(X), out, ctypes.byref(done))
+    _check(st, "ssnal_en_path", allow=(OK, ENOCONV))
+    return st, list(out), done.value
+
+
+def ssnal_en_path_host(ctx, b_host: np.ndarray, alpha, c_grid, X_host: np.ndarray | None = None):
+    """b_host: host float64 (m); X_host: host float64 (K, n) or None (written in place)."""
+    K = len(c_grid)
+    cg = (ctypes.c_double * K)(*[float(c) for c in c_grid])
+    out = (Result * K)()
+    done = ctypes.c_int32(0)
+    b_host = np.ascontiguousarray(b_host, dtype=np.float64)
+    bp = b_host.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    xp = None
+    if X_host is not None:
+        assert X_host.dtype == np.float64 and X_host.flags.c_contiguous
+        xp = ctypes.c_void_p(X_host.ctypes.data)
+    st = load_library().ssnal_en_path_host(ctx, bp, float(alpha), cg, K, xp, out, ctypes.byref(done))
+    _check(st, "ssnal_en_path_host", allow=(OK, ENOCONV))
+    return st, list(out), done.value
+
+
+def ssnal_en_op_at_y(ctx, y, u):
+    _check(load_library().ssnal_en_op_at_y(ctx, _ptr(y), _ptr(u)), "ssnal_en_op_at_y")
+
+
+def ssnal_en_op_prox_active(ctx, x, u, sigma, lambda1, lambda2, J, wJ) -> int:
+    r = ctypes.c_int64(0)
+    _check(load_library().ssnal_en_op_prox_active(ctx, _ptr(x), _ptr(u), float(sigma), float(lambda1),
+                                                  float(lambda2), _ptr(J), _ptr(wJ), ctypes.byref(r)),
+           "ssnal_en_op_prox_active")
+    return r.value
+
+
+def ssnal_en_op_grad(ctx, J, wJ, r, y, b, g):
+    _check(load_library().ssnal_en_op_grad(ctx, _ptr(J), _ptr(wJ), int(r), _ptr(y), _ptr(b), _ptr(g)),
+           "ssnal_en_op_grad")
+
+
+def ssnal_en_op_newton(ctx, r, kappa, g, d):
+    return _check(load_library().ssnal_en_op_newton(ctx, int(r), float(kappa), _ptr(g), _ptr(d)),
+                  "ssnal_en_op_newton", allow=(OK, ENOCONV))
+
+
+class Context:
+    """Owns one library context for a resident design matrix.
+
+    ``At`` is the feature-major (n, m) host array (== column-major A), or an
+    already padded device tensor together with ``m``.
+    """
+
+    def __init__(self, At, m: int | None = None, dtype: int = F64, options: Options | None = None, stream=None,
+                 col_mean=None, col_scale=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("SsNAL-EN needs a CUDA device; there is no CPU fallback")
+        if isinstance(At, np.ndarray):
+            self.A, self.m = device_matrix(At, dtype)
+        else:
+            self.A, self.m = At, int(m)
+        self.n = self.A.shape[0]
+        self.dtype = dtype
+        self._keep = (col_mean, col_scale)
+        self.ctx = ssnal_en_create(self.A, self.m, dtype, options, stream, col_mean, col_scale)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ssnal_en_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, options):
+        ssnal_en_set_options(self.ctx, options)
+
+    def solve(self, b, lambda1, lambda2, x0=None, y=None):
+        import torch
+        b = torch.as_tensor(b, dtype=torch.float64, device="cuda")
+        x = torch.zeros(self.n, dtype=torch.float64, device="cuda") if x0 is None else \
+            torch.as_tensor(x0, dtype=torch.float64, device="cuda").clone()
+        y = torch.zeros(self.m, dtype=torch.float64, device="cuda") if y is None else y
+        st, res = ssnal_en_solve(self.ctx, b, lambda1, lambda2, x, y)
+        return x, y, res
+
+    def path(self, b, alpha, c_grid, keep_X=True):
+        import torch
+        b = torch.as_tensor(b, dtype=torch.float64, device="cuda")
+        X = torch.zeros((len(c_grid), self.n), dtype=torch.float64, device="cuda") if keep_X else None
+        st, res, done = ssnal_en_path(self.ctx, b, alpha, c_grid, X)
+        return X, res, done

@@ -1,0 +1,626 @@
+// Host side of libssnal_en: the C ABI of include/ssnal_en.h, the context and
+// its device workspaces, and the AL / SsN control flow of Algorithm 1.  All
+// arithmetic on vectors and matrices runs in the kernels of kern_*.cu; the
+// host only sequences launches and reads a small status block once per
+// Newton step (r, norms, flags) to take the control-flow decisions.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "../../include/ssnal_en.h"
+#include "internal.h"
+
+using namespace ssnal;
+
+struct ssnal_en_ctx {
+  int64_t m = 0, n = 0, lda = 0;
+  int dtype = 0;
+  const void* A = nullptr;
+  const float* col_mean = nullptr;
+  const float* col_scale = nullptr;
+  ssnal_en_options opt;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int grid_stream = 0, grid_vec = 0;
+  // device workspaces
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;  // pinned mirror
+  double *u = nullptr, *t = nullptr, *xpath = nullptr;
+  double *y = nullptr, *d = nullptr, *g = nullptr, *bdev = nullptr, *res = nullptr, *tmpm = nullptr;
+  double* bstage = nullptr;  // b of ssnal_en_path_host
+  double *h = nullptr, *q = nullptr, *resr = nullptr;  // r-space vectors (capacity rcap)
+  int32_t* J = nullptr;
+  double* wJ = nullptr;
+  long long* counts = nullptr;
+  double* partials = nullptr;
+  double* vpartials = nullptr;
+  double* gemv_part = nullptr;
+  double* comb_scratch = nullptr;
+  double* P = nullptr;
+  float* P32 = nullptr;
+  int64_t ldp = 0, ldp32 = 0, rcap = 0;
+  float* G = nullptr;
+  int64_t ldg = 0;
+  double* Xdev = nullptr;  // path_host output staging
+  int64_t Xcap = 0;
+};
+
+namespace {
+
+int64_t round_up(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
+
+size_t elem_size(int dtype) {
+  switch (dtype) {
+    case SSNAL_EN_F64: return 8;
+    case SSNAL_EN_F32: return 4;
+    case SSNAL_EN_BF16: return 2;
+    case SSNAL_EN_I8_GENO: return 1;
+    default: return 0;
+  }
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return SSNAL_EN_ECUDA; \
+  } while (0)
+
+template <class T>
+ssnal_en_status dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return SSNAL_EN_ENOMEM;
+  }
+  return SSNAL_EN_OK;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Panel capacity: r columns of m rows (FP64 and FP32 copies) plus r-space vectors.
+ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
+  if (need <= c->rcap) return SSNAL_EN_OK;
+  int64_t cap = c->rcap > 0 ? c->rcap : 256;
+  while (cap < need) cap *= 2;
+  if (cap > c->n) cap = c->n;
+  if (cap < need) cap = need;
+  cudaStreamSynchronize(c->stream);
+  dev_free(c->P);
+  dev_free(c->P32);
+  dev_free(c->h);
+  dev_free(c->q);
+  dev_free(c->resr);
+  c->P = nullptr;
+  c->P32 = nullptr;
+  c->h = c->q = c->resr = nullptr;
+  c->rcap = 0;
+  ssnal_en_status s;
+  if ((s = dev_alloc(&c->P, (size_t)(c->ldp * cap))) != SSNAL_EN_OK) return s;
+  if ((s = dev_alloc(&c->P32, (size_t)(c->ldp32 * cap))) != SSNAL_EN_OK) return s;
+  if ((s = dev_alloc(&c->h, (size_t)cap)) != SSNAL_EN_OK) return s;
+  if ((s = dev_alloc(&c->q, (size_t)cap)) != SSNAL_EN_OK) return s;
+  if ((s = dev_alloc(&c->resr, (size_t)cap)) != SSNAL_EN_OK) return s;
+  c->rcap = cap;
+  return SSNAL_EN_OK;
+}
+
+void free_all(ssnal_en_ctx* c) {
+  dev_free(c->st);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  dev_free(c->u);
+  dev_free(c->t);
+  dev_free(c->xpath);
+  dev_free(c->y);
+  dev_free(c->d);
+  dev_free(c->g);
+  dev_free(c->bdev);
+  dev_free(c->res);
+  dev_free(c->tmpm);
+  dev_free(c->bstage);
+  dev_free(c->h);
+  dev_free(c->q);
+  dev_free(c->resr);
+  dev_free(c->J);
+  dev_free(c->wJ);
+  dev_free(c->counts);
+  dev_free(c->partials);
+  dev_free(c->vpartials);
+  dev_free(c->gemv_part);
+  dev_free(c->comb_scratch);
+  dev_free(c->P);
+  dev_free(c->P32);
+  dev_free(c->G);
+  dev_free(c->Xdev);
+}
+
+bool is_finite_d(double v) { return std::isfinite(v); }
+
+ProxParams make_pp(double sigma, double lam1, double lam2) {
+  ProxParams pp;
+  pp.sigma = sigma;
+  pp.lam1 = lam1;
+  pp.lam2 = lam2;
+  pp.thr = sigma * lam1;
+  pp.onep = 1.0 + sigma * lam2;
+  return pp;
+}
+
+ssnal_en_status read_state(ssnal_en_ctx* c) {
+  CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SSNAL_EN_OK;
+}
+
+// ---- pieces of the SsN step ------------------------------------------------
+
+// J, w_J at the current (x, u) (or the support of x in support mode), gather
+// of A_J, and g = y + b - A_J w_J (or y = A_J x_J - b in support mode).
+ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, const double* b, ProxParams pp,
+                                 int apply_update) {
+  cudaStream_t s = c->stream;
+  launch_prox_count(mode, x, c->u, c->t, c->y, c->d, c->n, (int)c->m, pp, apply_update, c->st, c->counts,
+                    c->vpartials, c->grid_vec, s);
+  launch_prox_scatter(mode, x, c->u, c->n, pp, c->counts + c->grid_vec, c->J, c->wJ, c->grid_vec, s);
+  launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, -1, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms,
+                s);
+  launch_gemv_n_partial(c->P, c->ldp, (int)c->m, c->wJ, c->st, -1, c->rcap, c->gemv_part, s);
+  if (mode == kProxSupport)
+    launch_combine(c->y, nullptr, 0.0, b, -1.0, c->gemv_part, 1.0, (int)c->m, 0, nullptr, nullptr, nullptr, c->st,
+                   c->comb_scratch, s);
+  else
+    launch_combine(c->g, c->y, 1.0, b, 1.0, c->gemv_part, -1.0, (int)c->m, 1, c->y, b, nullptr, c->st,
+                   c->comb_scratch, s);
+  CK(cudaGetLastError());
+  ssnal_en_status st = read_state(c);
+  if (st != SSNAL_EN_OK) return st;
+  if (c->st_host->overflow) {
+    // the panel was too small for r: grow it and redo the gather and the GEMV
+    int64_t r = c->st_host->r;
+    if ((st = grow_panel(c, r)) != SSNAL_EN_OK) return st;
+    CK(cudaMemsetAsync(&c->st->overflow, 0, sizeof(int32_t), s));
+    launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32,
+                  c->sms, s);
+    launch_gemv_n_partial(c->P, c->ldp, (int)c->m, c->wJ, c->st, r, c->rcap, c->gemv_part, s);
+    if (mode == kProxSupport)
+      launch_combine(c->y, nullptr, 0.0, b, -1.0, c->gemv_part, 1.0, (int)c->m, 0, nullptr, nullptr, nullptr, c->st,
+                     c->comb_scratch, s);
+    else
+      launch_combine(c->g, c->y, 1.0, b, 1.0, c->gemv_part, -1.0, (int)c->m, 1, c->y, b, nullptr, c->st,
+                     c->comb_scratch, s);
+    CK(cudaGetLastError());
+    if ((st = read_state(c)) != SSNAL_EN_OK) return st;
+  }
+  return SSNAL_EN_OK;
+}
+
+// Newton direction d for (I + kappa A_J A_J^T) d = -g on the gathered panel.
+// FP32 factorisation of the Newton matrix, FP64 residuals through the panel
+// (iterative refinement), and the dot products the line search needs.
+ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d,
+                                 const double* yv, const double* bv, int dots) {
+  cudaStream_t s = c->stream;
+  const int m = (int)c->m;
+  const int steps = 1 + (c->opt.refine_steps > 0 ? c->opt.refine_steps : 0);
+  if (r == 0) {
+    launch_combine(d, nullptr, 0.0, g, -1.0, nullptr, 0.0, m, dots ? 2 : 0, yv, bv, g, c->st, c->comb_scratch, s);
+  } else if (r < m) {
+    // SMW (eq. smw_formula): G = kappa^{-1} I + A_J^T A_J, h = A_J^T g, q = G^{-1} h, d = A_J q - g
+    launch_syrk_tn(c->P32, c->ldp32, m, r, 1.0 / kappa, c->G, c->ldg, s);
+    chol_factor(c->G, c->ldg, (int)r, c->st, s);
+    launch_gemv_t(c->P, c->ldp, m, r, g, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
+    launch_trsv_llt(c->G, c->ldg, (int)r, c->h, c->q, 1, s);
+    for (int it = 1; it < steps; it++) {
+      // resr = h - kappa^{-1} q - A_J^T (A_J q)
+      launch_gemv_n_partial(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->gemv_part, s);
+      launch_combine(c->tmpm, nullptr, 0.0, nullptr, 0.0, c->gemv_part, 1.0, m, 0, nullptr, nullptr, nullptr, c->st,
+                     c->comb_scratch, s);
+      launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
+      launch_trsv_llt(c->G, c->ldg, (int)r, c->resr, c->q, 0, s);
+    }
+    launch_gemv_n_partial(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->gemv_part, s);
+    launch_combine(d, nullptr, 0.0, g, -1.0, c->gemv_part, 1.0, m, dots ? 2 : 0, yv, bv, g, c->st, c->comb_scratch,
+                   s);
+  } else {
+    // m x m form (eq. AJ_system): M = I + kappa A_J A_J^T, d = -M^{-1} g
+    launch_syrk_nt(c->P32, c->ldp32, m, r, kappa, c->G, c->ldg, s);
+    chol_factor(c->G, c->ldg, m, c->st, s);
+    // res = -g
+    launch_combine(c->res, nullptr, 0.0, g, -1.0, nullptr, 0.0, m, 0, nullptr, nullptr, nullptr, c->st,
+                   c->comb_scratch, s);
+    launch_trsv_llt(c->G, c->ldg, m, c->res, d, 1, s);
+    for (int it = 1; it < steps; it++) {
+      // res = -g - d - kappa A_J (A_J^T d)
+      launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
+      launch_gemv_n_partial(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->gemv_part, s);
+      launch_combine(c->tmpm, g, -1.0, d, -1.0, c->gemv_part, -kappa, m, 0, nullptr, nullptr, nullptr, c->st,
+                     c->comb_scratch, s);
+      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, s);
+    }
+    if (dots)
+      launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);
+  }
+  CK(cudaGetLastError());
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double lam2, double* x, double* y_io,
+                           ssnal_en_result* out) {
+  auto t0 = std::chrono::steady_clock::now();
+  const ssnal_en_options& o = c->opt;
+  cudaStream_t s = c->stream;
+  const int m = (int)c->m;
+  ssnal_en_result R;
+  memset(&R, 0, sizeof(R));
+  R.lambda1 = lam1;
+  R.lambda2 = lam2;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  // ||b|| via the combine kernel's scalar products (y := b temporarily)
+  CK(cudaMemcpyAsync(c->bdev, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  launch_combine(c->tmpm, c->bdev, 1.0, nullptr, 0.0, nullptr, 0.0, m, 1, c->bdev, c->bdev, nullptr, c->st,
+                 c->comb_scratch, s);
+  ssnal_en_status e = read_state(c);
+  if (e != SSNAL_EN_OK) return e;
+  const double nb1 = 1.0 + sqrt(c->st_host->g2);
+  // ---- initial dual iterate and u = A^T y (reading: y0 = A x0 - b)
+  ProxParams pp = make_pp(o.sigma0, lam1, lam2);
+  if (o.use_y0 && y_io) {
+    CK(cudaMemcpyAsync(c->y, y_io, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  } else {
+    if ((e = prox_gather_grad(c, kProxSupport, x, c->bdev, pp, 0)) != SSNAL_EN_OK) return e;
+  }
+  launch_stream(kModeU, c->dtype, c->A, c->lda, m, c->n, c->y, c->u, nullptr, nullptr, pp, o.mu, o.beta, o.max_ls,
+                o.ls_fused, c->st, c->partials, c->grid_stream, s);
+  CK(cudaGetLastError());
+  double sigma = o.sigma0;
+  int converged = 0, failed = 0;
+  int al = 0;
+  double kkt1 = INFINITY, kkt3 = INFINITY;
+  for (al = 1; al <= o.max_al; al++) {
+    pp = make_pp(sigma, lam1, lam2);
+    const double kappa = sigma / (1.0 + sigma * lam2);
+    int apply = 0;
+    int newton_here = 0;
+    for (;;) {
+      if ((e = prox_gather_grad(c, kProxThreshold, x, c->bdev, pp, apply)) != SSNAL_EN_OK) return e;
+      const DevState& h = *c->st_host;
+      if (apply) R.ls_trials += h.ls_k + 1;
+      apply = 0;
+      if (h.chol_fail) {
+        // the FP32 factor of the Newton matrix lost positive definiteness
+        failed = 1;
+        break;
+      }
+      const double gn = sqrt(h.g2) / nb1;
+      if (!(gn > o.tol) || newton_here >= o.max_newton) break;
+      const int64_t r = h.r;
+      if ((e = newton_direction(c, r, kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
+      launch_stream(kModeT, c->dtype, c->A, c->lda, m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
+                    o.ls_fused, c->st, c->partials, c->grid_stream, s);
+      launch_ls_fallback(x, c->u, c->t, c->n, pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st, c->partials,
+                         c->grid_stream, s);
+      CK(cudaGetLastError());
+      apply = 1;
+      newton_here++;
+      R.newton_iters++;
+    }
+    const DevState& h = *c->st_host;
+    // AL step (2) via the Moreau decomposition; residuals of eq. kkt_res.
+    kkt1 = sqrt(h.g2) / nb1;
+    const double aty_z = sqrt(h.xw2) / sigma;
+    const double znorm = sqrt(h.vw2) / sigma;
+    kkt3 = aty_z / (1.0 + sqrt(h.y2) + znorm);
+    R.active = h.r;
+    R.primal_obj = 0.5 * h.yg2 + lam1 * h.w1 + 0.5 * lam2 * h.w2;
+    const double dual = -(0.5 * h.y2 + h.by) - (lam2 > 0 ? h.dualpen / (2.0 * lam2) : 0.0);
+    R.dual_gap = lam2 > 0 ? R.primal_obj - dual : NAN;
+    R.sigma = sigma;
+    launch_set_x(x, c->u, c->n, pp, c->sms, s);
+    CK(cudaGetLastError());
+    if (failed) break;
+    if (kkt1 <= o.tol && kkt3 <= o.tol) {
+      converged = 1;
+      break;
+    }
+    sigma = fmin(sigma * o.sigma_growth, o.sigma_max);
+  }
+  if (y_io) CK(cudaMemcpyAsync(y_io, c->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  R.al_iters = al > o.max_al ? o.max_al : al;
+  R.kkt1 = kkt1;
+  R.kkt3 = kkt3;
+  R.status = converged ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
+  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (out) *out = R;
+  return converged ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
+}
+
+ssnal_en_status check_options(const ssnal_en_options* o) {
+  if (!(o->sigma0 > 0) || !(o->sigma_growth >= 1) || !(o->sigma_max >= o->sigma0)) return SSNAL_EN_EINVAL;
+  if (!(o->mu > 0 && o->mu < 0.5) || !(o->beta > 0 && o->beta < 1) || !(o->tol > 0)) return SSNAL_EN_EINVAL;
+  if (o->max_al < 1 || o->max_newton < 0 || o->max_ls < 1 || o->max_ls > kMaxLS) return SSNAL_EN_EINVAL;
+  if (o->ls_fused < 1 || o->ls_fused > kFusedLS) return SSNAL_EN_EINVAL;
+  if (o->refine_steps < 0 || o->refine_steps > 8 || o->max_active < 0) return SSNAL_EN_EINVAL;
+  return SSNAL_EN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ssnal_en_default_options(ssnal_en_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->sigma0 = 5e-3;
+  o->sigma_growth = 5.0;
+  o->sigma_max = 1e8;
+  o->mu = 0.2;
+  o->beta = 0.5;
+  o->tol = 1e-6;
+  o->max_al = 100;
+  o->max_newton = 50;
+  o->max_ls = 40;
+  o->precision = 0;
+  o->refine_steps = 2;
+  o->use_y0 = 0;
+  o->ls_fused = kFusedLS;
+  o->max_active = 0;
+}
+
+const char* ssnal_en_status_string(int32_t s) {
+  switch (s) {
+    case SSNAL_EN_OK: return "ok";
+    case SSNAL_EN_EINVAL: return "invalid argument";
+    case SSNAL_EN_ENOMEM: return "out of device memory";
+    case SSNAL_EN_ENOCONV: return "iteration limit reached before the KKT tolerance";
+    case SSNAL_EN_ECUDA: return "CUDA runtime error";
+    case SSNAL_EN_ETIMEOUT: return "device wait timed out";
+    case SSNAL_EN_ENOTSUP: return "unsupported size or type";
+    default: return "unknown status";
+  }
+}
+
+ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, const ssnal_en_options* opts,
+                                void* stream) {
+  if (!out || !A) return SSNAL_EN_EINVAL;
+  *out = nullptr;
+  const size_t es = elem_size(A->dtype);
+  if (es == 0 || !A->data || A->m <= 0 || A->n <= 0 || A->lda < A->m) return SSNAL_EN_EINVAL;
+  if ((A->lda * (int64_t)es) % 16 != 0 || ((uintptr_t)A->data) % 16 != 0) return SSNAL_EN_EINVAL;
+  if (A->n >= (int64_t)0x7fffffff) return SSNAL_EN_ENOTSUP;
+  if (A->m > kMaxM) return SSNAL_EN_ENOTSUP;
+  if (A->dtype != SSNAL_EN_F64) return SSNAL_EN_ENOTSUP;  // other storage types: not in this build yet
+  ssnal_en_options o;
+  if (opts)
+    o = *opts;
+  else
+    ssnal_en_default_options(&o);
+  if (check_options(&o) != SSNAL_EN_OK) return SSNAL_EN_EINVAL;
+  ssnal_en_ctx* c = new (std::nothrow) ssnal_en_ctx();
+  if (!c) return SSNAL_EN_ENOMEM;
+  c->m = A->m;
+  c->n = A->n;
+  c->lda = A->lda;
+  c->dtype = A->dtype;
+  c->A = A->data;
+  c->col_mean = A->col_mean;
+  c->col_scale = A->col_scale;
+  c->opt = o;
+  c->stream = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess) {
+    delete c;
+    return SSNAL_EN_ECUDA;
+  }
+  c->grid_stream = stream_grid(c->sms);
+  c->grid_vec = vec_grid(c->n, c->sms);
+  const int64_t m = c->m, n = c->n;
+  c->ldp = round_up(m, 2);
+  c->ldp32 = round_up(m, 4);
+  c->ldg = round_up(m, 4);
+  ssnal_en_status s = SSNAL_EN_OK;
+#define AL(ptr, cnt)                                         \
+  do {                                                       \
+    if (s == SSNAL_EN_OK) s = dev_alloc(&(ptr), (size_t)(cnt)); \
+  } while (0)
+  AL(c->st, 1);
+  AL(c->u, n);
+  AL(c->t, n);
+  AL(c->xpath, n);
+  AL(c->y, m);
+  AL(c->d, m);
+  AL(c->g, m);
+  AL(c->bdev, m);
+  AL(c->res, m);
+  AL(c->tmpm, m);
+  AL(c->bstage, m);
+  AL(c->J, n);
+  AL(c->wJ, n);
+  AL(c->counts, 2 * c->grid_vec + 2);
+  AL(c->partials, (size_t)c->grid_stream * kMaxLS);
+  AL(c->vpartials, (size_t)c->grid_vec * 6);
+  AL(c->gemv_part, (size_t)kGemvGroups * m);
+  AL(c->comb_scratch, 4 * ((m + 255) / 256) + 4);
+  AL(c->G, c->ldg * m);
+#undef AL
+  if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) s = SSNAL_EN_ENOMEM;
+  if (s == SSNAL_EN_OK) s = grow_panel(c, m < n ? m : n);
+  if (s == SSNAL_EN_OK && cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
+  if (s == SSNAL_EN_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
+  if (s != SSNAL_EN_OK) {
+    free_all(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return SSNAL_EN_OK;
+}
+
+void ssnal_en_destroy(ssnal_en_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+ssnal_en_status ssnal_en_set_options(ssnal_en_ctx* c, const ssnal_en_options* opts) {
+  if (!c) return SSNAL_EN_EINVAL;
+  ssnal_en_options o;
+  if (opts)
+    o = *opts;
+  else
+    ssnal_en_default_options(&o);
+  if (check_options(&o) != SSNAL_EN_OK) return SSNAL_EN_EINVAL;
+  c->opt = o;
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_solve(ssnal_en_ctx* c, const double* b, double lambda1, double lambda2, double* x, double* y,
+                               ssnal_en_result* out) {
+  if (!c || !b || !x) return SSNAL_EN_EINVAL;
+  if (!is_finite_d(lambda1) || !is_finite_d(lambda2) || lambda1 < 0 || lambda2 < 0) return SSNAL_EN_EINVAL;
+  if (c->opt.use_y0 && !y) return SSNAL_EN_EINVAL;
+  return solve_impl(c, b, lambda1, lambda2, x, y, out);
+}
+
+ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, const double* c_grid, int32_t K,
+                              double* X, ssnal_en_result* out, int32_t* n_done) {
+  if (n_done) *n_done = 0;
+  if (!c || !b || !c_grid || K < 0) return SSNAL_EN_EINVAL;
+  if (!(alpha > 0.0 && alpha <= 1.0)) return SSNAL_EN_EINVAL;
+  for (int k = 0; k < K; k++)
+    if (!is_finite_d(c_grid[k]) || c_grid[k] < 0) return SSNAL_EN_EINVAL;
+  if (out) memset(out, 0, sizeof(ssnal_en_result) * (size_t)K);
+  cudaStream_t s = c->stream;
+  const int m = (int)c->m;
+  // ||A^T b||_inf from the same stream kernel that later forms u = A^T y
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  ProxParams pp0 = make_pp(c->opt.sigma0, 0.0, 0.0);
+  launch_stream(kModeGmax, c->dtype, c->A, c->lda, m, c->n, b, c->t, nullptr, nullptr, pp0, c->opt.mu, c->opt.beta,
+                c->opt.max_ls, c->opt.ls_fused, c->st, c->partials, c->grid_stream, s);
+  CK(cudaGetLastError());
+  ssnal_en_status e = read_state(c);
+  if (e != SSNAL_EN_OK) return e;
+  const double gmax = c->st_host->gmax;
+  CK(cudaMemsetAsync(c->xpath, 0, sizeof(double) * c->n, s));
+  ssnal_en_status worst = SSNAL_EN_OK;
+  const ssnal_en_options saved = c->opt;
+  c->opt.use_y0 = 0;
+  for (int k = 0; k < K; k++) {
+    const double lam1 = c_grid[k] * gmax;
+    const double lam2 = (1.0 - alpha) / alpha * c_grid[k] * gmax;
+    ssnal_en_result r;
+    e = solve_impl(c, b, lam1, lam2, c->xpath, nullptr, &r);
+    if (e != SSNAL_EN_OK && e != SSNAL_EN_ENOCONV) {
+      c->opt = saved;
+      return e;
+    }
+    if (e == SSNAL_EN_ENOCONV) worst = SSNAL_EN_ENOCONV;
+    if (out) out[k] = r;
+    if (X) {
+      cudaError_t ce = cudaMemcpyAsync(X + (size_t)k * c->n, c->xpath, sizeof(double) * c->n,
+                                       cudaMemcpyDeviceToDevice, s);
+      if (ce != cudaSuccess) {
+        c->opt = saved;
+        return SSNAL_EN_ECUDA;
+      }
+    }
+    if (n_done) *n_done = k + 1;
+    if (saved.max_active > 0 && r.active >= saved.max_active) break;
+  }
+  c->opt = saved;
+  CK(cudaStreamSynchronize(s));
+  return worst;
+}
+
+ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* c, const double* b_host, double alpha, const double* c_grid,
+                                   int32_t K, double* X_host, ssnal_en_result* out, int32_t* n_done) {
+  if (!c || !b_host || K < 0) return SSNAL_EN_EINVAL;
+  cudaStream_t s = c->stream;
+  double* X = nullptr;
+  if (X_host && K > 0) {
+    if (c->Xcap < (int64_t)K * c->n) {
+      dev_free(c->Xdev);
+      c->Xdev = nullptr;
+      c->Xcap = 0;
+      ssnal_en_status e = dev_alloc(&c->Xdev, (size_t)K * (size_t)c->n);
+      if (e != SSNAL_EN_OK) return e;
+      c->Xcap = (int64_t)K * c->n;
+    }
+    X = c->Xdev;
+  }
+  CK(cudaMemcpyAsync(c->bstage, b_host, sizeof(double) * c->m, cudaMemcpyHostToDevice, s));
+  int32_t done = 0;
+  ssnal_en_status e = ssnal_en_path(c, c->bstage, alpha, c_grid, K, X, out, &done);
+  if (n_done) *n_done = done;
+  if (e != SSNAL_EN_OK && e != SSNAL_EN_ENOCONV) return e;
+  if (X && done > 0)
+    CK(cudaMemcpyAsync(X_host, X, sizeof(double) * (size_t)done * c->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return e;
+}
+
+ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* c, const double* y, double* u) {
+  if (!c || !y || !u) return SSNAL_EN_EINVAL;
+  ProxParams pp = make_pp(1.0, 0.0, 0.0);
+  launch_stream(kModeU, c->dtype, c->A, c->lda, (int)c->m, c->n, y, u, nullptr, nullptr, pp, 0.2, 0.5, 1, 1, c->st,
+                c->partials, c->grid_stream, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_op_prox_active(ssnal_en_ctx* c, const double* x, const double* u, double sigma,
+                                        double lambda1, double lambda2, int32_t* J, double* wJ, int64_t* r) {
+  if (!c || !x || !u || !J || !wJ || !r) return SSNAL_EN_EINVAL;
+  if (!(sigma > 0) || !is_finite_d(lambda1) || !is_finite_d(lambda2) || lambda1 < 0 || lambda2 < 0) return SSNAL_EN_EINVAL;
+  ProxParams pp = make_pp(sigma, lambda1, lambda2);
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  launch_prox_count(kProxThreshold, x, const_cast<double*>(u), nullptr, nullptr, nullptr, c->n, (int)c->m, pp, 0,
+                    c->st, c->counts, c->vpartials, c->grid_vec, s);
+  launch_prox_scatter(kProxThreshold, x, u, c->n, pp, c->counts + c->grid_vec, J, wJ, c->grid_vec, s);
+  CK(cudaGetLastError());
+  ssnal_en_status e = read_state(c);
+  if (e != SSNAL_EN_OK) return e;
+  *r = c->st_host->r;
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_op_grad(ssnal_en_ctx* c, const int32_t* J, const double* wJ, int64_t r, const double* y,
+                                 const double* b, double* g) {
+  if (!c || (r > 0 && (!J || !wJ)) || !y || !b || !g || r < 0 || r > c->n) return SSNAL_EN_EINVAL;
+  ssnal_en_status e = grow_panel(c, r);
+  if (e != SSNAL_EN_OK) return e;
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  const int m = (int)c->m;
+  launch_gather(c->A, c->dtype, c->lda, m, J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms, s);
+  launch_gemv_n_partial(c->P, c->ldp, m, wJ, c->st, r, c->rcap, c->gemv_part, s);
+  launch_combine(g, y, 1.0, b, 1.0, c->gemv_part, -1.0, m, 0, nullptr, nullptr, nullptr, c->st, c->comb_scratch, s);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_op_newton(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d) {
+  if (!c || !g || !d || r < 0 || r > c->rcap || !(kappa > 0) || !is_finite_d(kappa)) return SSNAL_EN_EINVAL;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+  ssnal_en_status e = newton_direction(c, r, kappa, g, d, nullptr, nullptr, 0);
+  if (e != SSNAL_EN_OK) return e;
+  e = read_state(c);
+  if (e != SSNAL_EN_OK) return e;
+  return c->st_host->chol_fail ? SSNAL_EN_ENOCONV : SSNAL_EN_OK;
+}
+
+}  // extern "C"

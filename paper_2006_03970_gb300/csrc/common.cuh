@@ -1,0 +1,108 @@
+// Device helpers shared by the kernels: deterministic reductions, the
+// last-block-done pattern and the Elastic Net prox (eq. prox_elastic).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace ssnal {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum over the block in a fixed order (warp tree, then warp 0 over warp sums).
+// `red` must hold at least 32 doubles.  Result valid in every thread.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double out = red[0];
+  __syncthreads();
+  return out;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (warp == 0) t = warp_max(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double out = red[0];
+  __syncthreads();
+  return out;
+}
+
+// Last-block-done: after every block has written its partial results, exactly
+// one block (the last to arrive) sees `true` and may reduce the partials in a
+// fixed order.  That block resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned int* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+__device__ __forceinline__ void reset_counter(unsigned int* counter) {
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Loads that bypass L1 so that values written by other blocks of the same
+// kernel (before the fence of last_block) are observed.
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ long long ld_cg(const long long* p) { return __ldcg(p); }
+
+// soft(t, thr) magnitude part: max(|t| - thr, 0)
+__device__ __forceinline__ double shrink_mag(double t, double thr) { return fmax(fabs(t) - thr, 0.0); }
+
+// prox_{sigma p}(v) of eq. prox_elastic: sign(v) max(|v| - sigma*lam1, 0) / (1 + sigma*lam2).
+// The active test |v| > thr (eq. Q_def) and this value must agree: the value is
+// nonzero exactly when the test holds.
+__device__ __forceinline__ double prox_value(double v, const ProxParams& pp) {
+  double mag = __dsub_rn(fabs(v), pp.thr);
+  if (!(mag > 0.0)) return 0.0;
+  double w = __ddiv_rn(mag, pp.onep);
+  return v < 0.0 ? -w : w;
+}
+
+__device__ __forceinline__ bool is_active(double v, const ProxParams& pp) { return fabs(v) > pp.thr; }
+
+// v = x - sigma*u with two roundings (no contraction into an FMA), the same
+// rounding sequence as the plain elementwise evaluation of the definition.
+__device__ __forceinline__ double v_of(double x, double u, double sigma) { return __dsub_rn(x, __dmul_rn(sigma, u)); }
+
+}  // namespace ssnal

@@ -1,0 +1,100 @@
+// Internal declarations shared by the CUDA translation units of libssnal_en.
+// Nothing here is part of the public C ABI (include/ssnal_en.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ssnal {
+
+constexpr int kMaxM = 4096;       // largest supported number of observations m
+constexpr int kMaxLS = 64;        // largest supported number of line-search trials
+constexpr int kFusedLS = 16;      // trial steps evaluated inside the A^T d stream
+constexpr int kGemvGroups = 32;   // column groups of the panel GEMV partial sums
+constexpr int kCholNB = 32;       // block size of the blocked Cholesky
+constexpr int kNumCounters = 16;  // last-block-done counters
+
+// Counter slots (one per kernel that uses the last-block pattern).
+enum CounterSlot {
+  kCtrProx = 0, kCtrCombine = 1, kCtrStream = 2, kCtrFallback = 3, kCtrGmax = 4, kCtrMisc = 5
+};
+
+// Values computed on the device and read by the host once per Newton step.
+// The host never writes these except through cudaMemsetAsync of the whole struct.
+struct DevState {
+  // prox / active-set pass (eqs. prox_elastic, Q_def) at the current y
+  long long r;        // |J|
+  double w2;          // ||w||^2, w = prox_{sigma p}(v)
+  double w1;          // ||w||_1
+  double xw2;         // ||x - w||^2       (sigma^2 ||A^T y + z||^2)
+  double vw2;         // ||v - w||^2       (sigma^2 ||z||^2)
+  double dualpen;     // sum_j (|u_j| - lambda1)_+^2   (p*(-A^T y) * 2 lambda2)
+  // gradient pass (eq. grad_phy)
+  double g2;          // ||g||^2
+  double y2;          // ||y||^2
+  double yg2;         // ||y - g||^2 = ||A x - b||^2
+  double by;          // b^T y
+  // Newton direction dots used by the line search
+  double gd, yd, dd, bd;
+  // line search (eq. line_search)
+  double s;           // accepted step
+  int32_t ls_k;       // index of the accepted trial (trials = ls_k + 1)
+  int32_t ls_state;   // 0 accepted, 1 fallback pending
+  double lsdiff[kMaxLS];  // sum_j soft(v_j - s_k sigma t_j)^2 - soft(v_j)^2 per trial k
+  // flags
+  int32_t overflow;   // panel capacity exceeded by r
+  int32_t chol_fail;  // non-positive pivot in the Cholesky factorisation
+  double gmax;        // ||A^T b||_inf (path)
+  unsigned int counters[kNumCounters];
+};
+
+// Element access for the supported storage types.
+enum StreamMode { kModeU = 0, kModeT = 1, kModeGmax = 2 };
+enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
+
+struct ProxParams {
+  double sigma, lam1, lam2, thr, onep;  // thr = sigma*lam1, onep = 1 + sigma*lam2
+};
+
+// ---- launch wrappers (kern_vec.cu)
+int vec_grid(long long n, int sms);
+void launch_prox_count(int mode, const double* x, double* u, const double* t, double* y, const double* d,
+                       long long n, int m, ProxParams pp, int apply_update, DevState* st,
+                       long long* counts, double* partials, int grid, cudaStream_t s);
+void launch_prox_scatter(int mode, const double* x, const double* u, long long n, ProxParams pp,
+                         const long long* offsets, int32_t* J, double* wJ, int grid, cudaStream_t s);
+void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sms, cudaStream_t s);
+void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t* J, const DevState* st,
+                   long long r_host, long long rcap, double* P, long long ldp, float* P32, long long ldp32,
+                   int sms, cudaStream_t s);
+void launch_gemv_n_partial(const double* P, long long ldp, int m, const double* coef, const DevState* st,
+                           long long r_host, long long rcap, double* part, cudaStream_t s);
+// out = ca*a + cb*b + cs*sum_groups(part); norms selected by `which` (see kern_vec.cu)
+void launch_combine(double* out, const double* a, double ca, const double* b, double cb, const double* part,
+                    double cs, int m, int which, const double* y, const double* bb, const double* g,
+                    DevState* st, double* scratch, cudaStream_t s);
+// out_k = ch*h_k + cq*q_k + cd*dot(P[:,k], v)
+void launch_gemv_t(const double* P, long long ldp, int m, long long r, const double* v, double* out,
+                   const double* h, double ch, const double* q, double cq, double cd, int sms, cudaStream_t s);
+void launch_absmax_finish(DevState* st, cudaStream_t s);
+
+// ---- linear algebra (kern_linalg.cu)
+void launch_syrk_tn(const float* P32, long long ldp32, int m, long long r, double diag, float* G, long long ldg,
+                    cudaStream_t s);
+void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, double kappa, float* G, long long ldg,
+                    cudaStream_t s);
+void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s);
+// acc = (first ? c : acc + c) with (L L^T) c = rhs
+void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
+                     cudaStream_t s);
+
+// ---- streams over A (kern_stream.cu)
+void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,
+                   double* out, const double* x, const double* u, ProxParams pp, double mu, double beta,
+                   int max_ls, int fused, DevState* st, double* partials, int grid, cudaStream_t s);
+void launch_ls_fallback(const double* x, const double* u, const double* t, long long n, ProxParams pp, double mu,
+                        double beta, int max_ls, int fused, DevState* st, double* partials, int grid,
+                        cudaStream_t s);
+int stream_grid(int sms);
+
+}  // namespace ssnal

@@ -1,0 +1,400 @@
+// O(n) and O(m r) kernels of the SsN step:
+//   * prox + active set + ordered compaction of J (eqs. prox_elastic, Q_def),
+//   * gather of A_J into a packed panel,
+//   * the panel GEMVs A_J w (eq. grad_phy) and A_J^T v (eq. smw_formula),
+//   * m-vector combines with the scalar products the line search needs.
+// Every reduction runs in a fixed order, so results are bitwise repeatable.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ssnal {
+
+constexpr int kVecThreads = 256;
+
+int vec_grid(long long n, int sms) {
+  long long g = (n + 2047) / 2048;
+  long long cap = 4LL * sms;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// Inclusive scan over the block of one long long per thread (blockDim == 256).
+__device__ long long block_incl_scan(long long v, long long* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  __syncthreads();
+  if (lane == 31) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = (lane < (kVecThreads / 32)) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < (kVecThreads / 32)) sh[lane] = w;
+  }
+  __syncthreads();
+  long long add = warp > 0 ? sh[warp - 1] : 0;
+  __syncthreads();
+  return v + add;
+}
+
+__device__ __forceinline__ void block_range(long long n, long long& start, long long& stop) {
+  long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + kVecThreads - 1) / kVecThreads * kVecThreads;
+  start = (long long)blockIdx.x * chunk;
+  stop = start + chunk;
+  if (stop > n) stop = n;
+  if (start > n) start = n;
+}
+
+// Pass 1 of the prox / active-set step.  Optionally applies the accepted
+// line-search step first (u += s t, y += s d).  Per block: number of active
+// entries and partial norms; the last block scans the counts into offsets and
+// reduces the norms into the state.
+// counts: [0, grid) per-block counts, [grid, 2*grid] exclusive offsets.
+// partials: grid x 6 doubles.
+template <int MODE>
+__global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __restrict__ x, double* __restrict__ u,
+                                                            const double* __restrict__ t, double* __restrict__ y,
+                                                            const double* __restrict__ d, long long n, int m,
+                                                            ProxParams pp, int apply_update, DevState* st,
+                                                            long long* counts, double* partials) {
+  __shared__ double red[32];
+  __shared__ long long shl[32];
+  long long start, stop;
+  block_range(n, start, stop);
+  const double s = apply_update ? st->s : 0.0;
+  if (apply_update && blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = __dadd_rn(y[i], __dmul_rn(s, d[i]));
+  }
+  long long cnt = 0;
+  double w2 = 0, w1 = 0, xw2 = 0, vw2 = 0, pen = 0;
+  for (long long j = start + threadIdx.x; j < stop; j += blockDim.x) {
+    const double xj = x[j];
+    if (MODE == kProxSupport) {
+      if (xj != 0.0) cnt++;
+      continue;
+    }
+    double uj = u[j];
+    if (apply_update) {
+      uj = fma(s, t[j], uj);
+      u[j] = uj;
+    }
+    const double v = v_of(xj, uj, pp.sigma);
+    const double w = prox_value(v, pp);
+    if (w != 0.0) cnt++;
+    w2 += w * w;
+    w1 += fabs(w);
+    xw2 += (xj - w) * (xj - w);
+    vw2 += (v - w) * (v - w);
+    const double e = fmax(fabs(uj) - pp.lam1, 0.0);
+    pen += e * e;
+  }
+  // block totals
+  long long tot = block_incl_scan(cnt, shl);
+  if (threadIdx.x == kVecThreads - 1) counts[blockIdx.x] = tot;
+  double q[5] = {w2, w1, xw2, vw2, pen};
+  for (int k = 0; k < 5; k++) {
+    double b = block_sum(q[k], red);
+    if (threadIdx.x == 0) partials[blockIdx.x * 6 + k] = b;
+  }
+  if (!last_block(&st->counters[kCtrProx])) return;
+  // ---- last block: exclusive offsets and reductions, fixed order
+  const int G = gridDim.x;
+  long long* offsets = counts + G;
+  long long carry = 0;
+  for (int base = 0; base < G; base += kVecThreads) {
+    int b = base + threadIdx.x;
+    long long c = (b < G) ? ld_cg(&counts[b]) : 0;
+    long long incl = block_incl_scan(c, shl);
+    if (b < G) offsets[b] = carry + incl - c;
+    __syncthreads();
+    if (threadIdx.x == kVecThreads - 1) shl[31] = incl;
+    __syncthreads();
+    carry += shl[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    offsets[G] = carry;
+    st->r = carry;
+  }
+  if (MODE == kProxThreshold) {
+    for (int k = 0; k < 5; k++) {
+      double acc = 0;
+      for (int b = threadIdx.x; b < G; b += kVecThreads) acc += ld_cg(&partials[b * 6 + k]);
+      double tsum = block_sum(acc, red);
+      if (threadIdx.x == 0) {
+        if (k == 0) st->w2 = tsum;
+        if (k == 1) st->w1 = tsum;
+        if (k == 2) st->xw2 = tsum;
+        if (k == 3) st->vw2 = tsum;
+        if (k == 4) st->dualpen = tsum;
+      }
+    }
+  }
+  reset_counter(&st->counters[kCtrProx]);
+}
+
+// Pass 2: ordered compaction.  Block b writes its active indices, ascending,
+// starting at offsets[b]; w_J holds the prox values (eq. prox_elastic).
+template <int MODE>
+__global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __restrict__ x,
+                                                              const double* __restrict__ u, long long n,
+                                                              ProxParams pp, const long long* __restrict__ offsets,
+                                                              int32_t* __restrict__ J, double* __restrict__ wJ) {
+  __shared__ long long shl[32];
+  __shared__ long long tile_total;
+  long long start, stop;
+  block_range(n, start, stop);
+  long long pos = offsets[blockIdx.x];
+  for (long long base = start; base < stop; base += blockDim.x) {
+    long long j = base + threadIdx.x;
+    double w = 0.0;
+    bool act = false;
+    if (j < stop) {
+      const double xj = x[j];
+      if (MODE == kProxSupport) {
+        w = xj;
+        act = xj != 0.0;
+      } else {
+        const double v = v_of(xj, u[j], pp.sigma);
+        w = prox_value(v, pp);
+        act = w != 0.0;
+      }
+    }
+    long long incl = block_incl_scan(act ? 1 : 0, shl);
+    if (act) {
+      long long p = pos + incl - 1;
+      J[p] = (int32_t)j;
+      wJ[p] = w;
+    }
+    if (threadIdx.x == kVecThreads - 1) tile_total = incl;
+    __syncthreads();
+    pos += tile_total;
+    __syncthreads();
+  }
+}
+
+// x <- prox_{sigma p}(x - sigma u): the multiplier update of eq. update_x
+// written through the Moreau decomposition.
+__global__ void k_set_x(double* __restrict__ x, const double* __restrict__ u, long long n, ProxParams pp) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    x[j] = prox_value(v_of(x[j], u[j], pp.sigma), pp);
+}
+
+// Element loaders for the gather: value of A(i, col) as double.
+struct LoadF64 {
+  const double* A;
+  __device__ double operator()(long long off) const { return A[off]; }
+};
+struct LoadF32 {
+  const float* A;
+  __device__ double operator()(long long off) const { return (double)A[off]; }
+};
+struct LoadBF16 {
+  const __nv_bfloat16* A;
+  __device__ double operator()(long long off) const { return (double)__bfloat162float(A[off]); }
+};
+
+// Gather of A_J: P[:, k] = A[:, J[k]] (FP64) and P32[:, k] = float(P[:, k]).
+// One warp per column, grid-stride.  If r exceeds the panel capacity nothing is
+// written and the overflow flag is raised for the host.
+template <class Load>
+__global__ void k_gather(Load ld, long long lda, int m, const int32_t* __restrict__ J, const DevState* st,
+                         long long r_host, long long rcap, double* __restrict__ P, long long ldp,
+                         float* __restrict__ P32, long long ldp32, int* overflow) {
+  const long long r = r_host >= 0 ? r_host : st->r;
+  if (r > rcap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *overflow = 1;
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long tw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = gw; k < r; k += tw) {
+    const long long src = (long long)J[k] * lda;
+    double* dst = P + k * ldp;
+    float* dst32 = P32 + k * ldp32;
+    for (int i = lane; i < m; i += 32) {
+      double v = ld(src + i);
+      dst[i] = v;
+      dst32[i] = (float)v;
+    }
+  }
+}
+
+// part[g*m + i] = sum_{k in group g} P[i, k] * coef[k]; groups are contiguous
+// ranges of ceil(r / kGemvGroups) columns.  Grid (ceil(m/256), kGemvGroups).
+__global__ void __launch_bounds__(kVecThreads) k_gemv_n_partial(const double* __restrict__ P, long long ldp, int m,
+                                                                const double* __restrict__ coef,
+                                                                const DevState* st, long long r_host,
+                                                                long long rcap, double* __restrict__ part) {
+  const long long r = r_host >= 0 ? r_host : st->r;
+  if (r > rcap) return;  // the gather raised the overflow flag; the host redoes this step
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  const long long gs = (r + kGemvGroups - 1) / kGemvGroups;
+  long long k0 = g * gs, k1 = k0 + gs;
+  if (k1 > r) k1 = r;
+  if (i >= m) return;
+  double acc = 0.0;
+  for (long long k = k0; k < k1; k++) acc = fma(P[i + k * ldp], coef[k], acc);
+  part[(long long)g * m + i] = acc;
+}
+
+// out_i = ca*a_i + cb*b_i + cs*sum_g part[g][i], then optional scalar products.
+// which = 1: gradient (g2, y2, yg2, by); which = 2: direction (gd, yd, dd, bd).
+__global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ out, const double* __restrict__ a,
+                                                         double ca, const double* __restrict__ b, double cb,
+                                                         const double* __restrict__ part, double cs, int m,
+                                                         int which, const double* __restrict__ yv,
+                                                         const double* __restrict__ bv,
+                                                         const double* __restrict__ gv, DevState* st,
+                                                         double* scratch) {
+  __shared__ double red[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double o = 0.0;
+  if (i < m) {
+    double sum = 0.0;
+    if (part) {
+      for (int g = 0; g < kGemvGroups; g++) sum += part[(long long)g * m + i];
+    }
+    double lin = 0.0;
+    if (a) lin = ca * a[i];
+    if (b) lin = a ? lin + cb * b[i] : cb * b[i];
+    o = (a || b) ? (part ? lin + cs * sum : lin) : cs * sum;
+    out[i] = o;
+  }
+  if (which == 0) return;
+  double q[4] = {0, 0, 0, 0};
+  if (i < m) {
+    const double yi = yv[i], bi = bv[i];
+    if (which == 1) {
+      q[0] = o * o;
+      q[1] = yi * yi;
+      q[2] = (yi - o) * (yi - o);
+      q[3] = bi * yi;
+    } else {
+      const double gi = gv[i];
+      q[0] = gi * o;
+      q[1] = yi * o;
+      q[2] = o * o;
+      q[3] = bi * o;
+    }
+  }
+  for (int k = 0; k < 4; k++) {
+    double bsum = block_sum(q[k], red);
+    if (threadIdx.x == 0) scratch[blockIdx.x * 4 + k] = bsum;
+  }
+  if (!last_block(&st->counters[kCtrCombine])) return;
+  if (threadIdx.x == 0) {
+    double tot[4] = {0, 0, 0, 0};
+    for (int bl = 0; bl < (int)gridDim.x; bl++)
+      for (int k = 0; k < 4; k++) tot[k] += ld_cg(&scratch[bl * 4 + k]);
+    if (which == 1) {
+      st->g2 = tot[0];
+      st->y2 = tot[1];
+      st->yg2 = tot[2];
+      st->by = tot[3];
+    } else {
+      st->gd = tot[0];
+      st->yd = tot[1];
+      st->dd = tot[2];
+      st->bd = tot[3];
+    }
+  }
+  reset_counter(&st->counters[kCtrCombine]);
+}
+
+// out_k = ch*h_k + cq*q_k + cd*dot(P[:, k], v), one warp per column.
+__global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, long long r, const double* __restrict__ v,
+                         double* __restrict__ out, const double* __restrict__ h, double ch,
+                         const double* __restrict__ q, double cq, double cd) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long tw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long k = gw; k < r; k += tw) {
+    const double* col = P + k * ldp;
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc = fma(col[i], v[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      double o = cd * acc;
+      if (h) o = ch * h[k] + o;
+      if (q) o = cq * q[k] + o;
+      out[k] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_prox_count(int mode, const double* x, double* u, const double* t, double* y, const double* d,
+                       long long n, int m, ProxParams pp, int apply_update, DevState* st, long long* counts,
+                       double* partials, int grid, cudaStream_t s) {
+  if (mode == kProxSupport)
+    k_prox_count<kProxSupport><<<grid, kVecThreads, 0, s>>>(x, u, t, y, d, n, m, pp, 0, st, counts, partials);
+  else
+    k_prox_count<kProxThreshold><<<grid, kVecThreads, 0, s>>>(x, u, t, y, d, n, m, pp, apply_update, st, counts,
+                                                               partials);
+}
+
+void launch_prox_scatter(int mode, const double* x, const double* u, long long n, ProxParams pp,
+                         const long long* offsets, int32_t* J, double* wJ, int grid, cudaStream_t s) {
+  if (mode == kProxSupport)
+    k_prox_scatter<kProxSupport><<<grid, kVecThreads, 0, s>>>(x, u, n, pp, offsets, J, wJ);
+  else
+    k_prox_scatter<kProxThreshold><<<grid, kVecThreads, 0, s>>>(x, u, n, pp, offsets, J, wJ);
+}
+
+void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sms, cudaStream_t s) {
+  long long g = (n + kVecThreads - 1) / kVecThreads;
+  if (g > 8LL * sms) g = 8LL * sms;
+  if (g < 1) g = 1;
+  k_set_x<<<(int)g, kVecThreads, 0, s>>>(x, u, n, pp);
+}
+
+void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t* J, const DevState* st,
+                   long long r_host, long long rcap, double* P, long long ldp, float* P32, long long ldp32, int sms,
+                   cudaStream_t s) {
+  int grid = 2 * sms;
+  int* ovf = const_cast<int*>(&st->overflow);
+  if (dtype == 0)
+    k_gather<<<grid, 256, 0, s>>>(LoadF64{(const double*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
+  else if (dtype == 1)
+    k_gather<<<grid, 256, 0, s>>>(LoadF32{(const float*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
+  else
+    k_gather<<<grid, 256, 0, s>>>(LoadBF16{(const __nv_bfloat16*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32,
+                                  ldp32, ovf);
+}
+
+void launch_gemv_n_partial(const double* P, long long ldp, int m, const double* coef, const DevState* st,
+                           long long r_host, long long rcap, double* part, cudaStream_t s) {
+  dim3 grid((m + kVecThreads - 1) / kVecThreads, kGemvGroups);
+  k_gemv_n_partial<<<grid, kVecThreads, 0, s>>>(P, ldp, m, coef, st, r_host, rcap, part);
+}
+
+void launch_combine(double* out, const double* a, double ca, const double* b, double cb, const double* part,
+                    double cs, int m, int which, const double* y, const double* bb, const double* g, DevState* st,
+                    double* scratch, cudaStream_t s) {
+  int grid = (m + kVecThreads - 1) / kVecThreads;
+  k_combine<<<grid, kVecThreads, 0, s>>>(out, a, ca, b, cb, part, cs, m, which, y, bb, g, st, scratch);
+}
+
+void launch_gemv_t(const double* P, long long ldp, int m, long long r, const double* v, double* out, const double* h,
+                   double ch, const double* q, double cq, double cd, int sms, cudaStream_t s) {
+  if (r <= 0) return;
+  long long warps = r;
+  long long blocks = (warps * 32 + 255) / 256;
+  if (blocks > 4LL * sms) blocks = 4LL * sms;
+  k_gemv_t<<<(int)blocks, 256, 0, s>>>(P, ldp, m, r, v, out, h, ch, q, cq, cd);
+}
+
+}  // namespace ssnal
