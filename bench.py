@@ -1,0 +1,285 @@
+#!/usr/bin/env python
+"""Benchmark of the SsNAL-EN hot path on GB300.
+
+Workload (one "step"): the FP64 warm-started regularization path on the
+synthetic design of the path configuration -- m = 500 observations,
+n = 100,000 features in 100-feature AR(1) blocks (rho = 0.7), 20 nonzeros of
++-U[1,3], snr 5, alpha = 0.6, c = 1.0 -> 0.05 geometric (20 points), KKT
+tolerance 1e-6.  The metric is Elastic Net fits per second, counting a fit
+only when both res(kkt1) and res(kkt3) (FP64) are <= 1e-6.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle on the same workload (host cores).
+For N > 1 (torchrun) every rank solves its own replica of the workload
+(independent problems, no data-path collective); value = all fits / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "EN fits/s to KKT<=1e-6"
+UNIT = "fits/s"
+WORKLOAD = ("FP64 warm-started Elastic Net path: m=500, n=100000, 100-feature AR(1) blocks rho=0.7, "
+            "20 nonzeros +-U[1,3], snr 5, alpha=0.6, c 1.0->0.05 geometric (20 points), tol 1e-6, seed 2")
+M, N_FEAT, K_POINTS, ALPHA, SEED = 500, 100_000, 20, 0.6, 2
+TOL = 1e-6
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < len(self.FIELDS):
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx = float(parts[1])
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, parts[3:7]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload():
+    from paper_2006_03970_gb300 import synth
+    p = synth.config2(seed=SEED, m=M, n=N_FEAT)
+    return p, list(synth.path_grid(K_POINTS, 0.05))
+
+
+def _count_fits(results, done):
+    return sum(1 for r in results[:done] if r.status == 0 and r.kkt1 <= TOL and r.kkt3 <= TOL)
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import ssnal_en_ref as R
+    p, grid = _workload()
+    At = np.ascontiguousarray(p.At, dtype=np.float64)
+    for _ in range(args.warmup):
+        R.path(At, p.b, ALPHA, grid)
+    fits, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        res = R.path(At, p.b, ALPHA, grid)
+        fits += sum(1 for r in res if r.converged and r.kkt1 <= TOL and r.kkt3 <= TOL)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    value = fits / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (A is 400 MB)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full 20-point paths (NumPy/SciPy FP64, default BLAS threads)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline():
+    """The FP64 oracle on a bounded sample: one full 20-point path of the same workload."""
+    import numpy as np
+    from oracle import ssnal_en_ref as R
+    p, grid = _workload()
+    At = np.ascontiguousarray(p.At, dtype=np.float64)
+    t0 = time.perf_counter()
+    res = R.path(At, p.b, ALPHA, grid)
+    dt = time.perf_counter() - t0
+    fits = sum(1 for r in res if r.converged and r.kkt1 <= TOL and r.kkt3 <= TOL)
+    return {"value": fits / dt, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": "one full 20-point path of the same workload (NumPy/SciPy FP64, default BLAS threads)",
+            "seconds": dt}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2006_03970_gb300 as pkg
+    pkg.load_library()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    p, grid = _workload()
+    ctx = pkg.Context(p.At)
+    b = torch.as_tensor(p.b, dtype=torch.float64, device="cuda")
+    X = torch.zeros((len(grid), ctx.n), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        pkg.ssnal_en_path(ctx.ctx, b, ALPHA, grid, X)
+    torch.cuda.synchronize()
+    barrier()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the timed region
+    prof0 = pkg.ssnal_en_profile(ctx.ctx, True, True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fits = 0
+    for _ in range(args.steps):
+        st, res, done = pkg.ssnal_en_path(ctx.ctx, b, ALPHA, grid, X)
+        fits += _count_fits(res, done)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof1 = pkg.ssnal_en_profile(ctx.ctx, False, False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(fits)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms, fits_all = tmax[0].item(), t[1].item()
+    else:
+        fits_all = fits
+    value = fits_all / (ms / 1e3)
+
+    # end to end through the public C ABI with host buffers (b in, all solutions out)
+    b_host = torch.empty(M, dtype=torch.float64, pin_memory=True)
+    b_host.copy_(torch.from_numpy(p.b))
+    X_host = torch.empty((len(grid), ctx.n), dtype=torch.float64, pin_memory=True)
+    bh, xh = b_host.numpy(), X_host.numpy()
+    pkg.ssnal_en_path_host(ctx.ctx, bh, ALPHA, grid, xh)
+    barrier()
+    t0 = time.perf_counter()
+    efits = 0
+    for _ in range(args.steps):
+        st, res, done = pkg.ssnal_en_path_host(ctx.ctx, bh, ALPHA, grid, xh)
+        efits += _count_fits(res, done)
+    edt = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([edt, float(efits)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        edt, efits = tmax[0].item(), t[1].item()
+    e2e_value = efits / edt
+
+    peak, peak_kind = _peaks()
+    launches = prof1["stream_launches"] - 0
+    s_ms = prof1["stream_ms"]
+    achieved = (prof1["stream_bytes"] / (s_ms / 1e3) / 1e9) if s_ms > 0 else None
+    roofline = {"kernel": "k_stream_f64<kModeT> (t = A^T d with the fused line-search trial sums)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_kind": peak_kind, "launches": launches,
+                "avg_launch_us": (s_ms / launches * 1e3) if launches else None,
+                "bytes_per_launch": (prof1["stream_bytes"] / launches) if launches else None,
+                "share_of_step": (s_ms / ms) if ms > 0 else None}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (A is 400 MB, L2 129 MB)",
+                       "fits_per_step": K_POINTS, "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * M,
+                    "d2h_bytes_per_step": 8 * len(grid) * ctx.n},
+            "gpu_launches": prof1["kernel_launches"] - prof0["kernel_launches"],
+            "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

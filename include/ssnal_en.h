@@ -153,6 +153,21 @@ ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* ctx, const double* b_host, doub
                                    const double* c_grid, int32_t K, double* X_host,
                                    ssnal_en_result* out, int32_t* n_done);
 
+/* Kernel accounting of this context.  When enabled, CUDA events are recorded on
+ * the context's stream around every launch of the A^T d stream (the one pass
+ * over A of each Newton step, eq. line_search fused in) and their elapsed
+ * times are summed at the next synchronisation.
+ *  enable  1: record from now on, 0: stop recording.
+ *  reset   1: zero the sums before reporting.
+ *  stream_ms        summed device time of those launches (host, may be NULL)
+ *  stream_launches  number of those launches (host, may be NULL)
+ *  stream_bytes     algorithmic bytes of those launches: A once (m*n*elem) plus
+ *                   the vectors d (read), x, u (read) and t (written)
+ *  kernel_launches  kernels launched by this library in this process so far
+ * Synchronises the stream.  Errors: EINVAL (null ctx), ECUDA. */
+ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t reset, double* stream_ms,
+                                 int64_t* stream_launches, double* stream_bytes, int64_t* kernel_launches);
+
 /* ---------------------------------------------------------------------------
  * Single steps of the hot path, exposed for tests and for callers that build
  * their own loops.  Each runs the same kernels the solver uses.

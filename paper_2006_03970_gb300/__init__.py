@@ -21,7 +21,7 @@ __all__ = [
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
     "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_prox_active", "ssnal_en_op_grad",
-    "ssnal_en_op_newton", "Context",
+    "ssnal_en_op_newton", "ssnal_en_profile", "Context",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,7 +66,7 @@ class Result(ctypes.Structure):
 _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
-           "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton"]
+           "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile"]
 
 
 def load_library(path: str | None = None):
@@ -96,6 +96,8 @@ def load_library(path: str | None = None):
     L.ssnal_en_op_prox_active.argtypes = [vp, vp, vp, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64)]
     L.ssnal_en_op_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     L.ssnal_en_op_newton.argtypes = [vp, i64, dbl, vp, vp]
+    L.ssnal_en_profile.argtypes = [vp, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(dbl),
+                                   ctypes.POINTER(i64)]
     for name in EXPORTS:
         if getattr(L, name).restype is ctypes.c_int:
             getattr(L, name).restype = i32
@@ -249,6 +251,16 @@ def ssnal_en_op_grad(ctx, J, wJ, r, y, b, g):
 def ssnal_en_op_newton(ctx, r, kappa, g, d):
     return _check(load_library().ssnal_en_op_newton(ctx, int(r), float(kappa), _ptr(g), _ptr(d)),
                   "ssnal_en_op_newton", allow=(OK, ENOCONV))
+
+
+def ssnal_en_profile(ctx, enable: bool, reset: bool = False):
+    """Returns dict(stream_ms, stream_launches, stream_bytes, kernel_launches)."""
+    ms, nl, by, kl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    _check(load_library().ssnal_en_profile(ctx, int(bool(enable)), int(bool(reset)), ctypes.byref(ms),
+                                           ctypes.byref(nl), ctypes.byref(by), ctypes.byref(kl)),
+           "ssnal_en_profile")
+    return {"stream_ms": ms.value, "stream_launches": nl.value, "stream_bytes": by.value,
+            "kernel_launches": kl.value}
 
 
 class Context:

@@ -11,6 +11,8 @@
 #include <chrono>
 #include <cmath>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "../../include/ssnal_en.h"
 #include "internal.h"
@@ -48,6 +50,11 @@ struct ssnal_en_ctx {
   int64_t ldg = 0;
   double* Xdev = nullptr;  // path_host output staging
   int64_t Xcap = 0;
+  // event timing of the A^T d stream kernel (ssnal_en_profile)
+  int prof = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool, ev_pending;
+  double prof_ms = 0.0, prof_bytes = 0.0;
+  int64_t prof_launches = 0;
 };
 
 namespace {
@@ -115,6 +122,16 @@ ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
 }
 
 void free_all(ssnal_en_ctx* c) {
+  for (auto& pr : c->ev_pool) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (auto& pr : c->ev_pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  c->ev_pool.clear();
+  c->ev_pending.clear();
   dev_free(c->st);
   if (c->st_host) cudaFreeHost(c->st_host);
   dev_free(c->u);
@@ -155,9 +172,46 @@ ProxParams make_pp(double sigma, double lam1, double lam2) {
   return pp;
 }
 
+// Times of the stream launches recorded since the last synchronisation.
+void prof_harvest(ssnal_en_ctx* c) {
+  for (auto& pr : c->ev_pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->prof_ms += ms;
+    c->ev_pool.push_back(pr);
+  }
+  c->ev_pending.clear();
+}
+
 ssnal_en_status read_state(ssnal_en_ctx* c) {
   CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (!c->ev_pending.empty()) prof_harvest(c);
+  return SSNAL_EN_OK;
+}
+
+// The A^T d stream of one Newton step, bracketed by CUDA events when profiling.
+ssnal_en_status stream_t(ssnal_en_ctx* c, const double* x, ProxParams pp) {
+  const ssnal_en_options& o = c->opt;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (c->prof) {
+    if (c->ev_pool.empty()) {
+      CK(cudaEventCreate(&ev.first));
+      CK(cudaEventCreate(&ev.second));
+    } else {
+      ev = c->ev_pool.back();
+      c->ev_pool.pop_back();
+    }
+    CK(cudaEventRecord(ev.first, c->stream));
+  }
+  launch_stream(kModeT, c->dtype, c->A, c->lda, (int)c->m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
+                o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
+  if (c->prof) {
+    CK(cudaEventRecord(ev.second, c->stream));
+    c->ev_pending.push_back(ev);
+    c->prof_launches++;
+    const double es = (double)elem_size(c->dtype);
+    c->prof_bytes += (double)c->m * (double)c->n * es + 3.0 * 8.0 * (double)c->n + 8.0 * (double)c->m;
+  }
   return SSNAL_EN_OK;
 }
 
@@ -304,8 +358,7 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
       if (!(gn > o.tol) || newton_here >= o.max_newton) break;
       const int64_t r = h.r;
       if ((e = newton_direction(c, r, kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
-      launch_stream(kModeT, c->dtype, c->A, c->lda, m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
-                    o.ls_fused, c->st, c->partials, c->grid_stream, s);
+      if ((e = stream_t(c, x, pp)) != SSNAL_EN_OK) return e;
       launch_ls_fallback(x, c->u, c->t, c->n, pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st, c->partials,
                          c->grid_stream, s);
       CK(cudaGetLastError());
@@ -568,6 +621,24 @@ ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* c, const double* b_host, double
     CK(cudaMemcpyAsync(X_host, X, sizeof(double) * (size_t)done * c->n, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return e;
+}
+
+ssnal_en_status ssnal_en_profile(ssnal_en_ctx* c, int32_t enable, int32_t reset, double* stream_ms,
+                                 int64_t* stream_launches, double* stream_bytes, int64_t* kernel_launches) {
+  if (!c) return SSNAL_EN_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  prof_harvest(c);
+  if (reset) {
+    c->prof_ms = 0.0;
+    c->prof_bytes = 0.0;
+    c->prof_launches = 0;
+  }
+  c->prof = enable ? 1 : 0;
+  if (stream_ms) *stream_ms = c->prof_ms;
+  if (stream_launches) *stream_launches = c->prof_launches;
+  if (stream_bytes) *stream_bytes = c->prof_bytes;
+  if (kernel_launches) *kernel_launches = g_launches.load();
+  return SSNAL_EN_OK;
 }
 
 ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* c, const double* y, double* u) {

@@ -5,7 +5,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace ssnal {
+
+// Number of kernels this library has launched (all contexts).
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 constexpr int kMaxM = 4096;       // largest supported number of observations m
 constexpr int kMaxLS = 64;        // largest supported number of line-search trials

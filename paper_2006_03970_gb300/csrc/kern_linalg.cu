@@ -229,6 +229,7 @@ void launch_syrk_tn(const float* P32, long long ldp32, int m, long long r, doubl
                     cudaStream_t s) {
   int T = (int)((r + kT - 1) / kT);
   int blocks = T * (T + 1) / 2;
+  if (blocks > 0) count_launch();
   if (blocks > 0) k_syrk_tn<<<blocks, 256, 0, s>>>(P32, ldp32, m, (int)r, (float)diag, G, ldg);
 }
 
@@ -236,15 +237,18 @@ void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, doubl
                     cudaStream_t s) {
   int T = (m + kT - 1) / kT;
   int blocks = T * (T + 1) / 2;
+  if (blocks > 0) count_launch();
   if (blocks > 0) k_syrk_nt<<<blocks, 256, 0, s>>>(P32, ldp32, m, r, (float)kappa, G, ldg);
 }
 
 void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
   for (int kb = 0; kb < N; kb += kCholNB) {
     const int nb = N - kb < kCholNB ? N - kb : kCholNB;
+    count_launch();
     k_potrf_diag<<<1, dim3(32, 32), 0, s>>>(G, ldg, kb, nb, st);
     const int rem = N - kb - nb;
     if (rem > 0) {
+      count_launch(2);
       k_trsm_panel<<<(rem + 255) / 256, 256, 0, s>>>(G, ldg, kb, nb, N);
       const int T = (rem + kT - 1) / kT;
       k_syrk_update<<<T * (T + 1) / 2, 256, 0, s>>>(G, ldg, kb, nb, N);
@@ -255,6 +259,7 @@ void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      cudaStream_t s) {
   if (N <= 0) return;
+  count_launch();
   k_trsv_llt<<<1, kTrsvThreads, (size_t)N * sizeof(float), s>>>(L, ldl, N, rhs, acc, first);
 }
 

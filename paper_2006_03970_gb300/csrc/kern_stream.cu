@@ -199,6 +199,7 @@ void launch_stream(int mode, int dtype, const void* A, long long lda, int m, lon
   const size_t smem = (size_t)((m + 63) & ~63) * sizeof(double);
   (void)dtype;
   const double* Ad = (const double*)A;
+  count_launch();
   if (mode == kModeU)
     k_stream_f64<kModeU><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
   else if (mode == kModeT)
@@ -211,6 +212,7 @@ void launch_ls_fallback(const double* x, const double* u, const double* t, long 
                         double beta, int max_ls, int fused, DevState* st, double* partials, int grid, cudaStream_t s) {
   if (fused >= max_ls) return;
   LsParams lp{pp, mu, beta, max_ls, fused};
+  count_launch();
   k_ls_fallback<<<grid, 256, 0, s>>>(x, u, t, n, lp, st, partials);
 }
 

@@ -10,6 +10,8 @@
 
 namespace ssnal {
 
+std::atomic<long long> g_launches{0};
+
 constexpr int kVecThreads = 256;
 
 int vec_grid(long long n, int sms) {
@@ -339,6 +341,7 @@ __global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, lon
 void launch_prox_count(int mode, const double* x, double* u, const double* t, double* y, const double* d,
                        long long n, int m, ProxParams pp, int apply_update, DevState* st, long long* counts,
                        double* partials, int grid, cudaStream_t s) {
+  count_launch();
   if (mode == kProxSupport)
     k_prox_count<kProxSupport><<<grid, kVecThreads, 0, s>>>(x, u, t, y, d, n, m, pp, 0, st, counts, partials);
   else
@@ -348,6 +351,7 @@ void launch_prox_count(int mode, const double* x, double* u, const double* t, do
 
 void launch_prox_scatter(int mode, const double* x, const double* u, long long n, ProxParams pp,
                          const long long* offsets, int32_t* J, double* wJ, int grid, cudaStream_t s) {
+  count_launch();
   if (mode == kProxSupport)
     k_prox_scatter<kProxSupport><<<grid, kVecThreads, 0, s>>>(x, u, n, pp, offsets, J, wJ);
   else
@@ -358,6 +362,7 @@ void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sm
   long long g = (n + kVecThreads - 1) / kVecThreads;
   if (g > 8LL * sms) g = 8LL * sms;
   if (g < 1) g = 1;
+  count_launch();
   k_set_x<<<(int)g, kVecThreads, 0, s>>>(x, u, n, pp);
 }
 
@@ -365,6 +370,7 @@ void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t
                    long long r_host, long long rcap, double* P, long long ldp, float* P32, long long ldp32, int sms,
                    cudaStream_t s) {
   int grid = 2 * sms;
+  count_launch();
   int* ovf = const_cast<int*>(&st->overflow);
   if (dtype == 0)
     k_gather<<<grid, 256, 0, s>>>(LoadF64{(const double*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
@@ -378,6 +384,7 @@ void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t
 void launch_gemv_n_partial(const double* P, long long ldp, int m, const double* coef, const DevState* st,
                            long long r_host, long long rcap, double* part, cudaStream_t s) {
   dim3 grid((m + kVecThreads - 1) / kVecThreads, kGemvGroups);
+  count_launch();
   k_gemv_n_partial<<<grid, kVecThreads, 0, s>>>(P, ldp, m, coef, st, r_host, rcap, part);
 }
 
@@ -385,6 +392,7 @@ void launch_combine(double* out, const double* a, double ca, const double* b, do
                     double cs, int m, int which, const double* y, const double* bb, const double* g, DevState* st,
                     double* scratch, cudaStream_t s) {
   int grid = (m + kVecThreads - 1) / kVecThreads;
+  count_launch();
   k_combine<<<grid, kVecThreads, 0, s>>>(out, a, ca, b, cb, part, cs, m, which, y, bb, g, st, scratch);
 }
 
@@ -394,6 +402,7 @@ void launch_gemv_t(const double* P, long long ldp, int m, long long r, const dou
   long long warps = r;
   long long blocks = (warps * 32 + 255) / 256;
   if (blocks > 4LL * sms) blocks = 4LL * sms;
+  count_launch();
   k_gemv_t<<<(int)blocks, 256, 0, s>>>(P, ldp, m, r, v, out, h, ch, q, cq, cd);
 }
 
