@@ -196,6 +196,38 @@ ssnal_en_status ssnal_en_op_grad(ssnal_en_ctx* ctx, const int32_t* J, const doub
  * ssnal_en_op_grad call (same J, r).  g, d device length m. */
 ssnal_en_status ssnal_en_op_newton(ssnal_en_ctx* ctx, int64_t r, double kappa, const double* g, double* d);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free prox / active-set step.  The paper has no counterpart to this
+ * entry point; it exists for callers that cannot allocate device memory, for
+ * example code that runs while another component owns the device memory budget
+ * through its own pool, latency-critical loops where cudaMalloc / cudaFree (and
+ * the device synchronisation they can cause) are not acceptable, or plug-in
+ * code that may only touch the buffers it is handed.
+ *
+ * Computes what ssnal_en_op_prox_active computes, without a context:
+ *  x, u    device, length n (FP64)
+ *  J, wJ   device outputs, capacity n: J ascending (int32), wJ the prox values (FP64)
+ *  r       host output: |J|
+ *  stream  cudaStream_t to run on (NULL = legacy default stream); the call
+ *          synchronises it before returning.
+ * Its scratch memory is one fixed array in the library's device code (about
+ * 66 KB, kept by every GPU that loads the library until the process exits):
+ *  - n above SSNAL_EN_STATIC_MAX_N is rejected with ENOTSUP before any device work;
+ *  - the first call on a device looks up the array's device address once
+ *    (cudaGetSymbolAddress with that device current); make that first call
+ *    before any stream capture;
+ *  - all calls on a device share the array and it keeps the last call's
+ *    contents; each call clears what must start at zero, and calls whose GPU
+ *    work overlaps (several streams or host threads) race, so the caller must
+ *    serialise them.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: EINVAL (null pointer, n <= 0, sigma <= 0, negative or non-finite
+ * lambda), ENOTSUP (n too large, device index >= 64), ECUDA. */
+#define SSNAL_EN_STATIC_MAX_N 2097152
+ssnal_en_status ssnal_en_prox_active_static(const double* x, const double* u, int64_t n, double sigma,
+                                            double lambda1, double lambda2, int32_t* J, double* wJ, int64_t* r,
+                                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ __all__ = [
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
     "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_prox_active", "ssnal_en_op_grad",
-    "ssnal_en_op_newton", "ssnal_en_profile", "Context",
+    "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_prox_active_static", "STATIC_MAX_N", "Context",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -30,6 +30,7 @@ LIB_PATH = os.path.join(HERE, "libssnal_en.so")
 F64, F32, BF16, I8_GENO = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ENOCONV, ECUDA, ETIMEOUT, ENOTSUP = range(7)
 _ELEM = {F64: 8, F32: 4, BF16: 2, I8_GENO: 1}
+STATIC_MAX_N = 2097152  # SSNAL_EN_STATIC_MAX_N
 
 
 class SsnalError(RuntimeError):
@@ -66,7 +67,8 @@ class Result(ctypes.Structure):
 _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
-           "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile"]
+           "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
+           "ssnal_en_prox_active_static"]
 
 
 def load_library(path: str | None = None):
@@ -96,6 +98,7 @@ def load_library(path: str | None = None):
     L.ssnal_en_op_prox_active.argtypes = [vp, vp, vp, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64)]
     L.ssnal_en_op_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     L.ssnal_en_op_newton.argtypes = [vp, i64, dbl, vp, vp]
+    L.ssnal_en_prox_active_static.argtypes = [vp, vp, i64, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64), vp]
     L.ssnal_en_profile.argtypes = [vp, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                    ctypes.POINTER(i64)]
     for name in EXPORTS:
@@ -261,6 +264,18 @@ def ssnal_en_profile(ctx, enable: bool, reset: bool = False):
            "ssnal_en_profile")
     return {"stream_ms": ms.value, "stream_launches": nl.value, "stream_bytes": by.value,
             "kernel_launches": kl.value}
+
+
+def ssnal_en_prox_active_static(x, u, sigma, lambda1, lambda2, J, wJ, stream=None) -> int:
+    """Allocation-free prox / active-set step (no context; see the header for the
+    limits and the shared-scratch rules).  x, u: FP64 device tensors of length n;
+    J (int32), wJ (FP64): device outputs of capacity n.  Returns |J|."""
+    r = ctypes.c_int64(0)
+    _check(load_library().ssnal_en_prox_active_static(_ptr(x), _ptr(u), int(x.numel()), float(sigma),
+                                                      float(lambda1), float(lambda2), _ptr(J), _ptr(wJ),
+                                                      ctypes.byref(r), _stream_handle(stream)),
+           "ssnal_en_prox_active_static")
+    return r.value
 
 
 class Context:
