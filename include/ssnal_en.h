@@ -76,7 +76,13 @@ typedef struct {
   int32_t max_al;       /* 100: AL iterations */
   int32_t max_newton;   /* 50: SsN iterations per AL iteration */
   int32_t max_ls;       /* 40: line-search trials per SsN iteration, at most 64 */
-  int32_t precision;    /* 0: FP64 stream arithmetic; 1: mixed (FP32 accumulation of low-precision A) */
+  int32_t precision;    /* 0: FP64 results; the pass over A uses float-float arithmetic on the FP32 pipe
+                           (about 2^-47 relative per product) when every entry of A is 0 or has
+                           magnitude in [2^-100, 2^100], else FP64 FMAs.  For this the context
+                           keeps a float-pair copy of A (same size as A) made at create time.
+                           3: as 0 but without the copy (entries split on the fly, slower).
+                           2: FP64 FMAs always.
+                           1: reserved for the mixed path (low-precision storage of A). */
   int32_t refine_steps; /* 2: iterative-refinement steps of the Newton solve */
   int32_t use_y0;       /* 0: y0 = A x0 - b; 1: take y0 from the y argument of ssnal_en_solve */
   int32_t ls_fused;     /* 16: trial steps evaluated inside the A^T d pass (1..16); later trials

@@ -29,6 +29,12 @@ struct ssnal_en_ctx {
   cudaStream_t stream = nullptr;
   int sms = 0;
   int grid_stream = 0, grid_vec = 0;
+  int ff_ok = 0;       // A's entries allow the float-float stream
+  void* Asplit = nullptr;  // float-pair copy of A for the stream (FP64 storage), or null
+  int64_t lda_split = 0;
+  const void* A_stream = nullptr;  // what the stream reads (A or Asplit) and its leading dimension
+  int64_t lda_stream = 0;
+  int stream_kind = 0;  // kStreamFloatFloat or kStreamDfma (FP64 storage)
   // device workspaces
   DevState* st = nullptr;
   DevState* st_host = nullptr;  // pinned mirror
@@ -43,6 +49,8 @@ struct ssnal_en_ctx {
   double* vpartials = nullptr;
   double* gemv_part = nullptr;
   double* comb_scratch = nullptr;
+  double* cpart = nullptr;      // column-chunk partials of the panel GEMV
+  unsigned* tile_ctr = nullptr;  // per-row-tile counters of the panel GEMV
   double* P = nullptr;
   float* P32 = nullptr;
   int64_t ldp = 0, ldp32 = 0, rcap = 0;
@@ -154,10 +162,32 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->vpartials);
   dev_free(c->gemv_part);
   dev_free(c->comb_scratch);
+  dev_free(c->cpart);
+  dev_free(c->tile_ctr);
   dev_free(c->P);
   dev_free(c->P32);
   dev_free(c->G);
   dev_free(c->Xdev);
+  dev_free(c->Asplit);
+}
+
+// Arithmetic of the pass over A: float-float on the pre-split copy when it
+// exists, float-float with on-the-fly splitting, or FP64 FMAs (precision = 2 or
+// entries outside the range of the split).
+void set_stream_kind(ssnal_en_ctx* c) {
+  if (!c->ff_ok || c->opt.precision == 2) {
+    c->stream_kind = kStreamDfma;
+    c->A_stream = c->A;
+    c->lda_stream = c->lda;
+  } else if (c->Asplit && c->opt.precision != 3) {
+    c->stream_kind = kStreamSplit;
+    c->A_stream = c->Asplit;
+    c->lda_stream = c->lda_split;
+  } else {
+    c->stream_kind = kStreamFloatFloat;
+    c->A_stream = c->A;
+    c->lda_stream = c->lda;
+  }
 }
 
 bool is_finite_d(double v) { return std::isfinite(v); }
@@ -203,7 +233,7 @@ ssnal_en_status stream_t(ssnal_en_ctx* c, const double* x, ProxParams pp) {
     }
     CK(cudaEventRecord(ev.first, c->stream));
   }
-  launch_stream(kModeT, c->dtype, c->A, c->lda, (int)c->m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
+  launch_stream(kModeT, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
                 o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
   if (c->prof) {
     CK(cudaEventRecord(ev.second, c->stream));
@@ -219,6 +249,16 @@ ssnal_en_status stream_t(ssnal_en_ctx* c, const double* x, ProxParams pp) {
 
 // J, w_J at the current (x, u) (or the support of x in support mode), gather
 // of A_J, and g = y + b - A_J w_J (or y = A_J x_J - b in support mode).
+void launch_grad(ssnal_en_ctx* c, int mode, const double* b, long long r_host) {
+  const int m = (int)c->m;
+  if (mode == kProxSupport)
+    launch_gemv_n(c->P, c->ldp, m, c->wJ, c->st, r_host, c->rcap, c->y, nullptr, 0.0, b, -1.0, 1.0, 0, nullptr,
+                  nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, c->stream);
+  else
+    launch_gemv_n(c->P, c->ldp, m, c->wJ, c->st, r_host, c->rcap, c->g, c->y, 1.0, b, 1.0, -1.0, 1, c->y, b,
+                  nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, c->stream);
+}
+
 ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, const double* b, ProxParams pp,
                                  int apply_update) {
   cudaStream_t s = c->stream;
@@ -227,16 +267,11 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
   launch_prox_scatter(mode, x, c->u, c->n, pp, c->counts + c->grid_vec, c->J, c->wJ, c->grid_vec, s);
   launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, -1, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms,
                 s);
-  launch_gemv_n_partial(c->P, c->ldp, (int)c->m, c->wJ, c->st, -1, c->rcap, c->gemv_part, s);
-  if (mode == kProxSupport)
-    launch_combine(c->y, nullptr, 0.0, b, -1.0, c->gemv_part, 1.0, (int)c->m, 0, nullptr, nullptr, nullptr, c->st,
-                   c->comb_scratch, s);
-  else
-    launch_combine(c->g, c->y, 1.0, b, 1.0, c->gemv_part, -1.0, (int)c->m, 1, c->y, b, nullptr, c->st,
-                   c->comb_scratch, s);
+  launch_grad(c, mode, b, -1);
   CK(cudaGetLastError());
   ssnal_en_status st = read_state(c);
   if (st != SSNAL_EN_OK) return st;
+  if (c->st_host->timeout) return SSNAL_EN_ETIMEOUT;
   if (c->st_host->overflow) {
     // the panel was too small for r: grow it and redo the gather and the GEMV
     int64_t r = c->st_host->r;
@@ -244,61 +279,60 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
     CK(cudaMemsetAsync(&c->st->overflow, 0, sizeof(int32_t), s));
     launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32,
                   c->sms, s);
-    launch_gemv_n_partial(c->P, c->ldp, (int)c->m, c->wJ, c->st, r, c->rcap, c->gemv_part, s);
-    if (mode == kProxSupport)
-      launch_combine(c->y, nullptr, 0.0, b, -1.0, c->gemv_part, 1.0, (int)c->m, 0, nullptr, nullptr, nullptr, c->st,
-                     c->comb_scratch, s);
-    else
-      launch_combine(c->g, c->y, 1.0, b, 1.0, c->gemv_part, -1.0, (int)c->m, 1, c->y, b, nullptr, c->st,
-                     c->comb_scratch, s);
+    launch_grad(c, mode, b, r);
     CK(cudaGetLastError());
     if ((st = read_state(c)) != SSNAL_EN_OK) return st;
   }
   return SSNAL_EN_OK;
 }
 
-// Newton direction d for (I + kappa A_J A_J^T) d = -g on the gathered panel.
-// FP32 factorisation of the Newton matrix, FP64 residuals through the panel
-// (iterative refinement), and the dot products the line search needs.
+// Newton direction d for (I + kappa A_J A_J^T) d = -g on the gathered panel:
+// FP32 SYRK and Cholesky factor of the Newton matrix, FP64 residuals through
+// the panel (iterative refinement), and the dot products the line search needs.
 ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d,
                                  const double* yv, const double* bv, int dots) {
   cudaStream_t s = c->stream;
   const int m = (int)c->m;
-  const int steps = 1 + (c->opt.refine_steps > 0 ? c->opt.refine_steps : 0);
+  const int refine = c->opt.refine_steps > 0 ? c->opt.refine_steps : 0;
+  const int which = dots ? 2 : 0;
   if (r == 0) {
-    launch_combine(d, nullptr, 0.0, g, -1.0, nullptr, 0.0, m, dots ? 2 : 0, yv, bv, g, c->st, c->comb_scratch, s);
+    launch_gemv_n(c->P, c->ldp, m, c->wJ, c->st, 0, c->rcap, d, nullptr, 0.0, g, -1.0, 0.0, which, yv, bv, g, c->st,
+                  c->comb_scratch, c->cpart, c->tile_ctr, s);
   } else if (r < m) {
     // SMW (eq. smw_formula): G = kappa^{-1} I + A_J^T A_J, h = A_J^T g, q = G^{-1} h, d = A_J q - g
+    const int N = (int)r;
     launch_syrk_tn(c->P32, c->ldp32, m, r, 1.0 / kappa, c->G, c->ldg, s);
-    chol_factor(c->G, c->ldg, (int)r, c->st, s);
     launch_gemv_t(c->P, c->ldp, m, r, g, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
-    launch_trsv_llt(c->G, c->ldg, (int)r, c->h, c->q, 1, s);
-    for (int it = 1; it < steps; it++) {
-      // resr = h - kappa^{-1} q - A_J^T (A_J q)
-      launch_gemv_n_partial(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->gemv_part, s);
-      launch_combine(c->tmpm, nullptr, 0.0, nullptr, 0.0, c->gemv_part, 1.0, m, 0, nullptr, nullptr, nullptr, c->st,
-                     c->comb_scratch, s);
-      launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
-      launch_trsv_llt(c->G, c->ldg, (int)r, c->resr, c->q, 0, s);
+    if (N <= kSmallNewton) {
+      launch_chol_solve_small(c->G, c->ldg, N, c->st, c->h, c->q, 1.0, s);
+    } else {
+      chol_factor(c->G, c->ldg, N, c->st, s);
+      launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, s);
     }
-    launch_gemv_n_partial(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->gemv_part, s);
-    launch_combine(d, nullptr, 0.0, g, -1.0, c->gemv_part, 1.0, m, dots ? 2 : 0, yv, bv, g, c->st, c->comb_scratch,
-                   s);
+    for (int it = 0; it < refine; it++) {
+      // resr = h - kappa^{-1} q - A_J^T (A_J q)
+      launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->tmpm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr,
+                    nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
+      launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
+      launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, s);
+    }
+    launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, which, yv, bv, g, c->st,
+                  c->comb_scratch, c->cpart, c->tile_ctr, s);
   } else {
     // m x m form (eq. AJ_system): M = I + kappa A_J A_J^T, d = -M^{-1} g
     launch_syrk_nt(c->P32, c->ldp32, m, r, kappa, c->G, c->ldg, s);
-    chol_factor(c->G, c->ldg, m, c->st, s);
-    // res = -g
-    launch_combine(c->res, nullptr, 0.0, g, -1.0, nullptr, 0.0, m, 0, nullptr, nullptr, nullptr, c->st,
-                   c->comb_scratch, s);
-    launch_trsv_llt(c->G, c->ldg, m, c->res, d, 1, s);
-    for (int it = 1; it < steps; it++) {
-      // res = -g - d - kappa A_J (A_J^T d)
+    if (m <= kSmallNewton) {
+      launch_chol_solve_small(c->G, c->ldg, m, c->st, g, d, -1.0, s);
+    } else {
+      chol_factor(c->G, c->ldg, m, c->st, s);
+      launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, s);
+    }
+    for (int it = 0; it < refine; it++) {
+      // tmpm = -g - d - kappa A_J (A_J^T d)
       launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
-      launch_gemv_n_partial(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->gemv_part, s);
-      launch_combine(c->tmpm, g, -1.0, d, -1.0, c->gemv_part, -kappa, m, 0, nullptr, nullptr, nullptr, c->st,
-                     c->comb_scratch, s);
-      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, s);
+      launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
+                    nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
+      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, s);
     }
     if (dots)
       launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);
@@ -332,7 +366,7 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
   } else {
     if ((e = prox_gather_grad(c, kProxSupport, x, c->bdev, pp, 0)) != SSNAL_EN_OK) return e;
   }
-  launch_stream(kModeU, c->dtype, c->A, c->lda, m, c->n, c->y, c->u, nullptr, nullptr, pp, o.mu, o.beta, o.max_ls,
+  launch_stream(kModeU, c->stream_kind, c->A_stream, c->lda_stream, m, c->n, c->y, c->u, nullptr, nullptr, pp, o.mu, o.beta, o.max_ls,
                 o.ls_fused, c->st, c->partials, c->grid_stream, s);
   CK(cudaGetLastError());
   double sigma = o.sigma0;
@@ -403,6 +437,7 @@ ssnal_en_status check_options(const ssnal_en_options* o) {
   if (o->max_al < 1 || o->max_newton < 0 || o->max_ls < 1 || o->max_ls > kMaxLS) return SSNAL_EN_EINVAL;
   if (o->ls_fused < 1 || o->ls_fused > kFusedLS) return SSNAL_EN_EINVAL;
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->max_active < 0) return SSNAL_EN_EINVAL;
+  if (o->precision < 0 || o->precision > 3) return SSNAL_EN_EINVAL;
   return SSNAL_EN_OK;
 }
 
@@ -503,13 +538,39 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->partials, (size_t)c->grid_stream * kMaxLS);
   AL(c->vpartials, (size_t)c->grid_vec * 6);
   AL(c->gemv_part, (size_t)kGemvGroups * m);
-  AL(c->comb_scratch, 4 * ((m + 255) / 256) + 4);
+  AL(c->comb_scratch, 4 * ((m + 31) / 32) + 4);
+  AL(c->cpart, (size_t)kGemvSplitMax * m);
+  AL(c->tile_ctr, (m + 31) / 32);
   AL(c->G, c->ldg * m);
 #undef AL
   if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) s = SSNAL_EN_ENOMEM;
   if (s == SSNAL_EN_OK) s = grow_panel(c, m < n ? m : n);
   if (s == SSNAL_EN_OK && cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
+  if (s == SSNAL_EN_OK &&
+      cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned) * ((c->m + 31) / 32), c->stream) != cudaSuccess)
+    s = SSNAL_EN_ECUDA;
+  if (s == SSNAL_EN_OK) {
+    // one pass over A: may the stream use the float-float split?
+    launch_check_range((const double*)c->A, c->lda, (int)c->m, c->n, &c->st->overflow, c->sms, c->stream);
+    if (read_state(c) != SSNAL_EN_OK) s = SSNAL_EN_ECUDA;
+    else c->ff_ok = c->st_host->overflow ? 0 : 1;
+  }
+  if (s == SSNAL_EN_OK && cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
   if (s == SSNAL_EN_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
+  if (s == SSNAL_EN_OK && c->ff_ok && c->opt.precision != 3) {
+    // float-pair copy of A read by the stream (same bytes as A); without it the
+    // stream splits each FP64 entry on the fly
+    const int64_t mm = (c->m + 1) & ~1LL;
+    if (cudaMalloc(&c->Asplit, (size_t)mm * (size_t)c->n * sizeof(double)) == cudaSuccess) {
+      c->lda_split = mm;
+      launch_presplit((const double*)c->A, c->lda, (int)c->m, c->n, c->Asplit, c->sms, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
+    } else {
+      cudaGetLastError();
+      c->Asplit = nullptr;
+    }
+  }
+  set_stream_kind(c);
   if (s != SSNAL_EN_OK) {
     free_all(c);
     delete c;
@@ -535,6 +596,7 @@ ssnal_en_status ssnal_en_set_options(ssnal_en_ctx* c, const ssnal_en_options* op
     ssnal_en_default_options(&o);
   if (check_options(&o) != SSNAL_EN_OK) return SSNAL_EN_EINVAL;
   c->opt = o;
+  set_stream_kind(c);
   return SSNAL_EN_OK;
 }
 
@@ -559,7 +621,7 @@ ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, co
   // ||A^T b||_inf from the same stream kernel that later forms u = A^T y
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   ProxParams pp0 = make_pp(c->opt.sigma0, 0.0, 0.0);
-  launch_stream(kModeGmax, c->dtype, c->A, c->lda, m, c->n, b, c->t, nullptr, nullptr, pp0, c->opt.mu, c->opt.beta,
+  launch_stream(kModeGmax, c->stream_kind, c->A_stream, c->lda_stream, m, c->n, b, c->t, nullptr, nullptr, pp0, c->opt.mu, c->opt.beta,
                 c->opt.max_ls, c->opt.ls_fused, c->st, c->partials, c->grid_stream, s);
   CK(cudaGetLastError());
   ssnal_en_status e = read_state(c);
@@ -644,7 +706,7 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* c, int32_t enable, int32_t reset,
 ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* c, const double* y, double* u) {
   if (!c || !y || !u) return SSNAL_EN_EINVAL;
   ProxParams pp = make_pp(1.0, 0.0, 0.0);
-  launch_stream(kModeU, c->dtype, c->A, c->lda, (int)c->m, c->n, y, u, nullptr, nullptr, pp, 0.2, 0.5, 1, 1, c->st,
+  launch_stream(kModeU, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, y, u, nullptr, nullptr, pp, 0.2, 0.5, 1, 1, c->st,
                 c->partials, c->grid_stream, c->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
@@ -677,8 +739,8 @@ ssnal_en_status ssnal_en_op_grad(ssnal_en_ctx* c, const int32_t* J, const double
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   const int m = (int)c->m;
   launch_gather(c->A, c->dtype, c->lda, m, J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms, s);
-  launch_gemv_n_partial(c->P, c->ldp, m, wJ, c->st, r, c->rcap, c->gemv_part, s);
-  launch_combine(g, y, 1.0, b, 1.0, c->gemv_part, -1.0, m, 0, nullptr, nullptr, nullptr, c->st, c->comb_scratch, s);
+  launch_gemv_n(c->P, c->ldp, m, wJ, c->st, r, c->rcap, g, y, 1.0, b, 1.0, -1.0, 0, nullptr, nullptr, nullptr, c->st,
+                c->comb_scratch, c->cpart, c->tile_ctr, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
   return SSNAL_EN_OK;

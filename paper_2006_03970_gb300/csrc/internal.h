@@ -22,8 +22,11 @@ constexpr int kNumCounters = 16;  // last-block-done counters
 
 // Counter slots (one per kernel that uses the last-block pattern).
 enum CounterSlot {
-  kCtrProx = 0, kCtrCombine = 1, kCtrStream = 2, kCtrFallback = 3, kCtrGmax = 4, kCtrMisc = 5
+  kCtrProx = 0, kCtrCombine = 1, kCtrStream = 2, kCtrFallback = 3, kCtrGmax = 4, kCtrMisc = 5,
+  kCtrBarrier = 6,  // two words: arrival count and generation of the cooperative grid barrier
+  kCtrGemv = 8
 };
+constexpr int kSmallNewton = 128;  // Newton systems up to this size are factored by one CTA
 
 // Values computed on the device and read by the host once per Newton step.
 // The host never writes these except through cudaMemsetAsync of the whole struct.
@@ -50,12 +53,17 @@ struct DevState {
   // flags
   int32_t overflow;   // panel capacity exceeded by r
   int32_t chol_fail;  // non-positive pivot in the Cholesky factorisation
+  int32_t timeout;    // a bounded device-side wait gave up
   double gmax;        // ||A^T b||_inf (path)
   unsigned int counters[kNumCounters];
 };
 
 // Element access for the supported storage types.
 enum StreamMode { kModeU = 0, kModeT = 1, kModeGmax = 2 };
+// Stream arithmetic selector passed as `dtype` to launch_stream for FP64 storage.
+constexpr int kStreamDfma = 0;         // FP64 FMA per element
+constexpr int kStreamFloatFloat = 16;  // float-float on the FP32 pipe (entries 0 or in [2^-100, 2^100])
+constexpr int kStreamSplit = 17;       // same arithmetic on a pre-split float-pair copy of A (packed f32x2)
 enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
 
 struct ProxParams {
@@ -79,6 +87,14 @@ void launch_gemv_n_partial(const double* P, long long ldp, int m, const double* 
 void launch_combine(double* out, const double* a, double ca, const double* b, double cb, const double* part,
                     double cs, int m, int which, const double* y, const double* bb, const double* g,
                     DevState* st, double* scratch, cudaStream_t s);
+// out_i = ca*a_i + cb*b_i + cs*sum_k P[i,k] coef[k] in one launch, with the scalar products
+// of k_combine (which = 1: gradient, 2: direction); r read from st when r_host < 0.
+// cpart: kGemvSplitMax x m doubles; tile_ctr: ceil(m / 32) zeroed counters.
+constexpr int kGemvSplitMax = 32;
+void launch_gemv_n(const double* P, long long ldp, int m, const double* coef, const DevState* st, long long r_host,
+                   long long rcap, double* out, const double* a, double ca, const double* b, double cb, double cs,
+                   int which, const double* yv, const double* bv, const double* gv, DevState* stw, double* scratch,
+                   double* cpart, unsigned* tile_ctr, cudaStream_t s);
 // out_k = ch*h_k + cq*q_k + cd*dot(P[:,k], v)
 void launch_gemv_t(const double* P, long long ldp, int m, long long r, const double* v, double* out,
                    const double* h, double ch, const double* q, double cq, double cd, int sms, cudaStream_t s);
@@ -90,9 +106,12 @@ void launch_syrk_tn(const float* P32, long long ldp32, int m, long long r, doubl
 void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, double kappa, float* G, long long ldg,
                     cudaStream_t s);
 void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s);
-// acc = (first ? c : acc + c) with (L L^T) c = rhs
+// N <= kSmallNewton: factor and solve one right-hand side in one launch (acc = c)
+void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
+                             double alpha, cudaStream_t s);
+// acc = (first ? alpha c : acc + alpha c) with (L L^T) c = rhs
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
-                     cudaStream_t s);
+                     double alpha, cudaStream_t s);
 
 // ---- streams over A (kern_stream.cu)
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,
@@ -102,5 +121,7 @@ void launch_ls_fallback(const double* x, const double* u, const double* t, long 
                         double beta, int max_ls, int fused, DevState* st, double* partials, int grid,
                         cudaStream_t s);
 int stream_grid(int sms);
+void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s);
+void launch_check_range(const double* A, long long lda, int m, long long n, int* bad, int sms, cudaStream_t s);
 
 }  // namespace ssnal

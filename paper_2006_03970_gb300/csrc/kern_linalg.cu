@@ -4,6 +4,7 @@
 //   * blocked right-looking Cholesky factorisation (textbook algorithm, FP32);
 //   * forward/backward substitution with the factor, accumulating the
 //     correction into an FP64 vector (the solve of an iterative refinement).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(256) k_syrk_update(float* __restrict__ G, long
 constexpr int kTrsvThreads = 1024;
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv_llt(const float* __restrict__ L, long long ld, int N,
                                                            const double* __restrict__ rhs, double* __restrict__ acc,
-                                                           int first) {
+                                                           int first, double alpha) {
   extern __shared__ float z[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
@@ -221,7 +222,544 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_llt(const float* __restri
     }
     __syncthreads();
   }
-  for (int i = tid; i < N; i += blockDim.x) acc[i] = first ? (double)z[i] : acc[i] + (double)z[i];
+  for (int i = tid; i < N; i += blockDim.x)
+    acc[i] = first ? alpha * (double)z[i] : acc[i] + alpha * (double)z[i];
+}
+
+// ---------------------------------------------------------------------------
+// Small Newton systems (N <= kSmallN): one CTA factors the matrix in shared
+// memory (right-looking, column by column) and optionally solves one right-hand
+// side in the same launch.
+constexpr int kSmallN = 128;
+constexpr int kSmallThreads = 1024;
+
+__device__ void smem_forward_backward(const float* __restrict__ Ls, int ldl, int N, float* z) {
+  // L z' = z then L^T c = z' with L in shared memory (lower, column-major, ld ldl).
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int jb = 0; jb < N; jb += kT) {
+    const int nb = min(kT, N - jb);
+    if (warp == 0) {
+      float zl = lane < nb ? z[jb + lane] : 0.0f;
+      for (int j = 0; j < nb; j++) {
+        const float zj = __shfl_sync(0xffffffffu, zl / Ls[(jb + j) + (jb + j) * ldl], j);
+        if (lane == j) zl = zj;
+        if (lane > j && lane < nb) zl = fmaf(-Ls[(jb + lane) + (jb + j) * ldl], zj, zl);
+      }
+      if (lane < nb) z[jb + lane] = zl;
+    }
+    __syncthreads();
+    for (int i = jb + nb + tid; i < N; i += blockDim.x) {
+      float acc = z[i];
+      for (int j = 0; j < nb; j++) acc = fmaf(-Ls[i + (jb + j) * ldl], z[jb + j], acc);
+      z[i] = acc;
+    }
+    __syncthreads();
+  }
+  const int last = ((N - 1) / kT) * kT;
+  for (int jb = last; jb >= 0; jb -= kT) {
+    const int nb = min(kT, N - jb);
+    if (warp == 0) {
+      float zl = lane < nb ? z[jb + lane] : 0.0f;
+      for (int j = nb - 1; j >= 0; j--) {
+        const float zj = __shfl_sync(0xffffffffu, zl / Ls[(jb + j) + (jb + j) * ldl], j);
+        if (lane == j) zl = zj;
+        if (lane < j) zl = fmaf(-Ls[(jb + j) + (jb + lane) * ldl], zj, zl);
+      }
+      if (lane < nb) z[jb + lane] = zl;
+    }
+    __syncthreads();
+    for (int i = tid; i < jb; i += blockDim.x) {
+      float acc = z[i];
+      for (int j = 0; j < nb; j++) acc = fmaf(-Ls[(jb + j) + i * ldl], z[jb + j], acc);
+      z[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Factor G (N <= kSmallN) in place in shared memory, write L back to G, and if
+// rhs != nullptr solve (L L^T) c = rhs and store acc = c (FP64).
+constexpr size_t kSmallSmem = (size_t)(kSmallN * (kSmallN + 1) + kSmallN) * sizeof(float);
+
+__global__ void __launch_bounds__(kSmallThreads) k_chol_small(float* __restrict__ G, long long ld, int N,
+                                                              DevState* st, const double* __restrict__ rhs,
+                                                              double* __restrict__ acc, double alpha) {
+  extern __shared__ float sm_small[];
+  float* Ls = sm_small;
+  float* z = sm_small + kSmallN * (kSmallN + 1);
+  const int ldl = kSmallN + 1;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < N * N; e += blockDim.x) {
+    const int i = e % N, j = e / N;
+    Ls[i + j * ldl] = (i >= j) ? G[i + (long long)j * ld] : 0.0f;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; k++) {
+    if (tid == 0) {
+      float piv = Ls[k + k * ldl];
+      if (!(piv > 0.0f)) {
+        st->chol_fail = 1;
+        piv = 1.0f;
+      }
+      Ls[k + k * ldl] = sqrtf(piv);
+    }
+    __syncthreads();
+    const float dkk = Ls[k + k * ldl];
+    for (int i = k + 1 + tid; i < N; i += blockDim.x) Ls[i + k * ldl] /= dkk;
+    __syncthreads();
+    // trailing update of the lower part: (i, j) with k < j <= i < N
+    const int rem = N - k - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = k + 1 + e % rem, j = k + 1 + e / rem;
+      if (i >= j) Ls[i + j * ldl] = fmaf(-Ls[i + k * ldl], Ls[j + k * ldl], Ls[i + j * ldl]);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < N * N; e += blockDim.x) {
+    const int i = e % N, j = e / N;
+    if (i >= j) G[i + (long long)j * ld] = Ls[i + j * ldl];
+  }
+  if (!rhs) return;
+  for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
+  __syncthreads();
+  smem_forward_backward(Ls, ldl, N, z);
+  for (int i = tid; i < N; i += blockDim.x) acc[i] = alpha * (double)z[i];
+}
+
+// (L L^T) c = rhs with L (N <= kSmallN) staged into shared memory; acc = c or acc + c.
+__global__ void __launch_bounds__(kSmallThreads) k_trsv_small(const float* __restrict__ L, long long ld, int N,
+                                                              const double* __restrict__ rhs,
+                                                              double* __restrict__ acc, int first, double alpha) {
+  extern __shared__ float sm_small[];
+  float* Ls = sm_small;
+  float* z = sm_small + kSmallN * (kSmallN + 1);
+  const int ldl = kSmallN + 1;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < N * N; e += blockDim.x) {
+    const int i = e % N, j = e / N;
+    Ls[i + j * ldl] = (i >= j) ? L[i + (long long)j * ld] : 0.0f;
+  }
+  for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
+  __syncthreads();
+  smem_forward_backward(Ls, ldl, N, z);
+  for (int i = tid; i < N; i += blockDim.x)
+    acc[i] = first ? alpha * (double)z[i] : acc[i] + alpha * (double)z[i];
+}
+
+// ---------------------------------------------------------------------------
+// Medium systems (kSmallN < N <= kMidN): forward and backward substitution in
+// one CTA, block by block (32 rows/columns), with the next block of L copied
+// into a second shared-memory buffer (cp.async) while the current block is
+// solved, so that L2 latency stays off the critical path.
+constexpr int kMidN = 768;
+constexpr int kMidThreads = 1024;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Row block I of L (rows [32I, 32I+32) x columns [0, 32I + 32)) -> buf, column j at buf + 32 j.
+__device__ __forceinline__ void prefetch_rows(const float* L, long long ld, int N, int I, float* buf) {
+  const int r0 = 32 * I;
+  const int ncols = min(r0 + 32, N);
+  for (int e = threadIdx.x; e < ncols * 8; e += blockDim.x) {
+    const int j = e >> 3, ch = e & 7;
+    const int row = r0 + 4 * ch;
+    const int valid = row < N ? min(4, N - row) : 0;
+    const float* src = L + (long long)j * ld + (valid > 0 ? row : 0);
+    cp_async16(buf + 32 * j + 4 * ch, src, valid * 4);
+  }
+}
+
+// Column block I of L (columns [32I, 32I+32) x rows [32I, N)) -> buf, column c at buf + c ldb.
+__device__ __forceinline__ void prefetch_cols(const float* L, long long ld, int N, int I, float* buf, int ldb) {
+  const int r0 = 32 * I;
+  const int nc = min(32, N - r0);
+  const int chunks = ldb / 4;
+  for (int e = threadIdx.x; e < nc * chunks; e += blockDim.x) {
+    const int c = e / chunks, ch = e % chunks;
+    const int row = r0 + 4 * ch;
+    const int valid = row < N ? min(4, N - row) : 0;
+    const float* src = L + (long long)(r0 + c) * ld + (valid > 0 ? row : r0);
+    cp_async16(buf + c * ldb + 4 * ch, src, valid * 4);
+  }
+}
+
+__global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restrict__ L, long long ld, int N,
+                                                          const double* __restrict__ rhs, double* __restrict__ acc,
+                                                          int first, double alpha) {
+  extern __shared__ __align__(16) float sm_mid[];
+  const int ldb = (N + 3) & ~3;
+  float* buf[2] = {sm_mid, sm_mid + 32 * ldb};
+  float* z = sm_mid + 64 * ldb;
+  float* red = z + ldb;  // 32 x 33
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = (N + 31) / 32;
+  for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
+  // ---- forward: z_I = L_II^{-1} (z_I - L[I, 0:I] z[0:I])
+  prefetch_rows(L, ld, N, 0, buf[0]);
+  cp_async_commit();
+  for (int I = 0; I < T; I++) {
+    if (I + 1 < T) prefetch_rows(L, ld, N, I + 1, buf[(I + 1) & 1]);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const float* B = buf[I & 1];
+    const int r0 = 32 * I, nb = min(32, N - r0);
+    float a = 0.0f;
+    for (int j = warp; j < r0; j += 32) a = fmaf(B[32 * j + lane], z[j], a);
+    red[warp * 33 + lane] = a;
+    __syncthreads();
+    if (warp == 0) {
+      float sum = 0.0f;
+      for (int w = 0; w < 32; w++) sum += red[w * 33 + lane];
+      float zl = lane < nb ? z[r0 + lane] - sum : 0.0f;
+      const float rinv = lane < nb ? 1.0f / B[32 * (r0 + lane) + lane] : 0.0f;
+      for (int j = 0; j < nb; j++) {
+        const float zj = __shfl_sync(0xffffffffu, zl * rinv, j);
+        if (lane == j) zl = zj;
+        if (lane > j && lane < nb) zl = fmaf(-B[32 * (r0 + j) + lane], zj, zl);
+      }
+      if (lane < nb) z[r0 + lane] = zl;
+    }
+    __syncthreads();
+  }
+  cp_async_wait0();
+  __syncthreads();
+  // ---- backward: c_I = L_II^{-T} (z_I - L[>I, I]^T c[>I])
+  prefetch_cols(L, ld, N, T - 1, buf[(T - 1) & 1], ldb);
+  cp_async_commit();
+  for (int I = T - 1; I >= 0; I--) {
+    if (I > 0) prefetch_cols(L, ld, N, I - 1, buf[(I - 1) & 1], ldb);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const float* B = buf[I & 1];
+    const int r0 = 32 * I, nb = min(32, N - r0);
+    // column c of the block sits at B + c*ldb, row i at offset i - r0
+    float a = 0.0f;
+    if (lane < nb)
+      for (int i = r0 + 32 + warp; i < N; i += 32) a = fmaf(B[lane * ldb + (i - r0)], z[i], a);
+    red[warp * 33 + lane] = a;
+    __syncthreads();
+    if (warp == 0) {
+      float sum = 0.0f;
+      for (int w = 0; w < 32; w++) sum += red[w * 33 + lane];
+      float zl = lane < nb ? z[r0 + lane] - sum : 0.0f;
+      const float rinv = lane < nb ? 1.0f / B[lane * ldb + lane] : 0.0f;
+      for (int j = nb - 1; j >= 0; j--) {
+        const float zj = __shfl_sync(0xffffffffu, zl * rinv, j);
+        if (lane == j) zl = zj;
+        if (lane < j) zl = fmaf(-B[lane * ldb + j], zj, zl);
+      }
+      if (lane < nb) z[r0 + lane] = zl;
+    }
+    __syncthreads();
+  }
+  cp_async_wait0();
+  for (int i = tid; i < N; i += blockDim.x)
+    acc[i] = first ? alpha * (double)z[i] : acc[i] + alpha * (double)z[i];
+}
+
+// ---------------------------------------------------------------------------
+// Cluster tile Cholesky (kSmallN < N <= kClusterN).  The lower triangle is cut
+// into 32x32 tiles; tile (i, j), i >= j, with linear index i(i+1)/2 + j lives in
+// the shared memory of CTA (index mod kClusterCTAs) of one thread-block cluster.
+// Step k: the owner of (k, k) factors it and inverts the factor; after a
+// cluster barrier the owners of the panel tiles (i, k) form L_ik = A_ik L_kk^{-T};
+// after a second barrier every CTA copies the panel column through distributed
+// shared memory and updates its own trailing tiles A_ij -= L_ik L_jk^T; a third
+// barrier closes the step.  Rows and columns beyond N are padded with the
+// identity, so the factor of the padded matrix is L plus an identity block.
+namespace cgx = cooperative_groups;
+constexpr int kClusterCTAs = 8;
+constexpr int kClusterN = 640;
+constexpr int kClusterT = kClusterN / 32;                                   // 20 tiles per side
+constexpr int kTileF = 32 * 33;                                              // floats per padded tile
+constexpr int kClusterSlots = (kClusterT * (kClusterT + 1) / 2 + kClusterCTAs - 1) / kClusterCTAs;  // 27
+constexpr size_t kClusterSmem = (size_t)(kClusterSlots + kClusterT + 2) * kTileF * sizeof(float);
+
+__device__ __forceinline__ int tri_index(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
+    k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st) {
+  cgx::cluster_group cluster = cgx::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ float csm[];
+  float* own = csm;                                  // kClusterSlots tiles
+  float* panel = csm + kClusterSlots * kTileF;       // copy of panel column k (kClusterT tiles)
+  float* winv = panel + kClusterT * kTileF;          // inverse of L_kk (owner of (k, k))
+  float* tmp = winv + kTileF;                        // scratch tile
+  const int tid = threadIdx.x;
+  const int T = (N + 31) / 32;
+  const int r4 = tid >> 3, c4 = (tid & 7) * 4;       // 4 elements per thread: row r4, columns c4..c4+3
+
+  // ---- load the owned tiles (identity padding beyond N)
+  for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
+    int ti, tj;
+    tri_tile(t, ti, tj);
+    float* dst = own + (t / kClusterCTAs) * kTileF;
+    for (int e = tid; e < 1024; e += 256) {
+      const int r = e >> 5, c = e & 31;
+      const int gi = ti * 32 + r, gj = tj * 32 + c;
+      float v;
+      if (gi < N && gj < N)
+        v = (gi >= gj) ? G[gi + (long long)gj * ld] : 0.0f;
+      else
+        v = (gi == gj) ? 1.0f : 0.0f;
+      dst[r * 33 + c] = v;
+    }
+  }
+  cluster.sync();
+  for (int k = 0; k < T; k++) {
+    const int dkk = tri_index(k, k);
+    // ---- (a) factor the diagonal tile and invert its factor
+    if (dkk % kClusterCTAs == rank) {
+      float* D = own + (dkk / kClusterCTAs) * kTileF;
+      for (int q = 0; q < 32; q++) {
+        if (tid == 0) {
+          float piv = D[q * 33 + q];
+          if (!(piv > 0.0f)) {
+            st->chol_fail = 1;
+            piv = 1.0f;
+          }
+          D[q * 33 + q] = sqrtf(piv);
+        }
+        __syncthreads();
+        if (tid > q && tid < 32) D[tid * 33 + q] /= D[q * 33 + q];
+        __syncthreads();
+        for (int e = tid; e < 1024; e += 256) {
+          const int r = e >> 5, c = e & 31;
+          if (c > q && r >= c) D[r * 33 + c] = fmaf(-D[r * 33 + q], D[c * 33 + q], D[r * 33 + c]);
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < 1024; e += 256) {  // clear the strict upper part
+        const int r = e >> 5, c = e & 31;
+        if (c > r) D[r * 33 + c] = 0.0f;
+      }
+      __syncthreads();
+      if (tid < 32) {  // column tid of W = L_kk^{-1} by forward substitution
+        const int j = tid;
+        for (int i = 0; i < 32; i++) winv[i * 33 + j] = 0.0f;
+        winv[j * 33 + j] = 1.0f / D[j * 33 + j];
+        for (int i = j + 1; i < 32; i++) {
+          float acc = 0.0f;
+          for (int t = j; t < i; t++) acc = fmaf(D[i * 33 + t], winv[t * 33 + j], acc);
+          winv[i * 33 + j] = -acc / D[i * 33 + i];
+        }
+      }
+    }
+    cluster.sync();
+    // ---- (b) panel tiles L_ik = A_ik W^T
+    {
+      const float* W = cluster.map_shared_rank(winv, dkk % kClusterCTAs);
+      bool have_w = false;
+      for (int i = k + 1; i < T; i++) {
+        const int t = tri_index(i, k);
+        if (t % kClusterCTAs != rank) continue;
+        if (!have_w) {
+          for (int e = tid; e < kTileF; e += 256) tmp[e] = W[e];
+          __syncthreads();
+          have_w = true;
+        }
+        float* Ai = own + (t / kClusterCTAs) * kTileF;
+        float acc[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 32; q++) {
+          const float a = Ai[r4 * 33 + q];
+#pragma unroll
+          for (int e = 0; e < 4; e++) acc[e] = fmaf(a, tmp[(c4 + e) * 33 + q], acc[e]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 4; e++) Ai[r4 * 33 + c4 + e] = acc[e];
+        __syncthreads();
+      }
+    }
+    cluster.sync();
+    // ---- (c) trailing update of the owned tiles (i, j), k < j <= i
+    {
+      // copy panel column k (tiles i = k+1 .. T-1) into local shared memory
+      for (int i = k + 1; i < T; i++) {
+        const int t = tri_index(i, k);
+        const float* src = cluster.map_shared_rank(own + (t / kClusterCTAs) * kTileF, t % kClusterCTAs);
+        float* dst = panel + i * kTileF;
+        for (int e = tid; e < kTileF; e += 256) dst[e] = src[e];
+      }
+      __syncthreads();
+      for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
+        int ti, tj;
+        tri_tile(t, ti, tj);
+        if (tj <= k) continue;
+        float* C = own + (t / kClusterCTAs) * kTileF;
+        const float* Li = panel + ti * kTileF;
+        const float* Lj = panel + tj * kTileF;
+        float acc[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 32; q++) {
+          const float a = Li[r4 * 33 + q];
+#pragma unroll
+          for (int e = 0; e < 4; e++) acc[e] = fmaf(a, Lj[(c4 + e) * 33 + q], acc[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; e++) C[r4 * 33 + c4 + e] -= acc[e];
+      }
+    }
+    cluster.sync();
+  }
+  // ---- write the factor back (lower part, inside N)
+  for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
+    int ti, tj;
+    tri_tile(t, ti, tj);
+    const float* src = own + (t / kClusterCTAs) * kTileF;
+    for (int e = tid; e < 1024; e += 256) {
+      const int r = e >> 5, c = e & 31;
+      const int gi = ti * 32 + r, gj = tj * 32 + c;
+      if (gi < N && gj < N && gi >= gj) G[gi + (long long)gj * ld] = src[r * 33 + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Larger Newton systems: blocked right-looking Cholesky in ONE cooperative
+// launch.  Phases (diagonal block, panel, trailing update) are separated by a
+// grid barrier with a bounded wait; all CTAs are co-resident (cooperative
+// launch), so the barrier cannot deadlock, and a timeout raises
+// DevState::timeout instead of hanging.
+constexpr int kCoopThreads = 256;
+
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, DevState* st) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      *bar = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > 4000000000LL) {
+          ok = 0;
+          st->timeout = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(kCoopThreads) k_chol_coop(float* __restrict__ G, long long ld, int N,
+                                                            DevState* st, unsigned* bar) {
+  __shared__ float Ld[kT][kT + 1];
+  __shared__ float As[kT][kT + 1];
+  __shared__ float Bs[kT][kT + 1];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const unsigned nblk = gridDim.x;
+  for (int kb = 0; kb < N; kb += kT) {
+    const int nb = min(kT, N - kb);
+    // (1) diagonal block, CTA 0
+    if (blockIdx.x == 0) {
+      for (int e = tid; e < kT * kT; e += blockDim.x) {
+        const int i = e % kT, j = e / kT;
+        Ld[i][j] = (i < nb && j < nb && j <= i) ? G[(kb + i) + (long long)(kb + j) * ld] : 0.0f;
+      }
+      __syncthreads();
+      for (int k = 0; k < nb; k++) {
+        if (tid == 0) {
+          float piv = Ld[k][k];
+          if (!(piv > 0.0f)) {
+            st->chol_fail = 1;
+            piv = 1.0f;
+          }
+          Ld[k][k] = sqrtf(piv);
+        }
+        __syncthreads();
+        if (tid > k && tid < nb) Ld[tid][k] /= Ld[k][k];
+        __syncthreads();
+        for (int e = tid; e < kT * kT; e += blockDim.x) {
+          const int i = e % kT, j = e / kT;
+          if (j > k && i >= j && i < nb) Ld[i][j] = fmaf(-Ld[i][k], Ld[j][k], Ld[i][j]);
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < kT * kT; e += blockDim.x) {
+        const int i = e % kT, j = e / kT;
+        if (i < nb && j < nb && j <= i) G[(kb + i) + (long long)(kb + j) * ld] = Ld[i][j];
+      }
+    }
+    if (!grid_barrier(bar, nblk, st)) return;
+    const int k1 = kb + nb;
+    const int rem = N - k1;
+    if (rem <= 0) break;
+    // (2) panel L21 = A21 L11^{-T}, one row per thread across the grid
+    for (int e = tid; e < kT * kT; e += blockDim.x) {
+      const int i = e % kT, j = e / kT;
+      Ld[i][j] = (i < nb && j < nb && j <= i) ? G[(kb + i) + (long long)(kb + j) * ld] : 0.0f;
+    }
+    __syncthreads();
+    for (int row = k1 + blockIdx.x * blockDim.x + tid; row < N; row += gridDim.x * blockDim.x) {
+      float xv[kT];
+#pragma unroll
+      for (int j = 0; j < kT; j++) {
+        if (j < nb) {
+          float sacc = G[row + (long long)(kb + j) * ld];
+#pragma unroll
+          for (int k = 0; k < kT; k++)
+            if (k < j) sacc = fmaf(-xv[k], Ld[j][k], sacc);
+          xv[j] = sacc / Ld[j][j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kT; j++)
+        if (j < nb) G[row + (long long)(kb + j) * ld] = xv[j];
+    }
+    if (!grid_barrier(bar, nblk, st)) return;
+    // (3) trailing update on lower tiles of [k1, N)
+    const int T = (rem + kT - 1) / kT;
+    const int ntiles = T * (T + 1) / 2;
+    for (int id = blockIdx.x; id < ntiles; id += gridDim.x) {
+      int ti, tj;
+      tri_tile(id, ti, tj);
+      const int i0 = k1 + ti * kT, j0 = k1 + tj * kT;
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int k = ty + 8 * e;
+        As[k][tx] = (k < nb && i0 + tx < N) ? G[(i0 + tx) + (long long)(kb + k) * ld] : 0.0f;
+        Bs[k][tx] = (k < nb && j0 + tx < N) ? G[(j0 + tx) + (long long)(kb + k) * ld] : 0.0f;
+      }
+      __syncthreads();
+      float a4[4] = {0, 0, 0, 0};
+#pragma unroll 8
+      for (int k = 0; k < kT; k++) {
+        const float bv = Bs[k][tx];
+#pragma unroll
+        for (int e = 0; e < 4; e++) a4[e] = fmaf(As[k][ty + 8 * e], bv, a4[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int i = i0 + ty + 8 * e, j = j0 + tx;
+        if (i < N && j < N && i >= j) {
+          float* p = G + i + (long long)j * ld;
+          *p = *p - a4[e];
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, nblk, st)) return;
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -241,7 +779,53 @@ void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, doubl
   if (blocks > 0) k_syrk_nt<<<blocks, 256, 0, s>>>(P32, ldp32, m, r, (float)kappa, G, ldg);
 }
 
+static void small_smem_attr() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && done[dev]) return;
+  cudaFuncSetAttribute(k_chol_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
+  cudaFuncSetAttribute(k_trsv_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
+  if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
 void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
+  if (N <= kSmallN) {
+    small_smem_attr();
+    count_launch();
+    k_chol_small<<<1, kSmallThreads, kSmallSmem, s>>>(G, ldg, N, st, nullptr, nullptr, 1.0);
+    return;
+  }
+  if (N <= kClusterN) {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmem);
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    count_launch();
+    k_chol_cluster<<<kClusterCTAs, 256, kClusterSmem, s>>>(G, ldg, N, st);
+    if (cudaGetLastError() == cudaSuccess) return;
+  }
+  {
+    // one cooperative launch; the grid barrier counters live in DevState
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, kCoopThreads, 0);
+    int grid = sms * (per_sm > 0 ? 1 : 0);
+    const int T = (N + kT - 1) / kT;
+    if (grid > T * (T + 1) / 2) grid = T * (T + 1) / 2;
+    if (grid > 64) grid = 64;
+    if (grid >= 1) {
+      unsigned* bar = &st->counters[kCtrBarrier];
+      void* args[] = {&G, &ldg, &N, &st, &bar};
+      count_launch();
+      if (cudaLaunchCooperativeKernel((void*)k_chol_coop, grid, kCoopThreads, args, 0, s) == cudaSuccess) return;
+      cudaGetLastError();
+    }
+  }
   for (int kb = 0; kb < N; kb += kCholNB) {
     const int nb = N - kb < kCholNB ? N - kb : kCholNB;
     count_launch();
@@ -256,11 +840,40 @@ void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
   }
 }
 
-void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
-                     cudaStream_t s) {
-  if (N <= 0) return;
+void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
+                             double alpha, cudaStream_t s) {
+  small_smem_attr();
   count_launch();
-  k_trsv_llt<<<1, kTrsvThreads, (size_t)N * sizeof(float), s>>>(L, ldl, N, rhs, acc, first);
+  k_chol_small<<<1, kSmallThreads, kSmallSmem, s>>>(G, ldg, N, st, rhs, acc, alpha);
+}
+
+void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
+                     double alpha, cudaStream_t s) {
+  if (N <= 0) return;
+  if (N <= kSmallN) {
+    small_smem_attr();
+    count_launch();
+    k_trsv_small<<<1, kSmallThreads, kSmallSmem, s>>>(L, ldl, N, rhs, acc, first, alpha);
+    return;
+  }
+  if (N <= kMidN) {
+    const int ldb = (N + 3) & ~3;
+    const size_t smem = (size_t)(64 * ldb + ldb + 32 * 33) * sizeof(float);
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done[dev]) {
+      const int lb = (kMidN + 3) & ~3;
+      cudaFuncSetAttribute(k_trsv_mid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((64 * lb + lb + 32 * 33) * sizeof(float)));
+      if (dev >= 0 && dev < 64) done[dev] = true;
+    }
+    count_launch();
+    k_trsv_mid<<<1, kMidThreads, smem, s>>>(L, ldl, N, rhs, acc, first, alpha);
+    return;
+  }
+  count_launch();
+  k_trsv_llt<<<1, kTrsvThreads, (size_t)N * sizeof(float), s>>>(L, ldl, N, rhs, acc, first, alpha);
 }
 
 }  // namespace ssnal

@@ -192,20 +192,545 @@ __global__ void __launch_bounds__(256) k_ls_fallback(const double* __restrict__ 
   reset_counter(&st->counters[kCtrFallback]);
 }
 
+
+// ---------------------------------------------------------------------------
+// Float-float stream: FP64-stored A, dot products evaluated on the FP32 pipe.
+//
+// GB300 retires about 2 FP64 FMAs per clock per SM, too few for one FMA per
+// 8-byte element at HBM speed.  Each FP64 entry a is split exactly into
+// a_hi + a_lo (24 + 23 significant bits, integer bit operations only), the
+// vector entry d into a float-float pair, and each product a*d is formed as a
+// float-float (error-free product via FMA plus the cross terms) and added into
+// a float-float accumulator with Knuth's TwoSum.  The result is accurate to
+// about 2^-47 relative per product, the same order as FP64 accumulation.
+//
+// Staging: a persistent CTA per SM; one producer warp moves tiles of whole
+// columns (row chunks for tall columns) into a 4-stage shared-memory ring with
+// cp.async.bulk, completing on mbarriers; 8 consumer warps each own whole
+// columns of a tile.  Per-column epilogues are batched 32 columns at a time so
+// that the FP64 work (v = x - sigma u, trial sums) runs with full warps.
+// Every mbarrier wait is bounded; a timeout raises DevState::timeout.
+// ---------------------------------------------------------------------------
+constexpr int kFFConsumers = 8;
+constexpr int kFFThreads = (kFFConsumers + 1) * 32;
+constexpr int kFFStages = 4;
+constexpr int kFFStageBytes = 40 * 1024;
+constexpr unsigned kSpinLimit = 1u << 28;          // try_wait rounds
+constexpr long long kWaitCycles = 4000000000LL;    // about 2 s of SM clock
+
+struct FFCfg {
+  int cpw;          // columns per consumer warp in a tile
+  int tc;           // columns per tile (kFFConsumers * cpw)
+  int rows;         // rows per chunk (even)
+  int nchunks;      // chunks per tile
+  int mm;           // m rounded up to even: rows actually streamed
+  long long ntiles;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Bounded wait for the phase with the given parity; false after about two
+// seconds (or kSpinLimit rounds), so a protocol error cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (unsigned it = 0; it < kSpinLimit; it++) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) break;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Exact split of an FP64 value (0 or |a| in [2^-100, 2^100]) into float hi + lo
+// with 24 + 23 significant bits, using integer operations only.
+__device__ __forceinline__ void split_f64(unsigned long long bits, float& hi, float& lo) {
+  const unsigned H = (unsigned)(bits >> 32), L = (unsigned)bits;
+  const unsigned sign = H & 0x80000000u;
+  const unsigned habs = H & 0x7FFFFFFFu;
+  const unsigned e = habs - (896u << 20);                 // exponent bias 1023 -> 127
+  const unsigned hib = __funnelshift_l(L, e, 3) | sign;  // sign | exp | top 23 mantissa bits
+  const unsigned ebits = (hib & 0x7F800000u) - (23u << 23);
+  const unsigned fbits = ebits | ((L >> 6) & 0x7FFFFFu) | sign;
+  const unsigned mbits = ebits | sign;
+  const bool zero = habs < (1u << 20);
+  hi = zero ? 0.0f : __uint_as_float(hib);
+  lo = zero ? 0.0f : __fsub_rn(__uint_as_float(fbits), __uint_as_float(mbits));
+}
+
+// (S, L) += (ah + al) * (dh + dl) in float-float.
+__device__ __forceinline__ void ff_madd(float& S, float& L, float ah, float al, float dh, float dl) {
+  const float p = __fmul_rn(ah, dh);
+  float e = __fmaf_rn(ah, dh, -p);
+  e = __fmaf_rn(ah, dl, e);
+  e = __fmaf_rn(al, dh, e);
+  const float s = __fadd_rn(S, p);
+  const float z = __fsub_rn(s, S);
+  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, z)), __fsub_rn(p, z));
+  S = s;
+  L = __fadd_rn(L, __fadd_rn(t, e));
+}
+
+// (S, L) += (S2, L2)
+__device__ __forceinline__ void ff_merge(float& S, float& L, float S2, float L2) {
+  const float s = __fadd_rn(S, S2);
+  const float z = __fsub_rn(s, S);
+  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, z)), __fsub_rn(S2, z));
+  S = s;
+  L = __fadd_rn(__fadd_rn(L, L2), t);
+}
+
+// Packed (f32x2) float-float step on an element pair: (S, L) += a * d for both
+// lanes, with a = ah + al, d = dh + dl and the negated parts ndh = -dh,
+// ndl = -dl supplied (there is no packed negation).
+__device__ __forceinline__ unsigned long long f2add(unsigned long long x, unsigned long long y) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2sub(unsigned long long x, unsigned long long y) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long x, unsigned long long y) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long x, unsigned long long y,
+                                                    unsigned long long z) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(x), "l"(y), "l"(z));
+  return r;
+}
+__device__ __forceinline__ void ff2_madd(unsigned long long& S, unsigned long long& L, unsigned long long ah,
+                                         unsigned long long al, unsigned long long dh, unsigned long long ndh,
+                                         unsigned long long ndl) {
+  const unsigned long long p = f2mul(ah, dh);
+  unsigned long long ne = f2fma(ah, ndh, p);  // -(exact product error)
+  ne = f2fma(ah, ndl, ne);
+  ne = f2fma(al, ndh, ne);                     // -(error + cross terms)
+  const unsigned long long s = f2add(S, p);
+  const unsigned long long z = f2sub(s, S);
+  const unsigned long long t = f2add(f2sub(S, f2sub(s, z)), f2sub(p, z));
+  S = s;
+  L = f2add(L, f2sub(t, ne));
+}
+__device__ __forceinline__ float lo32f(unsigned long long v) { return __uint_as_float((unsigned)v); }
+__device__ __forceinline__ float hi32f(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+
+template <int MODE, bool PRESPLIT>
+__global__ void __launch_bounds__(kFFThreads, 1) k_stream_ff(const double* __restrict__ A, long long lda, int m,
+                                                             long long n, const double* __restrict__ vec,
+                                                             double* __restrict__ out, const double* __restrict__ x,
+                                                             const double* __restrict__ u, LsParams lp, DevState* st,
+                                                             double* __restrict__ partials, FFCfg cfg) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stages = smem;
+  float2* d2 = reinterpret_cast<float2*>(smem + (size_t)kFFStages * kFFStageBytes);
+  const int mpad = (m + 63) & ~63;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(smem + (size_t)kFFStages * kFFStageBytes + (size_t)mpad * 12);
+  __shared__ double wred[kFFConsumers + 1][32];
+  __shared__ double red[32];
+  __shared__ unsigned long long dmax_bits;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned full0 = smem_u32(bars), empty0 = smem_u32(bars + kFFStages);
+
+  // ---- prologue: barriers, and the vector scaled by a power of two and split
+  if (tid == 0) {
+    for (int s = 0; s < kFFStages; s++) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, kFFConsumers);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    dmax_bits = 0ull;
+  }
+  __syncthreads();
+  unsigned long long mb = 0ull;
+  for (int i = tid; i < m; i += blockDim.x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(vec[i]) & 0x7FFFFFFFFFFFFFFFull;
+    mb = b > mb ? b : mb;
+  }
+  atomicMax(&dmax_bits, mb);
+  __syncthreads();
+  int ex = (int)((dmax_bits >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) ex = 1023;  // zero vector (or non-finite): no scaling
+  const double scale = __longlong_as_double((long long)(2046 - ex) << 52);    // 2^(1023-ex)
+  const double unscale = __longlong_as_double((long long)ex << 52);           // 2^(ex-1023)
+  // PRESPLIT layout per row pair k: D4[k] = (dh0, dh1, -dh0, -dh1), DL[k] = (-dl0, -dl1)
+  float4* D4 = reinterpret_cast<float4*>(d2);
+  float2* DL = reinterpret_cast<float2*>(D4 + mpad / 2);
+  if (PRESPLIT) {
+    for (int k = tid; k < mpad / 2; k += blockDim.x) {
+      float h[2] = {0.0f, 0.0f}, l[2] = {0.0f, 0.0f};
+      for (int q = 0; q < 2; q++) {
+        const int i = 2 * k + q;
+        if (i < m) {
+          const double v = vec[i] * scale;
+          h[q] = __double2float_rn(v);
+          l[q] = __double2float_rn(v - (double)h[q]);
+        }
+      }
+      D4[k] = make_float4(h[0], h[1], -h[0], -h[1]);
+      DL[k] = make_float2(-l[0], -l[1]);
+    }
+  } else {
+    for (int i = tid; i < mpad; i += blockDim.x) {
+      float hi = 0.0f, lo = 0.0f;
+      if (i < m) {
+        const double v = vec[i] * scale;
+        hi = __double2float_rn(v);
+        lo = __double2float_rn(v - (double)hi);
+      }
+      d2[i] = make_float2(hi, lo);
+    }
+  }
+  __syncthreads();
+
+  bool timed_out = false;
+  if (warp == kFFConsumers) {
+    // ---- producer: one elected lane issues the bulk copies
+    if (lane == 0) {
+      unsigned it = 0;
+      for (long long tile = blockIdx.x; tile < cfg.ntiles && !timed_out; tile += gridDim.x) {
+        const long long c0 = tile * cfg.tc;
+        const int ncol = (int)((n - c0) < cfg.tc ? (n - c0) : cfg.tc);
+        for (int ch = 0; ch < cfg.nchunks; ch++, it++) {
+          const int r0 = ch * cfg.rows;
+          const int nr = (cfg.mm - r0) < cfg.rows ? (cfg.mm - r0) : cfg.rows;
+          const int s = it % kFFStages;
+          const unsigned ph = (it / kFFStages) & 1u;
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+            timed_out = true;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, (unsigned)(ncol * nr * 8));
+          const unsigned dst = smem_u32(stages + (size_t)s * kFFStageBytes);
+          for (int c = 0; c < ncol; c++)
+            bulk_g2s(dst + (unsigned)(c * nr * 8), A + (c0 + c) * lda + r0, (unsigned)(nr * 8), full0 + 8 * s);
+        }
+      }
+      if (timed_out) {
+        st->timeout = 1;
+        // let the copies already issued land before the block can exit
+        const unsigned issued = it;
+        for (unsigned k = issued > (unsigned)kFFStages ? issued - kFFStages : 0; k < issued; k++)
+          mbar_wait(full0 + 8 * (k % kFFStages), (k / kFFStages) & 1u);
+      }
+    }
+  } else {
+    // ---- consumers
+    float S[8], Lr[8];
+    double cand = 0.0, amax = 0.0;
+    double s_lane = 1.0;
+    if (MODE == kModeT)
+      for (int k = 0; k < lane; k++) s_lane *= lp.beta;
+    long long ej = -1;
+    float es = 0.0f, el = 0.0f;
+    int nb = 0;
+    auto flush = [&](int cnt) {
+      const bool mine = lane < cnt;
+      const double et = ((double)es + (double)el) * unscale;
+      if (mine) out[ej] = et;
+      if (MODE == kModeGmax && mine) amax = fmax(amax, fabs(et));
+      if (MODE == kModeT) {
+        double v = 0.0;
+        bool live = false;
+        if (mine) {
+          v = v_of(x[ej], u[ej], lp.pp.sigma);
+          live = !trial_skip(v, et, lp.pp);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, live);
+        while (mask) {
+          const int q = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const double bv = __shfl_sync(0xffffffffu, v, q);
+          const double bt = __shfl_sync(0xffffffffu, et, q);
+          if (lane < lp.fused) cand += trial_term(bv, bt, s_lane, lp.pp);
+        }
+      }
+    };
+    unsigned it = 0;
+    for (long long tile = blockIdx.x; tile < cfg.ntiles && !timed_out; tile += gridDim.x) {
+      const long long c0 = tile * cfg.tc;
+      const int ncol = (int)((n - c0) < cfg.tc ? (n - c0) : cfg.tc);
+#pragma unroll
+      for (int q = 0; q < 8; q++) S[q] = Lr[q] = 0.0f;
+      for (int ch = 0; ch < cfg.nchunks; ch++, it++) {
+        const int r0 = ch * cfg.rows;
+        const int nr = (cfg.mm - r0) < cfg.rows ? (cfg.mm - r0) : cfg.rows;
+        const int s = it % kFFStages;
+        if (!mbar_wait(full0 + 8 * s, (it / kFFStages) & 1u)) {
+          timed_out = true;
+          break;
+        }
+        const unsigned char* stg = stages + (size_t)s * kFFStageBytes;
+        const float4* dq = reinterpret_cast<const float4*>(d2 + r0);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const int c = warp * cfg.cpw + q;
+          if (q < cfg.cpw && c < ncol) {
+            const ulonglong2* col = reinterpret_cast<const ulonglong2*>(stg + (size_t)c * nr * 8);
+            float s0 = 0.0f, l0 = 0.0f, s1 = 0.0f, l1 = 0.0f;
+            if (PRESPLIT) {
+              // pairs of rows: col[k] = (ah0, ah1 | al0, al1)
+              const ulonglong2* D4p = reinterpret_cast<const ulonglong2*>(D4 + r0 / 2);
+              const unsigned long long* DLp = reinterpret_cast<const unsigned long long*>(DL + r0 / 2);
+              unsigned long long Sa = 0ull, La = 0ull, Sb = 0ull, Lb = 0ull;
+              int k = lane;
+              for (; k + 32 < nr / 2; k += 64) {
+                const ulonglong2 a0 = col[k], a1 = col[k + 32];
+                const ulonglong2 d0 = D4p[k], d1 = D4p[k + 32];
+                const unsigned long long n0 = DLp[k], n1 = DLp[k + 32];
+                ff2_madd(Sa, La, a0.x, a0.y, d0.x, d0.y, n0);
+                ff2_madd(Sb, Lb, a1.x, a1.y, d1.x, d1.y, n1);
+              }
+              if (k < nr / 2) {
+                const ulonglong2 a0 = col[k];
+                const ulonglong2 d0 = D4p[k];
+                ff2_madd(Sa, La, a0.x, a0.y, d0.x, d0.y, DLp[k]);
+              }
+              s0 = lo32f(Sa);
+              l0 = lo32f(La);
+              ff_merge(s0, l0, hi32f(Sa), hi32f(La));
+              s1 = lo32f(Sb);
+              l1 = lo32f(Lb);
+              ff_merge(s1, l1, hi32f(Sb), hi32f(Lb));
+            } else {
+#pragma unroll 2
+              for (int i = lane; 2 * i < nr; i += 32) {
+                ulonglong2 a = col[i];
+                const float4 dd = dq[i];
+                if (r0 + 2 * i + 1 >= m) a.y = 0ull;
+                float ah, al, bh, bl;
+                split_f64(a.x, ah, al);
+                split_f64(a.y, bh, bl);
+                ff_madd(s0, l0, ah, al, dd.x, dd.y);
+                ff_madd(s1, l1, bh, bl, dd.z, dd.w);
+              }
+            }
+            ff_merge(s0, l0, s1, l1);
+            ff_merge(S[q], Lr[q], s0, l0);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * s);
+      }
+      if (timed_out) break;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int c = warp * cfg.cpw + q;
+        if (q < cfg.cpw && c < ncol) {
+          float Sq = S[q], Lq = Lr[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float So = __shfl_xor_sync(0xffffffffu, Sq, o);
+            const float Lo = __shfl_xor_sync(0xffffffffu, Lq, o);
+            ff_merge(Sq, Lq, So, Lo);
+          }
+          if (lane == (nb & 31)) {
+            ej = c0 + c;
+            es = Sq;
+            el = Lq;
+          }
+          nb++;
+          if ((nb & 31) == 0) flush(32);
+        }
+      }
+    }
+    if (!timed_out && (nb & 31)) flush(nb & 31);
+    if (timed_out) st->timeout = 1;
+    if (MODE == kModeT) wred[warp][lane] = cand;
+    if (MODE == kModeGmax) wred[warp][lane] = amax;
+  }
+  if (warp == kFFConsumers) wred[warp][lane] = 0.0;
+  __syncthreads();
+  if (MODE == kModeU) return;
+  if (MODE == kModeGmax) {
+    double mx = 0.0;
+    if (warp == 0)
+      for (int w = 0; w < kFFConsumers; w++) mx = fmax(mx, wred[w][lane]);
+    mx = block_max(warp == 0 ? mx : 0.0, red);
+    if (tid == 0) partials[blockIdx.x] = mx;
+    if (!last_block(&st->counters[kCtrGmax])) return;
+    double g = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) g = fmax(g, ld_cg(&partials[b]));
+    g = block_max(g, red);
+    if (tid == 0) st->gmax = g;
+    reset_counter(&st->counters[kCtrGmax]);
+    return;
+  }
+  // kModeT: per-block trial sums in a fixed order, then the selection
+  if (warp == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kFFConsumers; w++) s += wred[w][lane];
+    partials[(long long)blockIdx.x * 32 + lane] = s;
+  }
+  if (!last_block(&st->counters[kCtrStream])) return;
+  if (warp == 0) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) s += ld_cg(&partials[(long long)b * 32 + lane]);
+    if (lane < lp.fused) st->lsdiff[lane] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence_block();
+    double s;
+    int k = armijo_select(st, lp, 0, lp.fused, s);
+    if (k >= 0) {
+      st->s = s;
+      st->ls_k = k;
+      st->ls_state = 0;
+    } else if (lp.fused < lp.max_ls) {
+      st->ls_state = 1;
+    } else {
+      st->s = s;
+      st->ls_k = lp.max_ls - 1;
+      st->ls_state = 0;
+    }
+  }
+  reset_counter(&st->counters[kCtrStream]);
+}
+
+static FFCfg ff_config(int m, long long n) {
+  FFCfg c;
+  c.mm = (m + 1) & ~1;
+  const long long colb = (long long)c.mm * 8;
+  if ((long long)kFFConsumers * colb <= kFFStageBytes) {
+    c.rows = c.mm;
+    c.nchunks = 1;
+    long long cpw = kFFStageBytes / (kFFConsumers * colb);
+    c.cpw = (int)(cpw > 8 ? 8 : (cpw < 1 ? 1 : cpw));
+  } else {
+    c.cpw = 1;
+    c.rows = (kFFStageBytes / (kFFConsumers * 8)) / 64 * 64;
+    c.nchunks = (c.mm + c.rows - 1) / c.rows;
+  }
+  c.tc = kFFConsumers * c.cpw;
+  c.ntiles = (n + c.tc - 1) / c.tc;
+  return c;
+}
+
+static size_t ff_smem(int m) {
+  return (size_t)kFFStages * kFFStageBytes + (size_t)((m + 63) & ~63) * 12 + 2 * kFFStages * 8;
+}
+
+template <int MODE, bool PRESPLIT>
+static void launch_ff(const double* A, long long lda, int m, long long n, const double* vec, double* out,
+                      const double* x, const double* u, LsParams lp, DevState* st, double* partials, int sms,
+                      cudaStream_t s) {
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    cudaFuncSetAttribute(k_stream_ff<MODE, PRESPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ff_smem(kMaxM));
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  FFCfg cfg = ff_config(m, n);
+  long long grid = cfg.ntiles < sms ? cfg.ntiles : sms;
+  if (grid < 1) grid = 1;
+  k_stream_ff<MODE, PRESPLIT>
+      <<<(int)grid, kFFThreads, ff_smem(m), s>>>(A, lda, m, n, vec, out, x, u, lp, st, partials, cfg);
+}
+
+// One-time conversion of FP64 A into the float-float pair layout read by the
+// PRESPLIT stream: per column, row pair k is (hi(2k), hi(2k+1), lo(2k), lo(2k+1))
+// as four floats; rows >= m are zero.  Column stride: mm = m rounded up to even.
+__global__ void k_presplit(const double* __restrict__ A, long long lda, int m, long long n, float4* __restrict__ S) {
+  const int pairs = (m + 1) / 2;
+  const long long total = (long long)pairs * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / pairs;
+    const int k = (int)(e % pairs);
+    const double* col = A + j * lda;
+    float h0, l0, h1 = 0.0f, l1 = 0.0f;
+    split_f64((unsigned long long)__double_as_longlong(col[2 * k]), h0, l0);
+    if (2 * k + 1 < m) split_f64((unsigned long long)__double_as_longlong(col[2 * k + 1]), h1, l1);
+    S[e] = make_float4(h0, h1, l0, l1);
+  }
+}
+
+void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s) {
+  count_launch();
+  k_presplit<<<8 * sms, 256, 0, s>>>(A, lda, m, n, reinterpret_cast<float4*>(S));
+}
+
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,
                    double* out, const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls,
                    int fused, DevState* st, double* partials, int grid, cudaStream_t s) {
   LsParams lp{pp, mu, beta, max_ls, fused};
   const size_t smem = (size_t)((m + 63) & ~63) * sizeof(double);
-  (void)dtype;
   const double* Ad = (const double*)A;
   count_launch();
+  if (dtype == kStreamFloatFloat) {
+    const int sms = grid / 4;
+    if (mode == kModeU)
+      launch_ff<kModeU, false>(Ad, lda, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    else if (mode == kModeT)
+      launch_ff<kModeT, false>(Ad, lda, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    else
+      launch_ff<kModeGmax, false>(Ad, lda, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    return;
+  }
+  if (dtype == kStreamSplit) {
+    const int sms = grid / 4;
+    if (mode == kModeU)
+      launch_ff<kModeU, true>(Ad, lda, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    else if (mode == kModeT)
+      launch_ff<kModeT, true>(Ad, lda, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    else
+      launch_ff<kModeGmax, true>(Ad, lda, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    return;
+  }
   if (mode == kModeU)
     k_stream_f64<kModeU><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
   else if (mode == kModeT)
     k_stream_f64<kModeT><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
   else
     k_stream_f64<kModeGmax><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
+}
+
+// Flags entries of A (rows < m) that the float-float split cannot represent:
+// non-zero values outside [2^-100, 2^100], subnormals, infinities and NaN.
+__global__ void k_check_range(const double* __restrict__ A, long long lda, int m, long long n, int* bad) {
+  const long long total = lda * n;
+  int local = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    if (k % lda >= m) continue;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(A[k]);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const bool zero = (b & 0x7FFFFFFFFFFFFFFFull) == 0ull;
+    if (!zero && (e < 1023 - 100 || e > 1023 + 100)) local = 1;
+  }
+  if (__syncthreads_or(local) && threadIdx.x == 0) atomicOr(bad, 1);
+}
+
+void launch_check_range(const double* A, long long lda, int m, long long n, int* bad, int sms, cudaStream_t s) {
+  count_launch();
+  k_check_range<<<4 * sms, 256, 0, s>>>(A, lda, m, n, bad);
 }
 
 void launch_ls_fallback(const double* x, const double* u, const double* t, long long n, ProxParams pp, double mu,

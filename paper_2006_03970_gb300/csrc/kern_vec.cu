@@ -15,7 +15,7 @@ std::atomic<long long> g_launches{0};
 constexpr int kVecThreads = 256;
 
 int vec_grid(long long n, int sms) {
-  long long g = (n + 2047) / 2048;
+  long long g = (n + 511) / 512;
   long long cap = 4LL * sms;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
@@ -194,8 +194,8 @@ __global__ void k_set_x(double* __restrict__ x, const double* __restrict__ u, lo
 
 // Element loaders for the gather: value of A(i, col) as double.
 struct LoadF64 {
-  const double* A;
-  __device__ double operator()(long long off) const { return A[off]; }
+  const double* __restrict__ A;
+  __device__ double operator()(long long off) const { return __ldg(A + off); }
 };
 struct LoadF32 {
   const float* A;
@@ -210,7 +210,7 @@ struct LoadBF16 {
 // One warp per column, grid-stride.  If r exceeds the panel capacity nothing is
 // written and the overflow flag is raised for the host.
 template <class Load>
-__global__ void k_gather(Load ld, long long lda, int m, const int32_t* __restrict__ J, const DevState* st,
+__global__ void __launch_bounds__(256) k_gather(Load ld, long long lda, int m, const int32_t* __restrict__ J, const DevState* st,
                          long long r_host, long long rcap, double* __restrict__ P, long long ldp,
                          float* __restrict__ P32, long long ldp32, int* overflow) {
   const long long r = r_host >= 0 ? r_host : st->r;
@@ -225,8 +225,9 @@ __global__ void k_gather(Load ld, long long lda, int m, const int32_t* __restric
     const long long src = (long long)J[k] * lda;
     double* dst = P + k * ldp;
     float* dst32 = P32 + k * ldp32;
+#pragma unroll 4
     for (int i = lane; i < m; i += 32) {
-      double v = ld(src + i);
+      const double v = ld(src + i);
       dst[i] = v;
       dst32[i] = (float)v;
     }
@@ -316,6 +317,123 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ ou
   reset_counter(&st->counters[kCtrCombine]);
 }
 
+// out_i = ca*a_i + cb*b_i + cs*sum_k P[i, k] coef[k]: 32 rows x 8 column groups per
+// block (coalesced column reads), the groups summed in a fixed order; optional
+// scalar products as in k_combine, reduced by the last block.
+constexpr int kGemvChunk = 64;     // columns per block of the panel GEMV
+constexpr int kGemvMaxSplit = 32;  // column chunks per row tile (more columns loop inside a chunk)
+
+__global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, long long ldp, int m,
+                                                const double* __restrict__ coef, const DevState* st,
+                                                long long r_host, long long rcap, double* __restrict__ out,
+                                                const double* __restrict__ a, double ca, const double* __restrict__ b,
+                                                double cb, double cs, int which, const double* __restrict__ yv,
+                                                const double* __restrict__ bv, const double* __restrict__ gv,
+                                                DevState* stw, double* scratch, double* __restrict__ cpart,
+                                                unsigned* tile_ctr) {
+  __shared__ double part[8][33];
+  __shared__ double red[32];
+  __shared__ bool tile_last;
+  const long long r = r_host >= 0 ? r_host : st->r;
+  if (r > rcap) return;  // the gather raised the overflow flag; the host redoes this step
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  // column chunks depend on r only (never on the launch shape), so the
+  // summation order -- and the result -- is the same for every launch
+  long long nsplit = (r + kGemvChunk - 1) / kGemvChunk;
+  if (nsplit > (long long)gridDim.y) nsplit = gridDim.y;
+  if (nsplit < 1) nsplit = 1;
+  const long long per = (r + nsplit - 1) / nsplit;
+  const long long k0 = blockIdx.y < nsplit ? (long long)blockIdx.y * per : r;
+  const long long k1 = (k0 + per) < r ? (k0 + per) : r;
+  double acc = 0.0;
+  if (i < m) {
+#pragma unroll 4
+    for (long long k = k0 + grp; k < k1; k += 8) acc = fma(P[i + k * ldp], coef[k], acc);
+  }
+  part[grp][lane] = acc;
+  __syncthreads();
+  if (gridDim.y > 1) {
+    if (grp == 0) {
+      double sum = 0.0;
+      for (int g = 0; g < 8; g++) sum += part[g][lane];
+      if (i < m) cpart[(long long)blockIdx.y * m + i] = sum;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned prev = atomicAdd(&tile_ctr[blockIdx.x], 1u);
+      tile_last = (prev == gridDim.y - 1);
+      if (tile_last) tile_ctr[blockIdx.x] = 0u;
+    }
+    __syncthreads();
+    if (!tile_last) return;
+    __threadfence();
+  }
+  double o = 0.0;
+  if (grp == 0 && i < m) {
+    double sum = 0.0;
+    if (gridDim.y > 1)
+      for (long long y = 0; y < nsplit; y++) sum += __ldcg(&cpart[y * m + i]);
+    else
+      for (int g = 0; g < 8; g++) sum += part[g][lane];
+    double lin = 0.0;
+    if (a) lin = ca * a[i];
+    if (b) lin = a ? lin + cb * b[i] : cb * b[i];
+    o = (a || b) ? lin + cs * sum : cs * sum;
+    out[i] = o;
+  }
+  if (which == 0) return;
+  double q[4] = {0, 0, 0, 0};
+  if (grp == 0 && i < m) {
+    const double yi = yv[i], bi = bv[i];
+    if (which == 1) {
+      q[0] = o * o;
+      q[1] = yi * yi;
+      q[2] = (yi - o) * (yi - o);
+      q[3] = bi * yi;
+    } else {
+      const double gi = gv[i];
+      q[0] = gi * o;
+      q[1] = yi * o;
+      q[2] = o * o;
+      q[3] = bi * o;
+    }
+  }
+  for (int k = 0; k < 4; k++) {
+    double bsum = block_sum(q[k], red);
+    if (threadIdx.x == 0) scratch[blockIdx.x * 4 + k] = bsum;
+  }
+  // only the row tiles' last blocks get here: count them against gridDim.x
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&stw->counters[kCtrGemv], 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double tot[4] = {0, 0, 0, 0};
+    for (int bl = 0; bl < (int)gridDim.x; bl++)
+      for (int k = 0; k < 4; k++) tot[k] += ld_cg(&scratch[bl * 4 + k]);
+    if (which == 1) {
+      stw->g2 = tot[0];
+      stw->y2 = tot[1];
+      stw->yg2 = tot[2];
+      stw->by = tot[3];
+    } else {
+      stw->gd = tot[0];
+      stw->yd = tot[1];
+      stw->dd = tot[2];
+      stw->bd = tot[3];
+    }
+  }
+  reset_counter(&stw->counters[kCtrGemv]);
+}
+
 // out_k = ch*h_k + cq*q_k + cd*dot(P[:, k], v), one warp per column.
 __global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, long long r, const double* __restrict__ v,
                          double* __restrict__ out, const double* __restrict__ h, double ch,
@@ -394,6 +512,19 @@ void launch_combine(double* out, const double* a, double ca, const double* b, do
   int grid = (m + kVecThreads - 1) / kVecThreads;
   count_launch();
   k_combine<<<grid, kVecThreads, 0, s>>>(out, a, ca, b, cb, part, cs, m, which, y, bb, g, st, scratch);
+}
+
+void launch_gemv_n(const double* P, long long ldp, int m, const double* coef, const DevState* st, long long r_host,
+                   long long rcap, double* out, const double* a, double ca, const double* b, double cb, double cs,
+                   int which, const double* yv, const double* bv, const double* gv, DevState* stw, double* scratch,
+                   double* cpart, unsigned* tile_ctr, cudaStream_t s) {
+  // a fixed launch shape; the kernel derives its column chunks from r alone
+  const long long split = kGemvMaxSplit;
+  (void)r_host;
+  count_launch();
+  dim3 grid((m + 31) / 32, (unsigned)split);
+  k_gemv_n<<<grid, 256, 0, s>>>(P, ldp, m, coef, st, r_host, rcap, out, a, ca, b, cb, cs, which, yv, bv, gv, stw,
+                                scratch, cpart, tile_ctr);
 }
 
 void launch_gemv_t(const double* P, long long ldp, int m, long long r, const double* v, double* out, const double* h,

@@ -62,7 +62,53 @@ def test_at_y_stream(m, n):
     u = torch.empty(n, dtype=torch.float64, device="cuda")
     pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
     ref = At @ y
+    # float-float products carry 47 significant bits; the low word accumulates m roundings of 2^-24
+    # relative to itself (itself ~2^-24 of the terms): |err| <= (2^-45 + m 2^-47) sum |a||y|.
+    bound = (2.0 ** -45 + m * 2.0 ** -47) * (np.abs(At) @ np.abs(y)) + 1e-300
+    assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
+    # float-float with on-the-fly splitting (precision = 3) meets the same bound
+    ctx.set_options(pkg.ssnal_en_default_options(precision=3))
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
+    assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
+    # the FP64-FMA stream (precision = 2) stays within the FP64 dot-product bound
+    ctx.set_options(pkg.ssnal_en_default_options(precision=2))
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
     bound = 4 * m * np.finfo(float).eps * (np.abs(At) @ np.abs(y)) + 1e-300
+    assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
+    ctx.close()
+
+
+@pytest.mark.parametrize("scale", [1e-200, 1e120])
+def test_at_y_out_of_range_entries_use_fp64_stream(scale):
+    rng = np.random.default_rng(3)
+    m, n = 50, 700
+    At = rng.normal(size=(n, m))
+    At[17, 3] = scale  # outside [2^-100, 2^100]: the float-float split is not used
+    y = rng.normal(size=m)
+    ctx = pkg.Context(At)
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
+    ref = At @ y
+    bound = 4 * m * np.finfo(float).eps * (np.abs(At) @ np.abs(y)) + 1e-300
+    assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
+    ctx.close()
+
+
+@pytest.mark.parametrize("m", [2, 64, 641, 1280, 1281, 4096])
+def test_at_y_stream_tile_shapes(m):
+    # single-chunk tiles (several columns per warp) and row-chunked tall columns
+    n = 1031
+    rng = np.random.default_rng(m)
+    At = rng.normal(size=(n, m))
+    y = rng.normal(size=m) * 1e-3
+    ctx = pkg.Context(At)
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
+    ref = At @ y
+    bound = (2.0 ** -45 + m * 2.0 ** -47) * (np.abs(At) @ np.abs(y)) + 1e-300
+    assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
+    ctx.set_options(pkg.ssnal_en_default_options(precision=3))
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
     assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
     ctx.close()
 
@@ -135,7 +181,8 @@ def test_grad_gather(m, n, r):
 
 # ---------------------------------------------------------------- a5 + a6: Newton system
 @pytest.mark.parametrize("m,r", [(30, 0), (30, 1), (30, 29), (30, 30), (30, 31), (100, 250), (257, 65),
-                                 (500, 120)])
+                                 (500, 120), (128, 129), (129, 300), (300, 200), (200, 400), (700, 600),
+                                 (1000, 999)])
 def test_newton_direction(m, r):
     rng = np.random.default_rng(m + r)
     n = max(r, 1) + 10
@@ -274,6 +321,16 @@ def test_path_host_matches_device_path():
     assert done == doneh
     np.testing.assert_array_equal(Xh, X.cpu().numpy())  # same kernels, same order: bitwise
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 2, 3])
+def test_config1_parity_both_streams(precision):
+    p = synth.config1()
+    lam1, lam2 = R.lambdas(p.At, p.b, p.alpha, p.c)
+    xg, yg, res, ro = _solve_both(p, lam1, lam2, options=pkg.ssnal_en_default_options(precision=precision))
+    assert res.status == pkg.OK
+    assert_parity(p.At, p.b, lam1, lam2, xg, ro)
+    assert res.al_iters == ro.al_iters
 
 
 def test_bitwise_repeatable():
