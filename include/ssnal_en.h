@@ -83,7 +83,8 @@ typedef struct {
                            3: as 0 but without the copy (entries split on the fly, slower).
                            2: FP64 FMAs always.
                            1: reserved for the mixed path (low-precision storage of A). */
-  int32_t refine_steps; /* 2: iterative-refinement steps of the Newton solve */
+  int32_t refine_steps; /* 1: iterative-refinement steps of the Newton solve (FP64 residual through
+                           the packed A_J, FP32 factor) */
   int32_t use_y0;       /* 0: y0 = A x0 - b; 1: take y0 from the y argument of ssnal_en_solve */
   int32_t ls_fused;     /* 16: trial steps evaluated inside the A^T d pass (1..16); later trials
                            are evaluated by a pass over the stored n-vectors only */
@@ -173,6 +174,17 @@ ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* ctx, const double* b_host, doub
  * Synchronises the stream.  Errors: EINVAL (null ctx), ECUDA. */
 ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t reset, double* stream_ms,
                                  int64_t* stream_launches, double* stream_bytes, int64_t* kernel_launches);
+
+/* Per-phase device time since the last ssnal_en_profile(reset = 1), recorded
+ * while profiling is enabled.  Four phases, in this order:
+ *  0 prox + active set + gather + gradient (eqs. prox_elastic, Q_def, grad_phy)
+ *  1 Newton direction: SYRK, Cholesky, solves and refinement (eqs. AJ_system, smw_formula)
+ *  2 the pass over A with the fused line search (eq. line_search)
+ *  3 the multiplier update x <- prox(x - sigma A^T y) (eq. update_x)
+ * phase_ms, phase_count: host arrays of 4 (either may be NULL).  Time on the
+ * stream outside these phases (host round trips) is not attributed.
+ * Synchronises the stream.  Errors: EINVAL (null ctx), ECUDA. */
+ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* ctx, double* phase_ms, int64_t* phase_count);
 
 /* ---------------------------------------------------------------------------
  * Single steps of the hot path, exposed for tests and for callers that build

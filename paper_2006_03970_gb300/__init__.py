@@ -21,7 +21,8 @@ __all__ = [
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
     "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_prox_active", "ssnal_en_op_grad",
-    "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_prox_active_static", "STATIC_MAX_N", "Context",
+    "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_profile_phases", "ssnal_en_prox_active_static",
+    "STATIC_MAX_N", "Context",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -68,7 +69,7 @@ _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
-           "ssnal_en_prox_active_static"]
+           "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
 
 
 def load_library(path: str | None = None):
@@ -98,6 +99,7 @@ def load_library(path: str | None = None):
     L.ssnal_en_op_prox_active.argtypes = [vp, vp, vp, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64)]
     L.ssnal_en_op_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     L.ssnal_en_op_newton.argtypes = [vp, i64, dbl, vp, vp]
+    L.ssnal_en_profile_phases.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
     L.ssnal_en_prox_active_static.argtypes = [vp, vp, i64, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64), vp]
     L.ssnal_en_profile.argtypes = [vp, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                    ctypes.POINTER(i64)]
@@ -254,6 +256,17 @@ def ssnal_en_op_grad(ctx, J, wJ, r, y, b, g):
 def ssnal_en_op_newton(ctx, r, kappa, g, d):
     return _check(load_library().ssnal_en_op_newton(ctx, int(r), float(kappa), _ptr(g), _ptr(d)),
                   "ssnal_en_op_newton", allow=(OK, ENOCONV))
+
+
+PHASES = ("prox_gather_grad", "newton_direction", "stream_line_search", "al_update")
+
+
+def ssnal_en_profile_phases(ctx):
+    """Device ms and counts per phase (see PHASES) since the last profile reset."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(load_library().ssnal_en_profile_phases(ctx, ms, n), "ssnal_en_profile_phases")
+    return {PHASES[k]: (ms[k], n[k]) for k in range(4)}
 
 
 def ssnal_en_profile(ctx, enable: bool, reset: bool = False):

@@ -19,6 +19,9 @@
 
 using namespace ssnal;
 
+// Phases timed by ssnal_en_profile_phases.
+enum { kPhaseGrad = 0, kPhaseNewton = 1, kPhaseStream = 2, kPhaseUpdate = 3, kPhases = 4 };
+
 struct ssnal_en_ctx {
   int64_t m = 0, n = 0, lda = 0;
   int dtype = 0;
@@ -56,13 +59,17 @@ struct ssnal_en_ctx {
   int64_t ldp = 0, ldp32 = 0, rcap = 0;
   float* G = nullptr;
   int64_t ldg = 0;
+  float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
   double* Xdev = nullptr;  // path_host output staging
   int64_t Xcap = 0;
   // event timing of the A^T d stream kernel (ssnal_en_profile)
   int prof = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool, ev_pending;
+  std::vector<int> ev_phase;  // phase of each pending pair
   double prof_ms = 0.0, prof_bytes = 0.0;
   int64_t prof_launches = 0;
+  double phase_ms[kPhases] = {};
+  int64_t phase_n[kPhases] = {};
 };
 
 namespace {
@@ -167,6 +174,7 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->P);
   dev_free(c->P32);
   dev_free(c->G);
+  dev_free(c->Wdiag);
   dev_free(c->Xdev);
   dev_free(c->Asplit);
 }
@@ -202,15 +210,48 @@ ProxParams make_pp(double sigma, double lam1, double lam2) {
   return pp;
 }
 
-// Times of the stream launches recorded since the last synchronisation.
+// Times of the launches recorded since the last synchronisation.
 void prof_harvest(ssnal_en_ctx* c) {
-  for (auto& pr : c->ev_pending) {
+  for (size_t k = 0; k < c->ev_pending.size(); k++) {
+    auto& pr = c->ev_pending[k];
     float ms = 0.0f;
-    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->prof_ms += ms;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+      const int ph = c->ev_phase[k];
+      if (ph == kPhaseStream) c->prof_ms += ms;
+      c->phase_ms[ph] += ms;
+      c->phase_n[ph]++;
+    }
     c->ev_pool.push_back(pr);
   }
   c->ev_pending.clear();
+  c->ev_phase.clear();
 }
+
+// Event pair around one phase (no-op unless profiling).
+struct PhaseTimer {
+  ssnal_en_ctx* c;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  int phase;
+  PhaseTimer(ssnal_en_ctx* c_, int ph) : c(c_), phase(ph) {
+    if (!c->prof) return;
+    if (c->ev_pool.empty()) {
+      if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+        c = nullptr;
+        return;
+      }
+    } else {
+      ev = c->ev_pool.back();
+      c->ev_pool.pop_back();
+    }
+    cudaEventRecord(ev.first, c->stream);
+  }
+  ~PhaseTimer() {
+    if (!c || !c->prof) return;
+    cudaEventRecord(ev.second, c->stream);
+    c->ev_pending.push_back(ev);
+    c->ev_phase.push_back(phase);
+  }
+};
 
 ssnal_en_status read_state(ssnal_en_ctx* c) {
   CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
@@ -222,22 +263,10 @@ ssnal_en_status read_state(ssnal_en_ctx* c) {
 // The A^T d stream of one Newton step, bracketed by CUDA events when profiling.
 ssnal_en_status stream_t(ssnal_en_ctx* c, const double* x, ProxParams pp) {
   const ssnal_en_options& o = c->opt;
-  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-  if (c->prof) {
-    if (c->ev_pool.empty()) {
-      CK(cudaEventCreate(&ev.first));
-      CK(cudaEventCreate(&ev.second));
-    } else {
-      ev = c->ev_pool.back();
-      c->ev_pool.pop_back();
-    }
-    CK(cudaEventRecord(ev.first, c->stream));
-  }
+  PhaseTimer timer(c, kPhaseStream);
   launch_stream(kModeT, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
                 o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
   if (c->prof) {
-    CK(cudaEventRecord(ev.second, c->stream));
-    c->ev_pending.push_back(ev);
     c->prof_launches++;
     const double es = (double)elem_size(c->dtype);
     c->prof_bytes += (double)c->m * (double)c->n * es + 3.0 * 8.0 * (double)c->n + 8.0 * (double)c->m;
@@ -262,12 +291,15 @@ void launch_grad(ssnal_en_ctx* c, int mode, const double* b, long long r_host) {
 ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, const double* b, ProxParams pp,
                                  int apply_update) {
   cudaStream_t s = c->stream;
+  {
+  PhaseTimer timer(c, kPhaseGrad);
   launch_prox_count(mode, x, c->u, c->t, c->y, c->d, c->n, (int)c->m, pp, apply_update, c->st, c->counts,
                     c->vpartials, c->grid_vec, s);
   launch_prox_scatter(mode, x, c->u, c->n, pp, c->counts + c->grid_vec, c->J, c->wJ, c->grid_vec, s);
   launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, -1, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms,
                 s);
   launch_grad(c, mode, b, -1);
+  }
   CK(cudaGetLastError());
   ssnal_en_status st = read_state(c);
   if (st != SSNAL_EN_OK) return st;
@@ -292,9 +324,11 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
 ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d,
                                  const double* yv, const double* bv, int dots) {
   cudaStream_t s = c->stream;
+  PhaseTimer timer(c, kPhaseNewton);
   const int m = (int)c->m;
   const int refine = c->opt.refine_steps > 0 ? c->opt.refine_steps : 0;
   const int which = dots ? 2 : 0;
+  const float* wd = nullptr;  // inverse diagonal blocks of the factor, when available
   if (r == 0) {
     launch_gemv_n(c->P, c->ldp, m, c->wJ, c->st, 0, c->rcap, d, nullptr, 0.0, g, -1.0, 0.0, which, yv, bv, g, c->st,
                   c->comb_scratch, c->cpart, c->tile_ctr, s);
@@ -306,15 +340,15 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
     if (N <= kSmallNewton) {
       launch_chol_solve_small(c->G, c->ldg, N, c->st, c->h, c->q, 1.0, s);
     } else {
-      chol_factor(c->G, c->ldg, N, c->st, s);
-      launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, s);
+      wd = chol_factor(c->G, c->ldg, N, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
+      launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, wd, s);
     }
     for (int it = 0; it < refine; it++) {
       // resr = h - kappa^{-1} q - A_J^T (A_J q)
       launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->tmpm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr,
                     nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
       launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
-      launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, s);
+      launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, wd, s);
     }
     launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, which, yv, bv, g, c->st,
                   c->comb_scratch, c->cpart, c->tile_ctr, s);
@@ -324,15 +358,15 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
     if (m <= kSmallNewton) {
       launch_chol_solve_small(c->G, c->ldg, m, c->st, g, d, -1.0, s);
     } else {
-      chol_factor(c->G, c->ldg, m, c->st, s);
-      launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, s);
+      wd = chol_factor(c->G, c->ldg, m, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
+      launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, wd, s);
     }
     for (int it = 0; it < refine; it++) {
       // tmpm = -g - d - kappa A_J (A_J^T d)
       launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
       launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
                     nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
-      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, s);
+      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, wd, s);
     }
     if (dots)
       launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);
@@ -411,7 +445,10 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
     const double dual = -(0.5 * h.y2 + h.by) - (lam2 > 0 ? h.dualpen / (2.0 * lam2) : 0.0);
     R.dual_gap = lam2 > 0 ? R.primal_obj - dual : NAN;
     R.sigma = sigma;
-    launch_set_x(x, c->u, c->n, pp, c->sms, s);
+    {
+      PhaseTimer timer(c, kPhaseUpdate);
+      launch_set_x(x, c->u, c->n, pp, c->sms, s);
+    }
     CK(cudaGetLastError());
     if (failed) break;
     if (kkt1 <= o.tol && kkt3 <= o.tol) {
@@ -458,7 +495,7 @@ void ssnal_en_default_options(ssnal_en_options* o) {
   o->max_newton = 50;
   o->max_ls = 40;
   o->precision = 0;
-  o->refine_steps = 2;
+  o->refine_steps = 1;
   o->use_y0 = 0;
   o->ls_fused = kFusedLS;
   o->max_active = 0;
@@ -542,6 +579,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->cpart, (size_t)kGemvSplitMax * m);
   AL(c->tile_ctr, (m + 31) / 32);
   AL(c->G, c->ldg * m);
+  AL(c->Wdiag, (size_t)((m + 31) / 32) * 1024);
 #undef AL
   if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) s = SSNAL_EN_ENOMEM;
   if (s == SSNAL_EN_OK) s = grow_panel(c, m < n ? m : n);
@@ -694,12 +732,27 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* c, int32_t enable, int32_t reset,
     c->prof_ms = 0.0;
     c->prof_bytes = 0.0;
     c->prof_launches = 0;
+    for (int k = 0; k < kPhases; k++) {
+      c->phase_ms[k] = 0.0;
+      c->phase_n[k] = 0;
+    }
   }
   c->prof = enable ? 1 : 0;
   if (stream_ms) *stream_ms = c->prof_ms;
   if (stream_launches) *stream_launches = c->prof_launches;
   if (stream_bytes) *stream_bytes = c->prof_bytes;
   if (kernel_launches) *kernel_launches = g_launches.load();
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* c, double* phase_ms, int64_t* phase_count) {
+  if (!c) return SSNAL_EN_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  prof_harvest(c);
+  for (int k = 0; k < kPhases; k++) {
+    if (phase_ms) phase_ms[k] = c->phase_ms[k];
+    if (phase_count) phase_count[k] = c->phase_n[k];
+  }
   return SSNAL_EN_OK;
 }
 

@@ -105,13 +105,16 @@ void launch_syrk_tn(const float* P32, long long ldp32, int m, long long r, doubl
                     cudaStream_t s);
 void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, double kappa, float* G, long long ldg,
                     cudaStream_t s);
-void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s);
+// Wdiag (may be null): receives the inverses of the 32 x 32 diagonal blocks of L
+// when the factorisation produces them (the cluster kernel).  Returns whether
+// they were written.
+bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s);
 // N <= kSmallNewton: factor and solve one right-hand side in one launch (acc = c)
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
                              double alpha, cudaStream_t s);
 // acc = (first ? alpha c : acc + alpha c) with (L L^T) c = rhs
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
-                     double alpha, cudaStream_t s);
+                     double alpha, const float* Wdiag, cudaStream_t s);
 
 // ---- streams over A (kern_stream.cu)
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,

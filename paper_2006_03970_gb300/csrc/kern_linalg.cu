@@ -277,48 +277,91 @@ __device__ void smem_forward_backward(const float* __restrict__ Ls, int ldl, int
   }
 }
 
-// Factor G (N <= kSmallN) in place in shared memory, write L back to G, and if
-// rhs != nullptr solve (L L^T) c = rhs and store acc = c (FP64).
 constexpr size_t kSmallSmem = (size_t)(kSmallN * (kSmallN + 1) + kSmallN) * sizeof(float);
 
+// Factor G (N <= kSmallN) with the matrix held in registers: thread t owns the
+// elements (lane + 32a, warp + 32b), a, b < 4.  Column k: the owner of (k, k)
+// takes the square root, the owners of column k scale it into a shared column
+// buffer, and every thread applies the rank-one update to its own elements
+// (two block barriers per column).  L is written back to G; if rhs != nullptr
+// the CTA also solves (L L^T) c = rhs and stores acc = alpha c (FP64).
 __global__ void __launch_bounds__(kSmallThreads) k_chol_small(float* __restrict__ G, long long ld, int N,
                                                               DevState* st, const double* __restrict__ rhs,
                                                               double* __restrict__ acc, double alpha) {
   extern __shared__ float sm_small[];
   float* Ls = sm_small;
   float* z = sm_small + kSmallN * (kSmallN + 1);
+  __shared__ float col[kSmallN];
+  __shared__ float rdiag;
   const int ldl = kSmallN + 1;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < N * N; e += blockDim.x) {
-    const int i = e % N, j = e / N;
-    Ls[i + j * ldl] = (i >= j) ? G[i + (long long)j * ld] : 0.0f;
-  }
-  __syncthreads();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float a[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int i = lane + 32 * p, j = warp + 32 * q;
+      a[p][q] = (i < N && j < N && i >= j) ? G[i + (long long)j * ld] : 0.0f;
+    }
   for (int k = 0; k < N; k++) {
-    if (tid == 0) {
-      float piv = Ls[k + k * ldl];
+    const int kl = k & 31, kb = k >> 5;
+    if (lane == kl && warp == kl) {
+      float piv = 0.0f;
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+        if (p == kb) piv = a[p][p];
       if (!(piv > 0.0f)) {
         st->chol_fail = 1;
         piv = 1.0f;
       }
-      Ls[k + k * ldl] = sqrtf(piv);
+      const float d = sqrtf(piv);
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+        if (p == kb) a[p][p] = d;
+      rdiag = 1.0f / d;
     }
     __syncthreads();
-    const float dkk = Ls[k + k * ldl];
-    for (int i = k + 1 + tid; i < N; i += blockDim.x) Ls[i + k * ldl] /= dkk;
-    __syncthreads();
-    // trailing update of the lower part: (i, j) with k < j <= i < N
-    const int rem = N - k - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = k + 1 + e % rem, j = k + 1 + e / rem;
-      if (i >= j) Ls[i + j * ldl] = fmaf(-Ls[i + k * ldl], Ls[j + k * ldl], Ls[i + j * ldl]);
+    if (warp == kl) {
+      const float rd = rdiag;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const int i = lane + 32 * p;
+        if (i > k && i < N) {
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            if (q == kb) {
+              a[p][q] *= rd;
+              col[i] = a[p][q];
+            }
+        }
+      }
     }
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int j = warp + 32 * q;
+      if (j > k && j < N) {
+        const float cj = col[j];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          const int i = lane + 32 * p;
+          if (i >= j && i < N) a[p][q] = fmaf(-col[i], cj, a[p][q]);
+        }
+      }
+    }
   }
-  for (int e = tid; e < N * N; e += blockDim.x) {
-    const int i = e % N, j = e / N;
-    if (i >= j) G[i + (long long)j * ld] = Ls[i + j * ldl];
-  }
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int i = lane + 32 * p, j = warp + 32 * q;
+      if (i < N && j < N && i >= j) {
+        G[i + (long long)j * ld] = a[p][q];
+        Ls[i + j * ldl] = a[p][q];
+      } else if (i < kSmallN && j < kSmallN) {
+        Ls[i + j * ldl] = 0.0f;
+      }
+    }
   if (!rhs) return;
   for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
   __syncthreads();
@@ -391,7 +434,8 @@ __device__ __forceinline__ void prefetch_cols(const float* L, long long ld, int 
 
 __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restrict__ L, long long ld, int N,
                                                           const double* __restrict__ rhs, double* __restrict__ acc,
-                                                          int first, double alpha) {
+                                                          int first, double alpha,
+                                                          const float* __restrict__ Wdiag) {
   extern __shared__ __align__(16) float sm_mid[];
   const int ldb = (N + 3) & ~3;
   float* buf[2] = {sm_mid, sm_mid + 32 * ldb};
@@ -418,11 +462,19 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
       float sum = 0.0f;
       for (int w = 0; w < 32; w++) sum += red[w * 33 + lane];
       float zl = lane < nb ? z[r0 + lane] - sum : 0.0f;
-      const float rinv = lane < nb ? 1.0f / B[32 * (r0 + lane) + lane] : 0.0f;
-      for (int j = 0; j < nb; j++) {
-        const float zj = __shfl_sync(0xffffffffu, zl * rinv, j);
-        if (lane == j) zl = zj;
-        if (lane > j && lane < nb) zl = fmaf(-B[32 * (r0 + j) + lane], zj, zl);
+      if (Wdiag) {
+        // z_I = W_II (b_I - ...): a 32 x 32 product with the stored inverse block
+        const float* W = Wdiag + (long long)I * 1024;
+        float out = 0.0f;
+        for (int t = 0; t < 32; t++) out = fmaf(W[lane * 32 + t], __shfl_sync(0xffffffffu, zl, t), out);
+        zl = out;
+      } else {
+        const float rinv = lane < nb ? 1.0f / B[32 * (r0 + lane) + lane] : 0.0f;
+        for (int j = 0; j < nb; j++) {
+          const float zj = __shfl_sync(0xffffffffu, zl * rinv, j);
+          if (lane == j) zl = zj;
+          if (lane > j && lane < nb) zl = fmaf(-B[32 * (r0 + j) + lane], zj, zl);
+        }
       }
       if (lane < nb) z[r0 + lane] = zl;
     }
@@ -450,11 +502,19 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
       float sum = 0.0f;
       for (int w = 0; w < 32; w++) sum += red[w * 33 + lane];
       float zl = lane < nb ? z[r0 + lane] - sum : 0.0f;
-      const float rinv = lane < nb ? 1.0f / B[lane * ldb + lane] : 0.0f;
-      for (int j = nb - 1; j >= 0; j--) {
-        const float zj = __shfl_sync(0xffffffffu, zl * rinv, j);
-        if (lane == j) zl = zj;
-        if (lane < j) zl = fmaf(-B[lane * ldb + j], zj, zl);
+      if (Wdiag) {
+        // c_I = W_II^T (z_I - ...)
+        const float* W = Wdiag + (long long)I * 1024;
+        float out = 0.0f;
+        for (int t = 0; t < 32; t++) out = fmaf(W[t * 32 + lane], __shfl_sync(0xffffffffu, zl, t), out);
+        zl = out;
+      } else {
+        const float rinv = lane < nb ? 1.0f / B[lane * ldb + lane] : 0.0f;
+        for (int j = nb - 1; j >= 0; j--) {
+          const float zj = __shfl_sync(0xffffffffu, zl * rinv, j);
+          if (lane == j) zl = zj;
+          if (lane < j) zl = fmaf(-B[lane * ldb + j], zj, zl);
+        }
       }
       if (lane < nb) z[r0 + lane] = zl;
     }
@@ -485,8 +545,8 @@ constexpr size_t kClusterSmem = (size_t)(kClusterSlots + kClusterT + 2) * kTileF
 
 __device__ __forceinline__ int tri_index(int i, int j) { return i * (i + 1) / 2 + j; }
 
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
-    k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st) {
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 1)
+    k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag) {
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ float csm[];
@@ -517,45 +577,68 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   cluster.sync();
   for (int k = 0; k < T; k++) {
     const int dkk = tri_index(k, k);
-    // ---- (a) factor the diagonal tile and invert its factor
-    if (dkk % kClusterCTAs == rank) {
+    // ---- (a) factor the diagonal tile and invert the factor: one warp, row r of
+    //      L (then of W = L^{-1}) in lane r's registers, exchanged by shuffles
+    if (dkk % kClusterCTAs == rank && tid < 32) {
       float* D = own + (dkk / kClusterCTAs) * kTileF;
+      const int lane = tid;
+      float row[32];
+#pragma unroll
+      for (int c = 0; c < 32; c++) row[c] = (c <= lane) ? D[lane * 33 + c] : 0.0f;
+      bool bad = false;
+      float rl = 1.0f;  // reciprocal of this lane's diagonal entry of L
+#pragma unroll
       for (int q = 0; q < 32; q++) {
-        if (tid == 0) {
-          float piv = D[q * 33 + q];
-          if (!(piv > 0.0f)) {
-            st->chol_fail = 1;
-            piv = 1.0f;
+        float piv = __shfl_sync(0xffffffffu, row[q], q);
+        if (!(piv > 0.0f)) {
+          bad = true;
+          piv = 1.0f;
+        }
+        const float rq = rsqrtf(piv);
+        if (lane == q) {
+          row[q] = piv * rq;
+          rl = rq;
+        }
+        if (lane > q) row[q] *= rq;
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+          if (c > q) {
+            const float lcq = __shfl_sync(0xffffffffu, row[q], c);
+            if (lane >= c) row[c] = fmaf(-row[q], lcq, row[c]);
           }
-          D[q * 33 + q] = sqrtf(piv);
         }
-        __syncthreads();
-        if (tid > q && tid < 32) D[tid * 33 + q] /= D[q * 33 + q];
-        __syncthreads();
-        for (int e = tid; e < 1024; e += 256) {
-          const int r = e >> 5, c = e & 31;
-          if (c > q && r >= c) D[r * 33 + c] = fmaf(-D[r * 33 + q], D[c * 33 + q], D[r * 33 + c]);
-        }
-        __syncthreads();
       }
-      for (int e = tid; e < 1024; e += 256) {  // clear the strict upper part
-        const int r = e >> 5, c = e & 31;
-        if (c > r) D[r * 33 + c] = 0.0f;
-      }
-      __syncthreads();
-      if (tid < 32) {  // column tid of W = L_kk^{-1} by forward substitution
-        const int j = tid;
-        for (int i = 0; i < 32; i++) winv[i * 33 + j] = 0.0f;
-        winv[j * 33 + j] = 1.0f / D[j * 33 + j];
-        for (int i = j + 1; i < 32; i++) {
-          float acc = 0.0f;
-          for (int t = j; t < i; t++) acc = fmaf(D[i * 33 + t], winv[t * 33 + j], acc);
-          winv[i * 33 + j] = -acc / D[i * 33 + i];
+      if (bad && lane == 0) st->chol_fail = 1;
+#pragma unroll
+      for (int c = 0; c < 32; c++) D[lane * 33 + c] = (c <= lane) ? row[c] : 0.0f;
+      // W = L^{-1}: row l of W from rows t < l (forward substitution across lanes)
+      float w[32];
+#pragma unroll
+      for (int c = 0; c < 32; c++) w[c] = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 32; t++) {
+        // finalise row t of W in lane t, then remove its contribution from rows > t
+        if (lane == t) {
+#pragma unroll
+          for (int c = 0; c < 32; c++) w[c] = (c == t) ? rl : -w[c] * rl;
         }
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+          if (c <= t) {
+            const float wtc = __shfl_sync(0xffffffffu, w[c], t);
+            if (lane > t) w[c] = fmaf(row[t], wtc, w[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 32; c++) winv[lane * 33 + c] = (c <= lane) ? w[c] : 0.0f;
+      if (Wdiag) {  // keep the inverse diagonal blocks for the triangular solves
+#pragma unroll
+        for (int c = 0; c < 32; c++) Wdiag[(long long)k * 1024 + lane * 32 + c] = (c <= lane) ? w[c] : 0.0f;
       }
     }
     cluster.sync();
-    // ---- (b) panel tiles L_ik = A_ik W^T
+    // ---- (b) panel tiles L_ik = A_ik W^T: independent dot products per element
     {
       const float* W = cluster.map_shared_rank(winv, dkk % kClusterCTAs);
       bool have_w = false;
@@ -563,12 +646,15 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
         const int t = tri_index(i, k);
         if (t % kClusterCTAs != rank) continue;
         if (!have_w) {
-          for (int e = tid; e < kTileF; e += 256) tmp[e] = W[e];
+          const float4* s4 = reinterpret_cast<const float4*>(W);
+          float4* d4 = reinterpret_cast<float4*>(tmp);
+          for (int e = tid; e < kTileF / 4; e += 256) d4[e] = s4[e];
           __syncthreads();
           have_w = true;
         }
         float* Ai = own + (t / kClusterCTAs) * kTileF;
         float acc[4] = {0, 0, 0, 0};
+#pragma unroll 8
         for (int q = 0; q < 32; q++) {
           const float a = Ai[r4 * 33 + q];
 #pragma unroll
@@ -586,9 +672,10 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
       // copy panel column k (tiles i = k+1 .. T-1) into local shared memory
       for (int i = k + 1; i < T; i++) {
         const int t = tri_index(i, k);
-        const float* src = cluster.map_shared_rank(own + (t / kClusterCTAs) * kTileF, t % kClusterCTAs);
-        float* dst = panel + i * kTileF;
-        for (int e = tid; e < kTileF; e += 256) dst[e] = src[e];
+        const float4* src =
+            reinterpret_cast<const float4*>(cluster.map_shared_rank(own + (t / kClusterCTAs) * kTileF, t % kClusterCTAs));
+        float4* dst = reinterpret_cast<float4*>(panel + i * kTileF);
+        for (int e = tid; e < kTileF / 4; e += 256) dst[e] = src[e];
       }
       __syncthreads();
       for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
@@ -789,12 +876,12 @@ static void small_smem_attr() {
   if (dev >= 0 && dev < 64) done[dev] = true;
 }
 
-void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
+bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s) {
   if (N <= kSmallN) {
     small_smem_attr();
     count_launch();
     k_chol_small<<<1, kSmallThreads, kSmallSmem, s>>>(G, ldg, N, st, nullptr, nullptr, 1.0);
-    return;
+    return false;
   }
   if (N <= kClusterN) {
     static bool done[64] = {};
@@ -805,8 +892,8 @@ void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    k_chol_cluster<<<kClusterCTAs, 256, kClusterSmem, s>>>(G, ldg, N, st);
-    if (cudaGetLastError() == cudaSuccess) return;
+    k_chol_cluster<<<kClusterCTAs, 256, kClusterSmem, s>>>(G, ldg, N, st, Wdiag);
+    if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
   }
   {
     // one cooperative launch; the grid barrier counters live in DevState
@@ -822,7 +909,7 @@ void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
       unsigned* bar = &st->counters[kCtrBarrier];
       void* args[] = {&G, &ldg, &N, &st, &bar};
       count_launch();
-      if (cudaLaunchCooperativeKernel((void*)k_chol_coop, grid, kCoopThreads, args, 0, s) == cudaSuccess) return;
+      if (cudaLaunchCooperativeKernel((void*)k_chol_coop, grid, kCoopThreads, args, 0, s) == cudaSuccess) return false;
       cudaGetLastError();
     }
   }
@@ -838,6 +925,7 @@ void chol_factor(float* G, long long ldg, int N, DevState* st, cudaStream_t s) {
       k_syrk_update<<<T * (T + 1) / 2, 256, 0, s>>>(G, ldg, kb, nb, N);
     }
   }
+  return false;
 }
 
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
@@ -848,7 +936,7 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 }
 
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
-                     double alpha, cudaStream_t s) {
+                     double alpha, const float* Wdiag, cudaStream_t s) {
   if (N <= 0) return;
   if (N <= kSmallN) {
     small_smem_attr();
@@ -869,7 +957,7 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    k_trsv_mid<<<1, kMidThreads, smem, s>>>(L, ldl, N, rhs, acc, first, alpha);
+    k_trsv_mid<<<1, kMidThreads, smem, s>>>(L, ldl, N, rhs, acc, first, alpha, Wdiag);
     return;
   }
   count_launch();

@@ -187,7 +187,8 @@ def test_newton_direction(m, r):
     rng = np.random.default_rng(m + r)
     n = max(r, 1) + 10
     At = rng.normal(size=(n, m))
-    ctx = pkg.Context(At)
+    # two refinement steps: FP32 factor error (cond * 2^-24) squared twice is below 1e-10
+    ctx = pkg.Context(At, options=pkg.ssnal_en_default_options(refine_steps=2))
     J = np.arange(r, dtype=np.int32)
     g = rng.normal(size=m)
     gd = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -199,6 +200,10 @@ def test_newton_direction(m, r):
     assert st == pkg.OK
     ref = R.newton_direction(At[J], g, kappa)
     np.testing.assert_allclose(d.cpu().numpy(), ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    # the default single refinement step: error about (cond * 2^-24)^2
+    ctx.set_options(pkg.ssnal_en_default_options())
+    pkg.ssnal_en_op_newton(ctx.ctx, r, kappa, dev(g), d)
+    np.testing.assert_allclose(d.cpu().numpy(), ref, rtol=1e-7, atol=1e-7 * np.abs(ref).max())
     ctx.close()
 
 
