@@ -37,6 +37,8 @@ struct ssnal_en_ctx {
   int64_t lda_split = 0;
   const void* A_stream = nullptr;  // what the stream reads (A or Asplit) and its leading dimension
   int64_t lda_stream = 0;
+  alignas(64) unsigned char tmap[128];  // 2-D TMA tensor map over Asplit
+  int tmap_ok = 0;
   int stream_kind = 0;  // kStreamFloatFloat or kStreamDfma (FP64 storage)
   // device workspaces
   DevState* st = nullptr;
@@ -187,6 +189,10 @@ void set_stream_kind(ssnal_en_ctx* c) {
     c->stream_kind = kStreamDfma;
     c->A_stream = c->A;
     c->lda_stream = c->lda;
+  } else if (c->Asplit && c->tmap_ok && c->opt.precision == 0) {
+    c->stream_kind = kStreamLane;
+    c->A_stream = c->Asplit;
+    c->lda_stream = c->lda_split;
   } else if (c->Asplit && c->opt.precision != 3) {
     c->stream_kind = kStreamSplit;
     c->A_stream = c->Asplit;
@@ -260,12 +266,22 @@ ssnal_en_status read_state(ssnal_en_ctx* c) {
   return SSNAL_EN_OK;
 }
 
+// One pass over A with the arithmetic and layout chosen at create time.
+void run_stream(ssnal_en_ctx* c, int mode, const double* vec, double* out, const double* x, const double* u,
+                ProxParams pp) {
+  const ssnal_en_options& o = c->opt;
+  if (c->stream_kind == kStreamLane)
+    launch_stream_lane(mode, c->tmap, (int)c->m, c->n, vec, out, x, u, pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st,
+                       c->partials, c->sms, c->stream);
+  else
+    launch_stream(mode, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, vec, out, x, u, pp, o.mu,
+                  o.beta, o.max_ls, o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
+}
+
 // The A^T d stream of one Newton step, bracketed by CUDA events when profiling.
 ssnal_en_status stream_t(ssnal_en_ctx* c, const double* x, ProxParams pp) {
-  const ssnal_en_options& o = c->opt;
   PhaseTimer timer(c, kPhaseStream);
-  launch_stream(kModeT, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, c->d, c->t, x, c->u, pp, o.mu, o.beta, o.max_ls,
-                o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
+  run_stream(c, kModeT, c->d, c->t, x, c->u, pp);
   if (c->prof) {
     c->prof_launches++;
     const double es = (double)elem_size(c->dtype);
@@ -400,8 +416,7 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
   } else {
     if ((e = prox_gather_grad(c, kProxSupport, x, c->bdev, pp, 0)) != SSNAL_EN_OK) return e;
   }
-  launch_stream(kModeU, c->stream_kind, c->A_stream, c->lda_stream, m, c->n, c->y, c->u, nullptr, nullptr, pp, o.mu, o.beta, o.max_ls,
-                o.ls_fused, c->st, c->partials, c->grid_stream, s);
+  run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
   CK(cudaGetLastError());
   double sigma = o.sigma0;
   int converged = 0, failed = 0;
@@ -603,6 +618,8 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
       c->lda_split = mm;
       launch_presplit((const double*)c->A, c->lda, (int)c->m, c->n, c->Asplit, c->sms, c->stream);
       if (cudaStreamSynchronize(c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
+      c->tmap_ok = (tensor_map_bytes() <= sizeof(c->tmap) &&
+                    make_split_tensor_map(c->tmap, c->Asplit, (int)c->m, c->n)) ? 1 : 0;
     } else {
       cudaGetLastError();
       c->Asplit = nullptr;
@@ -655,12 +672,10 @@ ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, co
     if (!is_finite_d(c_grid[k]) || c_grid[k] < 0) return SSNAL_EN_EINVAL;
   if (out) memset(out, 0, sizeof(ssnal_en_result) * (size_t)K);
   cudaStream_t s = c->stream;
-  const int m = (int)c->m;
   // ||A^T b||_inf from the same stream kernel that later forms u = A^T y
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   ProxParams pp0 = make_pp(c->opt.sigma0, 0.0, 0.0);
-  launch_stream(kModeGmax, c->stream_kind, c->A_stream, c->lda_stream, m, c->n, b, c->t, nullptr, nullptr, pp0, c->opt.mu, c->opt.beta,
-                c->opt.max_ls, c->opt.ls_fused, c->st, c->partials, c->grid_stream, s);
+  run_stream(c, kModeGmax, b, c->t, nullptr, nullptr, pp0);
   CK(cudaGetLastError());
   ssnal_en_status e = read_state(c);
   if (e != SSNAL_EN_OK) return e;
@@ -759,8 +774,7 @@ ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* c, double* phase_ms, int64
 ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* c, const double* y, double* u) {
   if (!c || !y || !u) return SSNAL_EN_EINVAL;
   ProxParams pp = make_pp(1.0, 0.0, 0.0);
-  launch_stream(kModeU, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, y, u, nullptr, nullptr, pp, 0.2, 0.5, 1, 1, c->st,
-                c->partials, c->grid_stream, c->stream);
+  run_stream(c, kModeU, y, u, nullptr, nullptr, pp);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   return SSNAL_EN_OK;

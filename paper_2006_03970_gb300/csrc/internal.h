@@ -64,6 +64,7 @@ enum StreamMode { kModeU = 0, kModeT = 1, kModeGmax = 2 };
 constexpr int kStreamDfma = 0;         // FP64 FMA per element
 constexpr int kStreamFloatFloat = 16;  // float-float on the FP32 pipe (entries 0 or in [2^-100, 2^100])
 constexpr int kStreamSplit = 17;       // same arithmetic on a pre-split float-pair copy of A (packed f32x2)
+constexpr int kStreamLane = 18;        // pre-split copy, lane per column, 2-D TMA tiles (tensor map)
 enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
 
 struct ProxParams {
@@ -124,6 +125,12 @@ void launch_ls_fallback(const double* x, const double* u, const double* t, long 
                         double beta, int max_ls, int fused, DevState* st, double* partials, int grid,
                         cudaStream_t s);
 int stream_grid(int sms);
+// Tensor map (opaque bytes, tensor_map_bytes() of them) over the pre-split copy.
+bool make_split_tensor_map(void* map_out, const void* split, int m, long long n);
+size_t tensor_map_bytes();
+void launch_stream_lane(int mode, const void* map, int m, long long n, const double* vec, double* out,
+                        const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls, int fused,
+                        DevState* st, double* partials, int sms, cudaStream_t s);
 void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s);
 void launch_check_range(const double* A, long long lda, int m, long long n, int* bad, int sms, cudaStream_t s);
 

@@ -8,6 +8,9 @@
 //             after one pass over A; the last block picks the first trial that
 //             satisfies the Armijo condition.
 // One warp per column, grid-stride over columns, y/d staged in shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace ssnal {
@@ -675,6 +678,314 @@ __global__ void k_presplit(const double* __restrict__ A, long long lda, int m, l
 void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s) {
   count_launch();
   k_presplit<<<8 * sms, 256, 0, s>>>(A, lda, m, n, reinterpret_cast<float4*>(S));
+}
+
+// ---------------------------------------------------------------------------
+// Lane-per-column stream over the pre-split float-pair copy of A.
+//
+// Each warp owns groups of 32 consecutive columns; lane l accumulates column
+// (32 g + l) over all rows, so no cross-lane reduction is needed and the
+// per-column epilogue runs on full warps.  Each warp streams its groups through
+// its own ring of shared-memory stages filled by 2-D TMA tensor copies
+// (cp.async.bulk.tensor.2d, box = 16 rows x 32 columns = 4 KB, zero fill past
+// the last row and column).  Lanes read the 8 row pairs of a stage in a
+// staggered order, which keeps the 16-byte shared loads conflict-free.
+// ---------------------------------------------------------------------------
+constexpr int kLWarps = 8;
+constexpr int kLThreads = kLWarps * 32;
+constexpr int kLCols = 64;                   // columns per group: lane l owns columns l and l + 32
+constexpr int kLBoxBytes = kLCols * 128;     // 64 columns x 16 rows x 8 bytes
+
+struct LaneCfg {
+  int stages;        // ring depth per warp
+  int chunks;        // boxes per column group (16 rows each)
+  long long groups;  // column groups of 32
+};
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_constant__ CUtensorMap tmap, int m, long long n,
+                                                              const double* __restrict__ vec, double* __restrict__ out,
+                                                              const double* __restrict__ x,
+                                                              const double* __restrict__ u, LsParams lp, DevState* st,
+                                                              double* __restrict__ partials, LaneCfg cfg) {
+  extern __shared__ __align__(1024) unsigned char smem_lane[];
+  const int mpad = (m + 63) & ~63;
+  unsigned char* ring = smem_lane;  // [kLWarps][stages][kLBoxBytes]
+  float4* D4 = reinterpret_cast<float4*>(smem_lane + (size_t)kLWarps * cfg.stages * kLBoxBytes);
+  float2* DL = reinterpret_cast<float2*>(D4 + mpad / 2);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(DL + mpad / 2);
+  __shared__ double wred[kLWarps][32];
+  __shared__ double red[32];
+  __shared__ unsigned long long dmax_bits;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) {
+    for (int b = 0; b < kLWarps * cfg.stages; b++) mbar_init(smem_u32(bars + b), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    dmax_bits = 0ull;
+  }
+  __syncthreads();
+  // the vector, scaled by a power of two and split: D4[k] = (dh0, dh1, -dh0, -dh1), DL[k] = (-dl0, -dl1)
+  unsigned long long mb = 0ull;
+  for (int i = tid; i < m; i += blockDim.x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(vec[i]) & 0x7FFFFFFFFFFFFFFFull;
+    mb = b > mb ? b : mb;
+  }
+  atomicMax(&dmax_bits, mb);
+  __syncthreads();
+  int ex = (int)((dmax_bits >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) ex = 1023;
+  const double scale = __longlong_as_double((long long)(2046 - ex) << 52);
+  const double unscale = __longlong_as_double((long long)ex << 52);
+  for (int k = tid; k < mpad / 2; k += blockDim.x) {
+    float h[2] = {0.0f, 0.0f}, l[2] = {0.0f, 0.0f};
+    for (int q = 0; q < 2; q++) {
+      const int i = 2 * k + q;
+      if (i < m) {
+        const double v = vec[i] * scale;
+        h[q] = __double2float_rn(v);
+        l[q] = __double2float_rn(v - (double)h[q]);
+      }
+    }
+    D4[k] = make_float4(h[0], h[1], -h[0], -h[1]);
+    DL[k] = make_float2(-l[0], -l[1]);
+  }
+  __syncthreads();
+
+  // ---- work split: the CTA owns column groups g = blockIdx.x + q * gridDim.x;
+  // warp w streams row chunks w, w + 8, ... of each group through its own ring.
+  // Per group, the warps' per-column partials are merged in shared memory.
+  __shared__ float2 part[2][kLWarps][kLCols];
+  const long long ngrp = (long long)blockIdx.x < cfg.groups ? (cfg.groups - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int nw = warp < cfg.chunks ? (cfg.chunks - warp + kLWarps - 1) / kLWarps : 0;  // chunks per group
+  const long long total = ngrp * nw;
+  unsigned char* wring = ring + (size_t)warp * cfg.stages * kLBoxBytes;
+  unsigned long long* wbars = bars + warp * cfg.stages;
+  auto issue = [&](long long item) {
+    const long long q = item / nw;
+    const int ch = warp + kLWarps * (int)(item % nw);
+    const int sidx = (int)(item % cfg.stages);
+    const unsigned bar = smem_u32(wbars + sidx);
+    mbar_expect_tx(bar, kLBoxBytes);
+    tma_load_2d(smem_u32(wring + (size_t)sidx * kLBoxBytes), &tmap, ch * 32,
+                (int)(((long long)blockIdx.x + q * gridDim.x) * kLCols), bar);
+  };
+  if (lane == 0)
+    for (long long it = 0; it < total && it < cfg.stages; it++) issue(it);
+  __syncwarp();
+
+  double s_lane = 1.0;
+  if (MODE == kModeT)
+    for (int k = 0; k < lane; k++) s_lane *= lp.beta;
+  double cand = 0.0, amax = 0.0;
+  bool timed_out = false;
+  long long it = 0;
+  for (long long q = 0; q < ngrp; q++) {
+    unsigned long long S2 = 0ull, L2 = 0ull, S2b = 0ull, L2b = 0ull;
+    for (int k = 0; k < nw && !timed_out; k++, it++) {
+      const int sidx = (int)(it % cfg.stages);
+      if (!mbar_wait(smem_u32(wbars + sidx), (unsigned)((it / cfg.stages) & 1))) {
+        timed_out = true;
+        break;
+      }
+      const int ch = warp + kLWarps * k;
+      const unsigned char* colbase = wring + (size_t)sidx * kLBoxBytes + lane * 128;
+      const ulonglong2* D4p = reinterpret_cast<const ulonglong2*>(D4 + ch * 8);
+      const unsigned long long* DLp = reinterpret_cast<const unsigned long long*>(DL + ch * 8);
+#pragma unroll
+      for (int p = 0; p < 8; p++) {
+        const int pp = (p + lane) & 7;
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(colbase + pp * 16);
+        const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(colbase + 32 * 128 + pp * 16);
+        const ulonglong2 d = D4p[pp];
+        const unsigned long long dl = DLp[pp];
+        ff2_madd(S2, L2, a.x, a.y, d.x, d.y, dl);
+        ff2_madd(S2b, L2b, b.x, b.y, d.x, d.y, dl);
+      }
+      __syncwarp();
+      if (lane == 0 && it + cfg.stages < total) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(it + cfg.stages);
+      }
+    }
+    {
+      float Sq = lo32f(S2), Lq = lo32f(L2);
+      ff_merge(Sq, Lq, hi32f(S2), hi32f(L2));
+      part[q & 1][warp][lane] = make_float2(Sq, Lq);
+      float Sb = lo32f(S2b), Lb = lo32f(L2b);
+      ff_merge(Sb, Lb, hi32f(S2b), hi32f(L2b));
+      part[q & 1][warp][lane + 32] = make_float2(Sb, Lb);
+    }
+    __syncthreads();
+    if (warp < 2) {
+      // warps 0 and 1 merge the partials of columns lane and lane + 32 in a fixed
+      // order, then run the column epilogue
+      const int cc = lane + 32 * warp;
+      float Sm = part[q & 1][0][cc].x, Lm = part[q & 1][0][cc].y;
+      for (int w = 1; w < kLWarps; w++) ff_merge(Sm, Lm, part[q & 1][w][cc].x, part[q & 1][w][cc].y);
+      const long long j = ((long long)blockIdx.x + q * gridDim.x) * kLCols + cc;
+      const bool mine = j < n;
+      const double t = ((double)Sm + (double)Lm) * unscale;
+      if (mine) out[j] = t;
+      if (MODE == kModeGmax && mine) amax = fmax(amax, fabs(t));
+      if (MODE == kModeT) {
+        double v = 0.0;
+        bool live = false;
+        if (mine) {
+          v = v_of(x[j], u[j], lp.pp.sigma);
+          live = !trial_skip(v, t, lp.pp);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, live);
+        while (mask) {
+          const int qq = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const double bv = __shfl_sync(0xffffffffu, v, qq);
+          const double bt = __shfl_sync(0xffffffffu, t, qq);
+          if (lane < lp.fused) cand += trial_term(bv, bt, s_lane, lp.pp);
+        }
+      }
+    }
+  }
+  if (timed_out) {
+    st->timeout = 1;
+    if (lane == 0)  // let this warp's copies in flight land before the block exits
+      for (long long k = it; k < total && k < it + cfg.stages; k++)
+        mbar_wait(smem_u32(wbars + (int)(k % cfg.stages)), (unsigned)((k / cfg.stages) & 1));
+    __syncwarp();
+  }
+  wred[warp][lane] = (MODE == kModeGmax) ? amax : cand;
+  __syncthreads();
+  if (MODE == kModeU) return;
+  if (MODE == kModeGmax) {
+    double mx = 0.0;
+    if (warp == 0)
+      for (int w = 0; w < kLWarps; w++) mx = fmax(mx, wred[w][lane]);
+    mx = block_max(warp == 0 ? mx : 0.0, red);
+    if (tid == 0) partials[blockIdx.x] = mx;
+    if (!last_block(&st->counters[kCtrGmax])) return;
+    double g = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) g = fmax(g, ld_cg(&partials[b]));
+    g = block_max(g, red);
+    if (tid == 0) st->gmax = g;
+    reset_counter(&st->counters[kCtrGmax]);
+    return;
+  }
+  if (warp == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < kLWarps; w++) sum += wred[w][lane];
+    partials[(long long)blockIdx.x * 32 + lane] = sum;
+  }
+  if (!last_block(&st->counters[kCtrStream])) return;
+  if (warp == 0) {
+    double sum = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) sum += ld_cg(&partials[(long long)b * 32 + lane]);
+    if (lane < lp.fused) st->lsdiff[lane] = sum;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence_block();
+    double sel;
+    int k = armijo_select(st, lp, 0, lp.fused, sel);
+    if (k >= 0) {
+      st->s = sel;
+      st->ls_k = k;
+      st->ls_state = 0;
+    } else if (lp.fused < lp.max_ls) {
+      st->ls_state = 1;
+    } else {
+      st->s = sel;
+      st->ls_k = lp.max_ls - 1;
+      st->ls_state = 0;
+    }
+  }
+  reset_counter(&st->counters[kCtrStream]);
+}
+
+constexpr size_t kLDynMax = 232448 - 12288;  // per-block limit minus the kernel's static shared memory
+
+static size_t lane_smem(int m, int stages) {
+  const int mpad = (m + 63) & ~63;
+  return (size_t)kLWarps * stages * kLBoxBytes + (size_t)mpad * 12 + (size_t)kLWarps * stages * 8 + 1024;
+}
+
+static int lane_stages(int m) {
+  const size_t budget = kLDynMax;  // dynamic shared memory left beside the static part
+  const int mpad = (m + 63) & ~63;
+  int st = (int)((budget - (size_t)mpad * 12 - 1024) / ((size_t)kLWarps * kLBoxBytes + kLWarps * 8));
+  if (st > 8) st = 8;
+  return st;
+}
+
+// Tensor map over the pre-split copy: 2-D, inner dimension = the 2 mm floats of
+// one column, outer = the n columns; boxes of 32 floats x 32 columns.
+bool make_split_tensor_map(void* map_out, const void* split, int m, long long n) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const long long mm = (m + 1) & ~1;
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * mm), (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(2 * mm * sizeof(float))};
+  cuuint32_t box[2] = {32, (cuuint32_t)kLCols};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<void*>(split), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+template <int MODE>
+static void launch_lane(const void* map, int m, long long n, const double* vec, double* out, const double* x,
+                        const double* u, LsParams lp, DevState* st, double* partials, int sms, cudaStream_t s) {
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int stages = lane_stages(m);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    cudaFuncSetAttribute(k_stream_lane<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLDynMax);
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  LaneCfg cfg;
+  cfg.stages = stages;
+  cfg.chunks = (((m + 1) & ~1) + 15) / 16;
+  cfg.groups = (n + kLCols - 1) / kLCols;
+  long long grid = cfg.groups;
+  if (grid > sms) grid = sms;
+  if (grid < 1) grid = 1;
+  const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(map);
+  k_stream_lane<MODE><<<(int)grid, kLThreads, lane_smem(m, stages), s>>>(*tm, m, n, vec, out, x, u, lp, st, partials,
+                                                                         cfg);
+}
+
+void launch_stream_lane(int mode, const void* map, int m, long long n, const double* vec, double* out,
+                        const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls, int fused,
+                        DevState* st, double* partials, int sms, cudaStream_t s) {
+  LsParams lp{pp, mu, beta, max_ls, fused};
+  count_launch();
+  if (mode == kModeU)
+    launch_lane<kModeU>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+  else if (mode == kModeT)
+    launch_lane<kModeT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+  else
+    launch_lane<kModeGmax>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
 }
 
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,
