@@ -88,7 +88,8 @@ typedef struct {
   int32_t use_y0;       /* 0: y0 = A x0 - b; 1: take y0 from the y argument of ssnal_en_solve */
   int32_t ls_fused;     /* 16: trial steps evaluated inside the A^T d pass (1..16); later trials
                            are evaluated by a pass over the stored n-vectors only */
-  int32_t reserved0;
+  int32_t syrk_tc;      /* 1: Newton-matrix SYRK on the tensor cores (tcgen05, BF16 operands, FP32
+                           accumulation; FP64 panels as a three-way BF16 split); 0: FP32 FMA */
   int64_t max_active;   /* 0: path stops after the first point with at least this many nonzeros (0 = never) */
 } ssnal_en_options;
 

@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
                 ("mu", ctypes.c_double), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_al", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("max_ls", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32), ("use_y0", ctypes.c_int32),
-                ("ls_fused", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("max_active", ctypes.c_int64)]
+                ("ls_fused", ctypes.c_int32), ("syrk_tc", ctypes.c_int32), ("max_active", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):

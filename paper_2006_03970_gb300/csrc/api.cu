@@ -62,6 +62,8 @@ struct ssnal_en_ctx {
   float* G = nullptr;
   int64_t ldg = 0;
   float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
+  void* Xtc = nullptr;     // BF16 split panels of the tensor-core SYRK (capacity rcap)
+  float* tc_part = nullptr;
   double* Xdev = nullptr;  // path_host output staging
   int64_t Xcap = 0;
   // event timing of the A^T d stream kernel (ssnal_en_profile)
@@ -124,8 +126,10 @@ ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
   dev_free(c->h);
   dev_free(c->q);
   dev_free(c->resr);
+  dev_free(c->Xtc);
   c->P = nullptr;
   c->P32 = nullptr;
+  c->Xtc = nullptr;
   c->h = c->q = c->resr = nullptr;
   c->rcap = 0;
   ssnal_en_status s;
@@ -134,6 +138,14 @@ ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
   if ((s = dev_alloc(&c->h, (size_t)cap)) != SSNAL_EN_OK) return s;
   if ((s = dev_alloc(&c->q, (size_t)cap)) != SSNAL_EN_OK) return s;
   if ((s = dev_alloc(&c->resr, (size_t)cap)) != SSNAL_EN_OK) return s;
+  {
+    // both orientations fit in 3 x m x round_up(max(m, cap), 64) BF16 entries
+    const int64_t big = c->m > cap ? c->m : cap;
+    const size_t elems = 3 * (size_t)c->m * (size_t)((big + 63) / 64 * 64);
+    unsigned short* xt = nullptr;
+    if ((s = dev_alloc(&xt, elems)) != SSNAL_EN_OK) return s;
+    c->Xtc = xt;
+  }
   c->rcap = cap;
   return SSNAL_EN_OK;
 }
@@ -177,6 +189,8 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->P32);
   dev_free(c->G);
   dev_free(c->Wdiag);
+  dev_free(c->Xtc);
+  dev_free(c->tc_part);
   dev_free(c->Xdev);
   dev_free(c->Asplit);
 }
@@ -351,7 +365,11 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
   } else if (r < m) {
     // SMW (eq. smw_formula): G = kappa^{-1} I + A_J^T A_J, h = A_J^T g, q = G^{-1} h, d = A_J q - g
     const int N = (int)r;
-    launch_syrk_tn(c->P32, c->ldp32, m, r, 1.0 / kappa, c->G, c->ldg, s);
+    if (c->opt.syrk_tc)
+      launch_syrk_tc(c->P, c->ldp, m, (int)r, 0, 3, c->Xtc, c->tc_part, 1.0f, (float)(1.0 / kappa), c->G, c->ldg,
+                     c->st, c->sms, s);
+    else
+      launch_syrk_tn(c->P32, c->ldp32, m, r, 1.0 / kappa, c->G, c->ldg, s);
     launch_gemv_t(c->P, c->ldp, m, r, g, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
     if (N <= kSmallNewton) {
       launch_chol_solve_small(c->G, c->ldg, N, c->st, c->h, c->q, 1.0, s);
@@ -370,7 +388,11 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
                   c->comb_scratch, c->cpart, c->tile_ctr, s);
   } else {
     // m x m form (eq. AJ_system): M = I + kappa A_J A_J^T, d = -M^{-1} g
-    launch_syrk_nt(c->P32, c->ldp32, m, r, kappa, c->G, c->ldg, s);
+    if (c->opt.syrk_tc)
+      launch_syrk_tc(c->P, c->ldp, m, (int)r, 1, 3, c->Xtc, c->tc_part, (float)kappa, 1.0f, c->G, c->ldg, c->st,
+                     c->sms, s);
+    else
+      launch_syrk_nt(c->P32, c->ldp32, m, r, kappa, c->G, c->ldg, s);
     if (m <= kSmallNewton) {
       launch_chol_solve_small(c->G, c->ldg, m, c->st, g, d, -1.0, s);
     } else {
@@ -490,6 +512,7 @@ ssnal_en_status check_options(const ssnal_en_options* o) {
   if (o->ls_fused < 1 || o->ls_fused > kFusedLS) return SSNAL_EN_EINVAL;
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->max_active < 0) return SSNAL_EN_EINVAL;
   if (o->precision < 0 || o->precision > 3) return SSNAL_EN_EINVAL;
+  if (o->syrk_tc < 0 || o->syrk_tc > 1) return SSNAL_EN_EINVAL;
   return SSNAL_EN_OK;
 }
 
@@ -513,6 +536,7 @@ void ssnal_en_default_options(ssnal_en_options* o) {
   o->refine_steps = 1;
   o->use_y0 = 0;
   o->ls_fused = kFusedLS;
+  o->syrk_tc = 1;
   o->max_active = 0;
 }
 
@@ -595,6 +619,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->tile_ctr, (m + 31) / 32);
   AL(c->G, c->ldg * m);
   AL(c->Wdiag, (size_t)((m + 31) / 32) * 1024);
+  AL(c->tc_part, syrk_tc_part_floats(c->sms));
 #undef AL
   if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) s = SSNAL_EN_ENOMEM;
   if (s == SSNAL_EN_OK) s = grow_panel(c, m < n ? m : n);

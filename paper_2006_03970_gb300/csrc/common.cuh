@@ -105,4 +105,36 @@ __device__ __forceinline__ bool is_active(double v, const ProxParams& pp) { retu
 // rounding sequence as the plain elementwise evaluation of the definition.
 __device__ __forceinline__ double v_of(double x, double u, double sigma) { return __dsub_rn(x, __dmul_rn(sigma, u)); }
 
+// ---- mbarrier helpers.  Every wait is bounded: it gives up after about two
+// seconds of SM clock (or kSpinLimit rounds), so a protocol error cannot hang
+// the GPU; the caller raises DevState::timeout and leaves.
+constexpr unsigned kSpinLimit = 1u << 28;          // try_wait rounds
+constexpr long long kWaitCycles = 4000000000LL;    // about 2 s of SM clock
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Bounded wait for the phase with the given parity; false on a timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (unsigned it = 0; it < kSpinLimit; it++) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitCycles) break;
+  }
+  return false;
+}
 }  // namespace ssnal

@@ -117,6 +117,12 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, cudaStream_t s);
 
+// ---- tensor-core SYRK (kern_tc.cu)
+size_t syrk_tc_panel_elems(int R, int K, int nsplit);
+size_t syrk_tc_part_floats(int sms);
+void launch_syrk_tc(const double* P, long long ldp, int m, int r, int trans, int nsplit, void* Xbuf, float* part,
+                    float alpha, float beta, float* out, long long ldo, DevState* st, int sms, cudaStream_t s);
+
 // ---- streams over A (kern_stream.cu)
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,
                    double* out, const double* x, const double* u, ProxParams pp, double mu, double beta,

@@ -529,19 +529,35 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
 // Cluster tile Cholesky (kSmallN < N <= kClusterN).  The lower triangle is cut
 // into 32x32 tiles; tile (i, j), i >= j, with linear index i(i+1)/2 + j lives in
 // the shared memory of CTA (index mod kClusterCTAs) of one thread-block cluster.
-// Step k: the owner of (k, k) factors it and inverts the factor; after a
-// cluster barrier the owners of the panel tiles (i, k) form L_ik = A_ik L_kk^{-T};
-// after a second barrier every CTA copies the panel column through distributed
-// shared memory and updates its own trailing tiles A_ij -= L_ik L_jk^T; a third
-// barrier closes the step.  Rows and columns beyond N are padded with the
-// identity, so the factor of the padded matrix is L plus an identity block.
+// Step k: (a) the owner of (k, k) factors it and inverts the factor in one warp;
+// after a cluster barrier (b) the owners of the panel tiles (i, k) form
+// L_ik = A_ik L_kk^{-T} and push each finished tile into the panel buffer of
+// every CTA with a bulk shared-to-shared copy that completes on the receiver's
+// mbarrier; (c) each CTA waits for its panel and updates its own trailing tiles
+// A_ij -= L_ik L_jk^T; a cluster barrier closes the step (the panel buffers are
+// reused).  Rows and columns beyond N are padded with the identity, so the
+// factor of the padded matrix is L plus an identity block.
 namespace cgx = cooperative_groups;
 constexpr int kClusterCTAs = 8;
 constexpr int kClusterN = 640;
 constexpr int kClusterT = kClusterN / 32;                                   // 20 tiles per side
 constexpr int kTileF = 32 * 33;                                              // floats per padded tile
 constexpr int kClusterSlots = (kClusterT * (kClusterT + 1) / 2 + kClusterCTAs - 1) / kClusterCTAs;  // 27
-constexpr size_t kClusterSmem = (size_t)(kClusterSlots + kClusterT + 2) * kTileF * sizeof(float);
+constexpr unsigned kTileBytes = kTileF * sizeof(float);                      // 4224, a multiple of 16
+constexpr size_t kClusterSmem = (size_t)(kClusterSlots + kClusterT + 2) * kTileBytes + 16;  // + the mbarrier
+
+__device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// bulk copy of `bytes` from this CTA's shared memory to (possibly) another
+// CTA's, completing `bytes` on that CTA's mbarrier
+__device__ __forceinline__ void bulk_s2c(unsigned dst, unsigned src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "r"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
 
 __device__ __forceinline__ int tri_index(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -556,7 +572,6 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 1)
   float* tmp = winv + kTileF;                        // scratch tile
   const int tid = threadIdx.x;
   const int T = (N + 31) / 32;
-  const int r4 = tid >> 3, c4 = (tid & 7) * 4;       // 4 elements per thread: row r4, columns c4..c4+3
 
   // ---- load the owned tiles (identity padding beyond N)
   for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
@@ -574,19 +589,33 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 1)
       dst[r * 33 + c] = v;
     }
   }
+  unsigned long long* pbar = reinterpret_cast<unsigned long long*>(tmp + kTileF);  // panel arrivals
+  if (tid == 0) {
+    mbar_init(smem_u32(pbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   cluster.sync();
+  bool ok = true;
   for (int k = 0; k < T; k++) {
     const int dkk = tri_index(k, k);
-    // ---- (a) factor the diagonal tile and invert the factor: one warp, row r of
-    //      L (then of W = L^{-1}) in lane r's registers, exchanged by shuffles
+    const int npanel = T - k - 1;
+    // this CTA's panel buffer receives tiles k+1 .. T-1 in this step; arm the
+    // barrier before the cluster barrier below, i.e. before any copy is issued
+    if (tid == 0 && npanel > 0) mbar_expect_tx(smem_u32(pbar), (unsigned)npanel * kTileBytes);
+    // ---- (a) factor the diagonal tile and invert the factor in one warp.  Lane l
+    //      holds row l of the tile (then of L) and row l of the running
+    //      forward substitution for W = L^{-1}; step q publishes column q of L and
+    //      row q of W through two small shared buffers.
     if (dkk % kClusterCTAs == rank && tid < 32) {
       float* D = own + (dkk / kClusterCTAs) * kTileF;
       const int lane = tid;
-      float row[32];
+      float row[32], acc[32];
 #pragma unroll
-      for (int c = 0; c < 32; c++) row[c] = (c <= lane) ? D[lane * 33 + c] : 0.0f;
+      for (int c = 0; c < 32; c++) {
+        row[c] = (c <= lane) ? D[lane * 33 + c] : 0.0f;
+        acc[c] = (c == lane) ? 1.0f : 0.0f;
+      }
       bool bad = false;
-      float rl = 1.0f;  // reciprocal of this lane's diagonal entry of L
 #pragma unroll
       for (int q = 0; q < 32; q++) {
         float piv = __shfl_sync(0xffffffffu, row[q], q);
@@ -595,108 +624,142 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 1)
           piv = 1.0f;
         }
         const float rq = rsqrtf(piv);
+        row[q] = (lane == q) ? piv * rq : row[q] * rq;  // L_lq (zero above the diagonal)
+        float* cb = tmp + (q & 1) * 32;                 // column q of L
+        float* wb = tmp + 64 + (q & 1) * 32;            // row q of W
+        cb[lane] = row[q];
         if (lane == q) {
-          row[q] = piv * rq;
-          rl = rq;
-        }
-        if (lane > q) row[q] *= rq;
 #pragma unroll
-        for (int c = 0; c < 32; c++) {
-          if (c > q) {
-            const float lcq = __shfl_sync(0xffffffffu, row[q], c);
-            if (lane >= c) row[c] = fmaf(-row[q], lcq, row[c]);
+          for (int c = 0; c < 32; c++) acc[c] *= rq;  // W_q = (e_q - sum_{t<q} L_qt W_t) / L_qq
+#pragma unroll
+          for (int g = 0; g < 8; g++)
+            reinterpret_cast<float4*>(wb)[g] = make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
+        }
+        __syncwarp();
+        const float lq = row[q];
+#pragma unroll
+        for (int g = 0; g < 8; g++) {
+          if (4 * g + 3 > q) {  // A_lc -= L_lq L_cq, q < c <= l
+            const float4 v = reinterpret_cast<const float4*>(cb)[g];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const int c = 4 * g + e;
+              if (c > q) row[c] = (lane >= c) ? fmaf(-lq, vv[e], row[c]) : row[c];
+            }
+          }
+        }
+        const float lw = (lane > q) ? lq : 0.0f;
+#pragma unroll
+        for (int g = 0; g < 8; g++) {
+          if (4 * g <= q) {  // rows below q: acc_l -= L_lq W_q
+            const float4 v = reinterpret_cast<const float4*>(wb)[g];
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+              if (4 * g + e <= q) acc[4 * g + e] = fmaf(-lw, vv[e], acc[4 * g + e]);
           }
         }
       }
       if (bad && lane == 0) st->chol_fail = 1;
 #pragma unroll
-      for (int c = 0; c < 32; c++) D[lane * 33 + c] = (c <= lane) ? row[c] : 0.0f;
-      // W = L^{-1}: row l of W from rows t < l (forward substitution across lanes)
-      float w[32];
+      for (int c = 0; c < 32; c++) {
+        D[lane * 33 + c] = (c <= lane) ? row[c] : 0.0f;
+        winv[lane * 33 + c] = (c <= lane) ? acc[c] : 0.0f;
+      }
+      __syncwarp();
+      if (Wdiag)  // keep the inverse diagonal blocks for the triangular solves
+        for (int e = lane; e < 1024; e += 32) Wdiag[(long long)k * 1024 + e] = winv[(e >> 5) * 33 + (e & 31)];
+    }
+    cluster.sync();
+    // ---- (b) panel tiles L_ik = A_ik W^T: four tiles at a time, 64 threads per
+    //      tile, a 4 x 4 register block per thread; each finished tile is pushed
+    //      to slot i of every CTA's panel buffer
+    {
+      int mine = 0;
+      for (int i = k + 1; i < T; i++)
+        if (tri_index(i, k) % kClusterCTAs == rank) mine++;
+      if (mine > 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(cluster.map_shared_rank(winv, dkk % kClusterCTAs));
+        float4* d4 = reinterpret_cast<float4*>(tmp);
+        for (int e = tid; e < kTileF / 4; e += 256) d4[e] = s4[e];
+        __syncthreads();
+        const int grp = tid >> 6, gt = tid & 63, tr = gt >> 3, tc = gt & 7;
+        int seen = 0;
+        for (int i = k + 1; i < T; i++) {
+          const int t = tri_index(i, k);
+          if (t % kClusterCTAs != rank) continue;
+          if ((seen++ & 3) != grp) continue;
+          float* Ai = own + (t / kClusterCTAs) * kTileF;
+          float acc[4][4] = {};
+#pragma unroll 4
+          for (int q = 0; q < 32; q++) {
+            float a[4], w[4];
 #pragma unroll
-      for (int c = 0; c < 32; c++) w[c] = 0.0f;
+            for (int u = 0; u < 4; u++) {
+              a[u] = Ai[(4 * tr + u) * 33 + q];
+              w[u] = tmp[(4 * tc + u) * 33 + q];
+            }
 #pragma unroll
-      for (int t = 0; t < 32; t++) {
-        // finalise row t of W in lane t, then remove its contribution from rows > t
-        if (lane == t) {
+            for (int u = 0; u < 4; u++)
 #pragma unroll
-          for (int c = 0; c < 32; c++) w[c] = (c == t) ? rl : -w[c] * rl;
-        }
+              for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], w[v], acc[u][v]);
+          }
+          // the 64 threads of this tile finish reading A_ik before it is overwritten
+          asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory");
 #pragma unroll
-        for (int c = 0; c < 32; c++) {
-          if (c <= t) {
-            const float wtc = __shfl_sync(0xffffffffu, w[c], t);
-            if (lane > t) w[c] = fmaf(row[t], wtc, w[c]);
+          for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) Ai[(4 * tr + u) * 33 + 4 * tc + v] = acc[u][v];
+          // make the writes visible to the copy engine, then one thread pushes the tile
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory");
+          if (gt == 0) {
+            const unsigned src = smem_u32(Ai), dst = smem_u32(panel + i * kTileF), bar = smem_u32(pbar);
+#pragma unroll 1
+            for (int r = 0; r < kClusterCTAs; r++)
+              bulk_s2c(cluster_addr(dst, r), src, kTileBytes, cluster_addr(bar, r));
           }
         }
       }
-#pragma unroll
-      for (int c = 0; c < 32; c++) winv[lane * 33 + c] = (c <= lane) ? w[c] : 0.0f;
-      if (Wdiag) {  // keep the inverse diagonal blocks for the triangular solves
-#pragma unroll
-        for (int c = 0; c < 32; c++) Wdiag[(long long)k * 1024 + lane * 32 + c] = (c <= lane) ? w[c] : 0.0f;
-      }
     }
-    cluster.sync();
-    // ---- (b) panel tiles L_ik = A_ik W^T: independent dot products per element
-    {
-      const float* W = cluster.map_shared_rank(winv, dkk % kClusterCTAs);
-      bool have_w = false;
-      for (int i = k + 1; i < T; i++) {
-        const int t = tri_index(i, k);
-        if (t % kClusterCTAs != rank) continue;
-        if (!have_w) {
-          const float4* s4 = reinterpret_cast<const float4*>(W);
-          float4* d4 = reinterpret_cast<float4*>(tmp);
-          for (int e = tid; e < kTileF / 4; e += 256) d4[e] = s4[e];
-          __syncthreads();
-          have_w = true;
-        }
-        float* Ai = own + (t / kClusterCTAs) * kTileF;
-        float acc[4] = {0, 0, 0, 0};
-#pragma unroll 8
-        for (int q = 0; q < 32; q++) {
-          const float a = Ai[r4 * 33 + q];
-#pragma unroll
-          for (int e = 0; e < 4; e++) acc[e] = fmaf(a, tmp[(c4 + e) * 33 + q], acc[e]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < 4; e++) Ai[r4 * 33 + c4 + e] = acc[e];
-        __syncthreads();
-      }
-    }
-    cluster.sync();
     // ---- (c) trailing update of the owned tiles (i, j), k < j <= i
-    {
-      // copy panel column k (tiles i = k+1 .. T-1) into local shared memory
-      for (int i = k + 1; i < T; i++) {
-        const int t = tri_index(i, k);
-        const float4* src =
-            reinterpret_cast<const float4*>(cluster.map_shared_rank(own + (t / kClusterCTAs) * kTileF, t % kClusterCTAs));
-        float4* dst = reinterpret_cast<float4*>(panel + i * kTileF);
-        for (int e = tid; e < kTileF / 4; e += 256) dst[e] = src[e];
-      }
-      __syncthreads();
-      for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
+    if (npanel > 0) {
+      if (ok && !mbar_wait(smem_u32(pbar), (unsigned)(k & 1))) ok = false;
+      // four tiles at a time, 64 threads per tile, a 4 x 4 register block per thread
+      const int grp = tid >> 6, gt = tid & 63, tr = gt >> 3, tc = gt & 7;
+      int seen = 0;
+      for (int t = rank; t < T * (T + 1) / 2 && ok; t += kClusterCTAs) {
         int ti, tj;
         tri_tile(t, ti, tj);
         if (tj <= k) continue;
+        if ((seen++ & 3) != grp) continue;
         float* C = own + (t / kClusterCTAs) * kTileF;
         const float* Li = panel + ti * kTileF;
         const float* Lj = panel + tj * kTileF;
-        float acc[4] = {0, 0, 0, 0};
+        float acc[4][4] = {};
+#pragma unroll 4
         for (int q = 0; q < 32; q++) {
-          const float a = Li[r4 * 33 + q];
+          float a[4], b[4];
 #pragma unroll
-          for (int e = 0; e < 4; e++) acc[e] = fmaf(a, Lj[(c4 + e) * 33 + q], acc[e]);
+          for (int u = 0; u < 4; u++) {
+            a[u] = Li[(4 * tr + u) * 33 + q];
+            b[u] = Lj[(4 * tc + u) * 33 + q];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+#pragma unroll
+            for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
         }
 #pragma unroll
-        for (int e = 0; e < 4; e++) C[r4 * 33 + c4 + e] -= acc[e];
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int v = 0; v < 4; v++) C[(4 * tr + u) * 33 + 4 * tc + v] -= acc[u][v];
       }
     }
     cluster.sync();
   }
+  if (!ok) st->timeout = 1;
   // ---- write the factor back (lower part, inside N)
   for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
     int ti, tj;

@@ -218,8 +218,6 @@ constexpr int kFFConsumers = 8;
 constexpr int kFFThreads = (kFFConsumers + 1) * 32;
 constexpr int kFFStages = 4;
 constexpr int kFFStageBytes = 40 * 1024;
-constexpr unsigned kSpinLimit = 1u << 28;          // try_wait rounds
-constexpr long long kWaitCycles = 4000000000LL;    // about 2 s of SM clock
 
 struct FFCfg {
   int cpw;          // columns per consumer warp in a tile
@@ -230,33 +228,6 @@ struct FFCfg {
   long long ntiles;
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-// Bounded wait for the phase with the given parity; false after about two
-// seconds (or kSpinLimit rounds), so a protocol error cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  const long long t0 = clock64();
-  for (unsigned it = 0; it < kSpinLimit; it++) {
-    unsigned ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > kWaitCycles) break;
-  }
-  return false;
-}
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
   asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)

@@ -180,15 +180,18 @@ def test_grad_gather(m, n, r):
 
 
 # ---------------------------------------------------------------- a5 + a6: Newton system
+@pytest.mark.parametrize("syrk_tc", [1, 0])
 @pytest.mark.parametrize("m,r", [(30, 0), (30, 1), (30, 29), (30, 30), (30, 31), (100, 250), (257, 65),
                                  (500, 120), (128, 129), (129, 300), (300, 200), (200, 400), (700, 600),
                                  (1000, 999)])
-def test_newton_direction(m, r):
+def test_newton_direction(m, r, syrk_tc):
+    # syrk_tc = 1: Newton matrix on the tensor cores (three-way BF16 split, FP32 accumulation);
+    # 0: FP32 FMA.  Both feed an FP32 factor refined through the FP64 panel.
     rng = np.random.default_rng(m + r)
     n = max(r, 1) + 10
     At = rng.normal(size=(n, m))
     # two refinement steps: FP32 factor error (cond * 2^-24) squared twice is below 1e-10
-    ctx = pkg.Context(At, options=pkg.ssnal_en_default_options(refine_steps=2))
+    ctx = pkg.Context(At, options=pkg.ssnal_en_default_options(refine_steps=2, syrk_tc=syrk_tc))
     J = np.arange(r, dtype=np.int32)
     g = rng.normal(size=m)
     gd = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -201,7 +204,7 @@ def test_newton_direction(m, r):
     ref = R.newton_direction(At[J], g, kappa)
     np.testing.assert_allclose(d.cpu().numpy(), ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
     # the default single refinement step: error about (cond * 2^-24)^2
-    ctx.set_options(pkg.ssnal_en_default_options())
+    ctx.set_options(pkg.ssnal_en_default_options(syrk_tc=syrk_tc))
     pkg.ssnal_en_op_newton(ctx.ctx, r, kappa, dev(g), d)
     np.testing.assert_allclose(d.cpu().numpy(), ref, rtol=1e-7, atol=1e-7 * np.abs(ref).max())
     ctx.close()
