@@ -227,6 +227,7 @@ ProxParams make_pp(double sigma, double lam1, double lam2) {
   pp.lam2 = lam2;
   pp.thr = sigma * lam1;
   pp.onep = 1.0 + sigma * lam2;
+  pp.inv_onep = 1.0 / pp.onep;
   return pp;
 }
 

@@ -105,6 +105,44 @@ __device__ __forceinline__ bool is_active(double v, const ProxParams& pp) { retu
 // rounding sequence as the plain elementwise evaluation of the definition.
 __device__ __forceinline__ double v_of(double x, double u, double sigma) { return __dsub_rn(x, __dmul_rn(sigma, u)); }
 
+// Sum p[0], p[stride], ..., p[(count-1) stride] in index order (the same
+// association as a plain loop), with B loads in flight at a time: partial
+// results written by other blocks are read at L2 latency, so a serial chain of
+// dependent round trips would dominate a reduction tail.
+template <int B = 8>
+__device__ __forceinline__ double ordered_sum_cg(const double* p, long long stride, int count) {
+  double s = 0.0;
+  int b = 0;
+  for (; b + B <= count; b += B) {
+    double v[B];
+#pragma unroll
+    for (int e = 0; e < B; e++) v[e] = ld_cg(p + (long long)(b + e) * stride);
+#pragma unroll
+    for (int e = 0; e < B; e++) s += v[e];
+  }
+  for (; b < count; b++) s += ld_cg(p + (long long)b * stride);
+  return s;
+}
+
+// Lane-wise sum of the 32-wide rows 0..nb-1 of P (row b at P + 32 b) with every
+// warp of the block: warp w adds its contiguous share of rows in order, then
+// warp 0 adds the warps' results in order (a fixed order for a given block
+// size).  Every thread must call it; the result is valid in warp 0.
+// scratch: (blockDim.x / 32) x 32 doubles of shared memory.
+__device__ __forceinline__ double rows_sum32(const double* P, int nb, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = (nb + nw - 1) / nw;
+  const int b0 = min(nb, warp * per), b1 = min(nb, b0 + per);
+  const double s = ordered_sum_cg(P + (long long)b0 * 32 + lane, 32, b1 - b0);
+  __syncthreads();
+  scratch[warp * 32 + lane] = s;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0)
+    for (int w = 0; w < nw; w++) t += scratch[w * 32 + lane];
+  return t;
+}
+
 // ---- mbarrier helpers.  Every wait is bounded: it gives up after about two
 // seconds of SM clock (or kSpinLimit rounds), so a protocol error cannot hang
 // the GPU; the caller raises DevState::timeout and leaves.

@@ -69,6 +69,7 @@ enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
 
 struct ProxParams {
   double sigma, lam1, lam2, thr, onep;  // thr = sigma*lam1, onep = 1 + sigma*lam2
+  double inv_onep;                      // 1 / onep, for values that only feed norms
 };
 
 // ---- launch wrappers (kern_vec.cu)

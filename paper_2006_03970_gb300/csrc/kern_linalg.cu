@@ -529,22 +529,45 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
 // Cluster tile Cholesky (kSmallN < N <= kClusterN).  The lower triangle is cut
 // into 32x32 tiles; tile (i, j), i >= j, with linear index i(i+1)/2 + j lives in
 // the shared memory of CTA (index mod kClusterCTAs) of one thread-block cluster.
-// Step k: (a) the owner of (k, k) factors it and inverts the factor in one warp;
-// after a cluster barrier (b) the owners of the panel tiles (i, k) form
-// L_ik = A_ik L_kk^{-T} and push each finished tile into the panel buffer of
-// every CTA with a bulk shared-to-shared copy that completes on the receiver's
-// mbarrier; (c) each CTA waits for its panel and updates its own trailing tiles
-// A_ij -= L_ik L_jk^T; a cluster barrier closes the step (the panel buffers are
-// reused).  Rows and columns beyond N are padded with the identity, so the
+// Right-looking blocked Cholesky with a lookahead of one column: in step k every
+// CTA updates its trailing tiles A_ij -= L_ik L_jk^T (one warp per tile) with
+// the panel column k it received, while warp 0 of the owner of (k+1, k+1)
+// updates that tile first, factors it and pushes L^T of it to the owners of the
+// panel tiles (i, k+1); those solve L_i,k+1 L_k+1,k+1^T = A_i,k+1 as soon as
+// their own updates are done and push the solved tiles (stored transposed) into
+// the panel buffer of every CTA.  Pushes are bulk shared-to-shared copies that
+// complete on the receiver's mbarriers.  With T <= 16 tile rows the panel
+// buffer is double-buffered and the cluster barrier that frees a buffer is
+// split (arrive after the reads, wait before the next overwrite), so it never
+// waits in practice; with more tile rows a full cluster barrier precedes each
+// push.  At the end each CTA inverts its diagonal tiles for the triangular
+// solves.  Rows and columns beyond N are padded with the identity, so the
 // factor of the padded matrix is L plus an identity block.
+// Layout in shared memory: owned tiles (row stride 33; off-diagonal tiles are
+// stored transposed with row stride 32 once solved), the panel buffer(s) of
+// transposed tiles (32 x 32), L^T of the current diagonal tile with its
+// reciprocal diagonal, a staging copy of it, and the mbarriers.
 namespace cgx = cooperative_groups;
 constexpr int kClusterCTAs = 8;
 constexpr int kClusterN = 640;
-constexpr int kClusterT = kClusterN / 32;                                   // 20 tiles per side
-constexpr int kTileF = 32 * 33;                                              // floats per padded tile
-constexpr int kClusterSlots = (kClusterT * (kClusterT + 1) / 2 + kClusterCTAs - 1) / kClusterCTAs;  // 27
-constexpr unsigned kTileBytes = kTileF * sizeof(float);                      // 4224, a multiple of 16
-constexpr size_t kClusterSmem = (size_t)(kClusterSlots + kClusterT + 2) * kTileBytes + 16;  // + the mbarrier
+constexpr int kClusterT = kClusterN / 32;                 // 20 tiles per side
+constexpr int kClusterDoubleT = 16;                       // double-buffered panel up to this many tile rows
+constexpr int kTileF = 32 * 33;                           // floats per padded tile
+constexpr unsigned kTileBytes = kTileF * sizeof(float);   // 4224, a multiple of 16
+constexpr unsigned kPanelBytes = 1024 * sizeof(float);    // a transposed panel tile
+
+__host__ __device__ constexpr int cluster_slots(int T) { return (T * (T + 1) / 2 + kClusterCTAs - 1) / kClusterCTAs; }
+__host__ __device__ constexpr int cluster_nbuf(int T) { return T <= kClusterDoubleT ? 2 : 1; }
+__host__ __device__ constexpr size_t cluster_smem(int T) {
+  return ((size_t)(cluster_slots(T) + 2) * kTileF + (size_t)cluster_nbuf(T) * T * 1024) * sizeof(float) + 32;
+}
+constexpr size_t cluster_smem_max() {
+  size_t m = 0;
+  for (int T = 5; T <= kClusterT; T++) m = cluster_smem(T) > m ? cluster_smem(T) : m;
+  return m;
+}
+static_assert(cluster_slots(kClusterT) <= 32, "one lane per owned slot");
+static_assert(cluster_smem_max() <= 232448 - 1024, "shared memory per CTA");
 
 __device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank) {
   unsigned r;
@@ -558,28 +581,156 @@ __device__ __forceinline__ void bulk_s2c(unsigned dst, unsigned src, unsigned by
                "r"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ int tri_index(int i, int j) { return i * (i + 1) / 2 + j; }
 
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 1)
+// C -= Li Lj^T for 32x32 tiles by one warp; C has row stride 33, Pi = Li^T and
+// Pj = Lj^T have row stride 32 (one 128-bit load brings 4 rows of Li at one k).
+// Lane (tr, tc) owns rows 4tr..4tr+3 and columns 8tc..8tc+7 of C.
+__device__ __forceinline__ void tile_update_warp(float* C, const float* Pi, const float* Pj, int lane) {
+  const int tr = lane >> 2, tc = lane & 3;
+  float acc[4][8] = {};
+#pragma unroll 4
+  for (int q = 0; q < 32; q++) {
+    const float4 a = reinterpret_cast<const float4*>(Pi + q * 32)[tr];
+    const float4 b0 = reinterpret_cast<const float4*>(Pj + q * 32)[2 * tc];
+    const float4 b1 = reinterpret_cast<const float4*>(Pj + q * 32)[2 * tc + 1];
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int v = 0; v < 8; v++) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 8; v++) C[(4 * tr + u) * 33 + 8 * tc + v] -= acc[u][v];
+}
+
+// Factor the 32x32 tile D (row stride 33) in place, D = L L^T, by one warp:
+// lane l holds row l; in step q every lane publishes its entry of column q in
+// cb (64 floats, double-buffered) and reads the whole column back with
+// broadcast loads.  Entries above the diagonal collect products that are never
+// read.  Also writes U = L^T (row stride 32) and the reciprocal diagonal to
+// U[1024..].  Returns false if a pivot was not positive (it is replaced by 1).
+__device__ __forceinline__ bool factor_tile_warp(float* D, float* U, float* cb, int lane) {
+  float row[32];
+#pragma unroll
+  for (int c = 0; c < 32; c++) row[c] = (c <= lane) ? D[lane * 33 + c] : 0.0f;
+  bool bad = false;
+  float rl = 1.0f;
+#pragma unroll
+  for (int q = 0; q < 32; q++) {
+    float* col = cb + (q & 1) * 32;
+    const float u = row[q];  // A_lq after the updates of steps < q
+    col[lane] = u;
+    __syncwarp();
+    float piv = col[q];
+    if (!(piv > 0.0f)) {
+      bad = true;
+      piv = 1.0f;
+    }
+    const float t = u * __fdividef(1.0f, piv);
+    const float rs = rsqrtf(piv);
+    row[q] = u * rs;  // L_lq
+    if (lane == q) rl = rs;
+#pragma unroll
+    for (int g = 0; g < 8; g++) {
+      if (4 * g + 3 > q) {  // A_lc -= A_lq A_cq / A_qq, c > q
+        const float4 v = reinterpret_cast<const float4*>(col)[g];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+          if (4 * g + e > q) row[4 * g + e] = fmaf(-t, vv[e], row[4 * g + e]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; c++) {
+    const float v = (c <= lane) ? row[c] : 0.0f;
+    D[lane * 33 + c] = v;
+    U[c * 32 + lane] = v;
+  }
+  U[1024 + lane] = rl;
+  return !bad;
+}
+
+// Solve X L^T = A for one 32x32 panel tile A (row stride 33) by one warp, lane
+// r owning row r; U = L^T (row stride 32) with 1/L_jj at U[1024 + j].  X is
+// written back transposed (row stride 32) over A.
+__device__ __forceinline__ void panel_solve_warp(float* A, const float* U, int lane) {
+  float x[32];
+#pragma unroll
+  for (int c = 0; c < 32; c++) x[c] = A[lane * 33 + c];
+#pragma unroll
+  for (int j = 0; j < 32; j++) {
+    x[j] *= U[1024 + j];
+    const float4* u4 = reinterpret_cast<const float4*>(U + j * 32);
+#pragma unroll
+    for (int g = 0; g < 8; g++) {
+      if (4 * g + 3 > j) {
+        const float4 v = u4[g];
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+          if (4 * g + e > j) x[4 * g + e] = fmaf(-x[j], vv[e], x[4 * g + e]);
+      }
+    }
+  }
+  __syncwarp();  // every lane has read its row before the transposed write
+#pragma unroll
+  for (int c = 0; c < 32; c++) A[c * 32 + lane] = x[c];
+}
+
+// Lanes 0..kClusterCTAs-1 of a warp push `bytes` from src (this CTA) to dst in
+// the CTAs of `mask`, completing on their mbarrier `bar`.  The data must have
+// been fenced for the async proxy and synchronised within the warp.
+__device__ __forceinline__ void push_tile(unsigned src, unsigned dst, unsigned bytes, unsigned bar, unsigned mask,
+                                          int lane) {
+  if (lane < kClusterCTAs && (mask >> lane & 1u)) bulk_s2c(cluster_addr(dst, lane), src, bytes, cluster_addr(bar, lane));
+}
+
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag) {
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
-  extern __shared__ float csm[];
-  float* own = csm;                                  // kClusterSlots tiles
-  float* panel = csm + kClusterSlots * kTileF;       // copy of panel column k (kClusterT tiles)
-  float* winv = panel + kClusterT * kTileF;          // inverse of L_kk (owner of (k, k))
-  float* tmp = winv + kTileF;                        // scratch tile
-  const int tid = threadIdx.x;
+  extern __shared__ __align__(16) float csm[];
   const int T = (N + 31) / 32;
-
-  // ---- load the owned tiles (identity padding beyond N)
-  for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
+  const int nbuf = cluster_nbuf(T);
+  float* own = csm;                                        // owned tiles
+  float* panel = own + cluster_slots(T) * kTileF;          // nbuf x T transposed panel tiles
+  float* dbuf = panel + nbuf * T * 1024;                   // L^T of the next diagonal tile, 1/diag at [1024..]
+  float* ustage = dbuf + kTileF;                           // the owner of a diagonal tile builds that buffer here
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ustage + kTileF);
+  const unsigned pbar0 = smem_u32(bars), dbar = smem_u32(bars + 2);  // panel arrivals per buffer, diagonal arrivals
+  __shared__ int slot_ij[32];                    // (i << 8) | j of the tile in each owned slot
+  __shared__ __align__(16) float fcol[64];       // column exchange of the diagonal factor
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned all = (1u << kClusterCTAs) - 1u;
+  const int nslots = (T * (T + 1) / 2 - rank + kClusterCTAs - 1) / kClusterCTAs;
+  for (int sl = tid; sl < nslots; sl += blockDim.x) {
     int ti, tj;
-    tri_tile(t, ti, tj);
-    float* dst = own + (t / kClusterCTAs) * kTileF;
+    tri_tile(rank + sl * kClusterCTAs, ti, tj);
+    slot_ij[sl] = (ti << 8) | tj;
+  }
+  __syncthreads();
+  // lane l of every warp keeps (i, j) of slot l: the per-step work lists are
+  // ballots over these
+  const int my_i = lane < nslots ? slot_ij[lane] >> 8 : -1;
+  const int my_j = lane < nslots ? slot_ij[lane] & 255 : -1;
+  auto panel_tile = [&](int k, int i) { return panel + ((k % nbuf) * T + i) * 1024; };
+  auto pbar = [&](int k) { return pbar0 + 8u * (unsigned)(k % nbuf); };
+
+  // ---- load the owned tiles (identity padding beyond N); consecutive threads
+  //      read consecutive rows of a column
+  for (int sl = 0; sl < nslots; sl++) {
+    const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+    float* dst = own + sl * kTileF;
     for (int e = tid; e < 1024; e += 256) {
-      const int r = e >> 5, c = e & 31;
+      const int r = e & 31, c = e >> 5;
       const int gi = ti * 32 + r, gj = tj * 32 + c;
       float v;
       if (gi < N && gj < N)
@@ -589,188 +740,275 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256, 1)
       dst[r * 33 + c] = v;
     }
   }
-  unsigned long long* pbar = reinterpret_cast<unsigned long long*>(tmp + kTileF);  // panel arrivals
+  // panel-column ownership of column j: the CTAs owning a tile (i, j), i > j
+  auto receivers_of = [&](int j) {
+    unsigned m = 0;
+    for (int i = j + 1; i < T; i++) m |= 1u << (tri_index(i, j) % kClusterCTAs);
+    return m;
+  };
   if (tid == 0) {
-    mbar_init(smem_u32(pbar), 1);
+    mbar_init(pbar0, 1);
+    mbar_init(pbar0 + 8, 1);
+    mbar_init(dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // arm for the first diagonal push and the first panel
+    if (receivers_of(0) >> rank & 1u) mbar_expect_tx(dbar, kTileBytes);
+    if (T > 1) mbar_expect_tx(pbar(0), (unsigned)(T - 1) * kPanelBytes);
   }
+  __syncthreads();
   cluster.sync();
-  bool ok = true;
-  for (int k = 0; k < T; k++) {
-    const int dkk = tri_index(k, k);
-    const int npanel = T - k - 1;
-    // this CTA's panel buffer receives tiles k+1 .. T-1 in this step; arm the
-    // barrier before the cluster barrier below, i.e. before any copy is issued
-    if (tid == 0 && npanel > 0) mbar_expect_tx(smem_u32(pbar), (unsigned)npanel * kTileBytes);
-    // ---- (a) factor the diagonal tile and invert the factor in one warp.  Lane l
-    //      holds row l of the tile (then of L) and row l of the running
-    //      forward substitution for W = L^{-1}; step q publishes column q of L and
-    //      row q of W through two small shared buffers.
-    if (dkk % kClusterCTAs == rank && tid < 32) {
-      float* D = own + (dkk / kClusterCTAs) * kTileF;
-      const int lane = tid;
-      float row[32], acc[32];
-#pragma unroll
-      for (int c = 0; c < 32; c++) {
-        row[c] = (c <= lane) ? D[lane * 33 + c] : 0.0f;
-        acc[c] = (c == lane) ? 1.0f : 0.0f;
+  if (nbuf == 2) cluster_arrive();  // the split barrier runs one phase ahead
+  bool ok = true, bad = false;
+  unsigned dphase = 0;  // completed phases of dbar
+
+  // ---- prologue: factor (0, 0), solve and push panel column 0
+  if (rank == 0 && warp == 0) {
+    bad |= !factor_tile_warp(own, ustage, fcol, lane);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, receivers_of(0), lane);
+  }
+  if (receivers_of(0) >> rank & 1u) {
+    if (ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
+    dphase++;
+    unsigned m = __ballot_sync(0xffffffffu, my_j == 0 && my_i > 0);
+    for (int e = 0; m; e++, m &= m - 1) {
+      if ((e & 7) != warp) continue;
+      const int sl = __ffs(m) - 1, i = __shfl_sync(0xffffffffu, my_i, sl);
+      float* Ai = own + sl * kTileF;
+      panel_solve_warp(Ai, dbuf, lane);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      push_tile(smem_u32(Ai), smem_u32(panel_tile(0, i)), kPanelBytes, pbar(0), all, lane);
+    }
+  }
+
+  for (int k = 0; k + 1 < T; k++) {
+    const int next = tri_index(k + 1, k + 1);
+    const bool diag_here = next % kClusterCTAs == rank;
+    const unsigned recv_next = receivers_of(k + 1);
+    // arm for the push of the next diagonal tile (the previous one was consumed)
+    if (tid == 0 && (recv_next >> rank & 1u)) mbar_expect_tx(dbar, kTileBytes);
+    // panel column k has arrived
+    if (ok && !mbar_wait(pbar(k), (unsigned)((k / nbuf) & 1))) ok = false;
+    // arm for panel column k+1 (its buffer's previous phase was consumed)
+    if (tid == 0 && k + 2 < T) mbar_expect_tx(pbar(k + 1), (unsigned)(T - k - 2) * kPanelBytes);
+    // ---- lookahead: warp 0 of the owner of (k+1, k+1) updates, factors and publishes it
+    if (diag_here && warp == 0) {
+      float* D = own + (next / kClusterCTAs) * kTileF;
+      const float* Pk = panel_tile(k, k + 1);
+      tile_update_warp(D, Pk, Pk, lane);
+      __syncwarp();
+      bad |= !factor_tile_warp(D, ustage, fcol, lane);
+      if (recv_next) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, recv_next, lane);
       }
-      bool bad = false;
+    }
+    // ---- trailing update of the other owned tiles (i, j), k < j <= i, one warp
+    //      per tile; the next panel column k+1 first
+    if (!(diag_here && warp == 0) && ok) {
+      const int nw = diag_here ? kClusterCTAs - 1 : kClusterCTAs;
+      const int me = diag_here ? warp - 1 : warp;
+      int turn = 0;  // cycles through 0 .. nw-1 over the work list
+      for (int pass = 0; pass < 2; pass++) {
+        unsigned m = __ballot_sync(0xffffffffu, pass == 0 ? (my_j == k + 1 && my_i > k + 1) : (my_j > k + 1));
+        for (; m; m &= m - 1) {
+          const bool mine = turn == me;
+          turn = (turn + 1 == nw) ? 0 : turn + 1;
+          if (!mine) continue;
+          const int sl = __ffs(m) - 1;
+          const int ti = __shfl_sync(0xffffffffu, my_i, sl), tj = __shfl_sync(0xffffffffu, my_j, sl);
+          tile_update_warp(own + sl * kTileF, panel_tile(k, ti), panel_tile(k, tj), lane);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- solve the owned tiles of panel column k+1
+    if (recv_next >> rank & 1u) {
+      if (ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
+      dphase++;
+      unsigned m = __ballot_sync(0xffffffffu, my_j == k + 1 && my_i > k + 1);
+      for (int e = 0; m; e++, m &= m - 1) {
+        if ((e & 7) != warp) continue;
+        panel_solve_warp(own + (__ffs(m) - 1) * kTileF, dbuf, lane);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+    }
+    // the buffer that panel k+1 goes to must be free: with two buffers it was
+    // read in step k-1 (the wait matches the arrive issued then); with one it
+    // is panel k itself, so every CTA must be done with this step
+    if (nbuf == 2) {
+      cluster_wait();
+      cluster_arrive();  // this CTA is done reading panel k
+    } else {
+      cluster.sync();
+    }
+    if (recv_next >> rank & 1u) {
+      unsigned m = __ballot_sync(0xffffffffu, my_j == k + 1 && my_i > k + 1);
+      for (int e = 0; m; e++, m &= m - 1) {
+        if ((e & 7) != warp) continue;
+        const int sl = __ffs(m) - 1, i = __shfl_sync(0xffffffffu, my_i, sl);
+        push_tile(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, pbar(k + 1), all, lane);
+      }
+    }
+  }
+  if (nbuf == 2) cluster_wait();
+  if (bad) st->chol_fail = 1;
+  if (!ok) st->timeout = 1;
+  __syncthreads();
+  // ---- inverse diagonal blocks for the triangular solves, W_kk = L_kk^{-1}:
+  //      one warp per owned diagonal tile, lane j forms column j of W by forward
+  //      substitution; W is stored row-major
+  if (Wdiag) {
+    unsigned m = __ballot_sync(0xffffffffu, my_i >= 0 && my_i == my_j);
+    for (int e = 0; m; e++, m &= m - 1) {
+      if ((e & 7) != warp) continue;
+      const int sl = __ffs(m) - 1, k = __shfl_sync(0xffffffffu, my_i, sl);
+      const float* D = own + sl * kTileF;
+      float w[32];
+#pragma unroll
+      for (int i = 0; i < 32; i++) {
+        float s = (i == lane) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int q = 0; q < i; q++) s = fmaf(-D[i * 33 + q], w[q], s);
+        w[i] = s * __frcp_rn(D[i * 33 + i]);
+      }
+#pragma unroll
+      for (int i = 0; i < 32; i++) Wdiag[(long long)k * 1024 + i * 32 + lane] = w[i];
+    }
+  }
+  // ---- write the factor back (lower part, inside N); consecutive threads take
+  //      consecutive rows of a column.  Off-diagonal tiles are stored transposed.
+  for (int sl = 0; sl < nslots; sl++) {
+    const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+    const float* src = own + sl * kTileF;
+    for (int e = tid; e < 1024; e += 256) {
+      const int r = e & 31, c = e >> 5;
+      const int gi = ti * 32 + r, gj = tj * 32 + c;
+      if (gi < N && gj < N && gi >= gj) G[gi + (long long)gj * ld] = (ti == tj) ? src[r * 33 + c] : src[c * 32 + r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solves with the factor of the cluster Cholesky (kSmallN < N <=
+// kClusterN) and its inverse diagonal blocks W_II = L_II^{-1}: right-looking
+// block substitution in one CTA.  Thread t owns row t of the right-hand side.
+// Step I of the forward pass: warp I forms z_I = W_II r_I; every row below
+// block I then subtracts L[t, I] z_I.  The backward pass runs the same way
+// with L^T.  The block column (forward) or block row (backward) that the next
+// step reads is staged into shared memory with cp.async while the current
+// step runs; rows at or beyond N are zero-filled.
+constexpr int kBlkThreads = 1024;
+constexpr int kBlkRowStride = 36;  // floats per staged column of a block row (16-byte rows, 4-way bank spread)
+
+__host__ __device__ constexpr int blk_stage_floats(int N) {
+  // forward: 32 columns x ldb rows; backward: up to 32 (T - 1) columns x 36
+  return (32 * ((N + 3) & ~3)) > (kBlkRowStride * 32 * ((N + 31) / 32 - 1))
+             ? (32 * ((N + 3) & ~3))
+             : (kBlkRowStride * 32 * ((N + 31) / 32 - 1));
+}
+
+__device__ __forceinline__ void blk_stage_forward(const float* __restrict__ L, long long ld, int N, int I,
+                                                  const float* __restrict__ Wd, float* dst, float* wdst) {
+  const int r0 = 32 * (I + 1), ldb = (N + 3) & ~3;
+  const int nch = (N - r0 + 3) / 4;  // 4-row chunks per column below the diagonal block
+  for (int e = threadIdx.x; e < 32 * nch; e += blockDim.x) {
+    const int q = e / nch, c = e - q * nch, row = r0 + 4 * c;
+    cp_async16(dst + q * ldb + 4 * c, L + row + (long long)(32 * I + q) * ld, 4 * min(4, N - row));
+  }
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) cp_async16(wdst + 4 * e, Wd + (long long)I * 1024 + 4 * e, 16);
+}
+
+__device__ __forceinline__ void blk_stage_backward(const float* __restrict__ L, long long ld, int N, int I,
+                                                   const float* __restrict__ Wd, float* dst, float* wdst) {
+  for (int e = threadIdx.x; e < 32 * I * 8; e += blockDim.x) {
+    const int j = e >> 3, g = e & 7, row = 32 * I + 4 * g;
+    const int valid = max(0, min(4, N - row));
+    cp_async16(dst + j * kBlkRowStride + 4 * g, valid ? L + row + (long long)j * ld : L, 4 * valid);
+  }
+  for (int e = threadIdx.x; e < 256; e += blockDim.x) cp_async16(wdst + 4 * e, Wd + (long long)I * 1024 + 4 * e, 16);
+}
+
+__global__ void __launch_bounds__(kBlkThreads) k_trsv_blk(const float* __restrict__ L, long long ld, int N,
+                                                          const double* __restrict__ rhs, double* __restrict__ acc,
+                                                          int first, double alpha, const float* __restrict__ Wd) {
+  extern __shared__ __align__(16) float sm_blk[];
+  const int T = (N + 31) / 32, ldb = (N + 3) & ~3, stage = blk_stage_floats(N);
+  // staging buffer b: L part at sm_blk + b * stage, W_II at sm_blk + 2 * stage + b * 1024
+  auto Lb = [&](int b) { return sm_blk + b * stage; };
+  auto Wb = [&](int b) { return sm_blk + 2 * stage + b * 1024; };
+  float* vec = sm_blk + 2 * stage + 2048;  // z_I (forward) or c_I (backward) of the current step
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float r = (t < N) ? (float)rhs[t] : 0.0f;
+  // ---- forward: z = L^{-1} rhs
+  blk_stage_forward(L, ld, N, 0, Wd, Lb(0), Wb(0));
+  cp_async_commit();
+  for (int I = 0; I < T; I++) {
+    cp_async_wait0();
+    __syncthreads();  // step I staged for everyone; step I-1 finished reading the other buffer
+    if (I + 1 < T) blk_stage_forward(L, ld, N, I + 1, Wd, Lb((I + 1) & 1), Wb((I + 1) & 1));
+    cp_async_commit();
+    if (warp == I) {
+      // z_l = sum_p W[l][p] r_p, the column index rotated by the lane (no bank conflicts)
+      const float* W = Wb(I & 1);
+      float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int q = 0; q < 32; q++) {
-        float piv = __shfl_sync(0xffffffffu, row[q], q);
-        if (!(piv > 0.0f)) {
-          bad = true;
-          piv = 1.0f;
-        }
-        const float rq = rsqrtf(piv);
-        row[q] = (lane == q) ? piv * rq : row[q] * rq;  // L_lq (zero above the diagonal)
-        float* cb = tmp + (q & 1) * 32;                 // column q of L
-        float* wb = tmp + 64 + (q & 1) * 32;            // row q of W
-        cb[lane] = row[q];
-        if (lane == q) {
-#pragma unroll
-          for (int c = 0; c < 32; c++) acc[c] *= rq;  // W_q = (e_q - sum_{t<q} L_qt W_t) / L_qq
-#pragma unroll
-          for (int g = 0; g < 8; g++)
-            reinterpret_cast<float4*>(wb)[g] = make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
-        }
-        __syncwarp();
-        const float lq = row[q];
-#pragma unroll
-        for (int g = 0; g < 8; g++) {
-          if (4 * g + 3 > q) {  // A_lc -= L_lq L_cq, q < c <= l
-            const float4 v = reinterpret_cast<const float4*>(cb)[g];
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-              const int c = 4 * g + e;
-              if (c > q) row[c] = (lane >= c) ? fmaf(-lq, vv[e], row[c]) : row[c];
-            }
-          }
-        }
-        const float lw = (lane > q) ? lq : 0.0f;
-#pragma unroll
-        for (int g = 0; g < 8; g++) {
-          if (4 * g <= q) {  // rows below q: acc_l -= L_lq W_q
-            const float4 v = reinterpret_cast<const float4*>(wb)[g];
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; e++)
-              if (4 * g + e <= q) acc[4 * g + e] = fmaf(-lw, vv[e], acc[4 * g + e]);
-          }
-        }
+        const int p = (q + lane) & 31;
+        a[q & 3] = fmaf(W[lane * 32 + p], __shfl_sync(0xffffffffu, r, p), a[q & 3]);
       }
-      if (bad && lane == 0) st->chol_fail = 1;
-#pragma unroll
-      for (int c = 0; c < 32; c++) {
-        D[lane * 33 + c] = (c <= lane) ? row[c] : 0.0f;
-        winv[lane * 33 + c] = (c <= lane) ? acc[c] : 0.0f;
-      }
-      __syncwarp();
-      if (Wdiag)  // keep the inverse diagonal blocks for the triangular solves
-        for (int e = lane; e < 1024; e += 32) Wdiag[(long long)k * 1024 + e] = winv[(e >> 5) * 33 + (e & 31)];
+      r = (a[0] + a[1]) + (a[2] + a[3]);  // this row is final: r holds z from here on
+      vec[lane] = r;
     }
-    cluster.sync();
-    // ---- (b) panel tiles L_ik = A_ik W^T: four tiles at a time, 64 threads per
-    //      tile, a 4 x 4 register block per thread; each finished tile is pushed
-    //      to slot i of every CTA's panel buffer
-    {
-      int mine = 0;
-      for (int i = k + 1; i < T; i++)
-        if (tri_index(i, k) % kClusterCTAs == rank) mine++;
-      if (mine > 0) {
-        const float4* s4 = reinterpret_cast<const float4*>(cluster.map_shared_rank(winv, dkk % kClusterCTAs));
-        float4* d4 = reinterpret_cast<float4*>(tmp);
-        for (int e = tid; e < kTileF / 4; e += 256) d4[e] = s4[e];
-        __syncthreads();
-        const int grp = tid >> 6, gt = tid & 63, tr = gt >> 3, tc = gt & 7;
-        int seen = 0;
-        for (int i = k + 1; i < T; i++) {
-          const int t = tri_index(i, k);
-          if (t % kClusterCTAs != rank) continue;
-          if ((seen++ & 3) != grp) continue;
-          float* Ai = own + (t / kClusterCTAs) * kTileF;
-          float acc[4][4] = {};
-#pragma unroll 4
-          for (int q = 0; q < 32; q++) {
-            float a[4], w[4];
+    __syncthreads();
+    if (t >= 32 * (I + 1) && t < N) {
+      const float* B = Lb(I & 1) + (t - 32 * (I + 1));
+      float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-              a[u] = Ai[(4 * tr + u) * 33 + q];
-              w[u] = tmp[(4 * tc + u) * 33 + q];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-#pragma unroll
-              for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], w[v], acc[u][v]);
-          }
-          // the 64 threads of this tile finish reading A_ik before it is overwritten
-          asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory");
-#pragma unroll
-          for (int u = 0; u < 4; u++)
-#pragma unroll
-            for (int v = 0; v < 4; v++) Ai[(4 * tr + u) * 33 + 4 * tc + v] = acc[u][v];
-          // make the writes visible to the copy engine, then one thread pushes the tile
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory");
-          if (gt == 0) {
-            const unsigned src = smem_u32(Ai), dst = smem_u32(panel + i * kTileF), bar = smem_u32(pbar);
-#pragma unroll 1
-            for (int r = 0; r < kClusterCTAs; r++)
-              bulk_s2c(cluster_addr(dst, r), src, kTileBytes, cluster_addr(bar, r));
-          }
-        }
-      }
-    }
-    // ---- (c) trailing update of the owned tiles (i, j), k < j <= i
-    if (npanel > 0) {
-      if (ok && !mbar_wait(smem_u32(pbar), (unsigned)(k & 1))) ok = false;
-      // four tiles at a time, 64 threads per tile, a 4 x 4 register block per thread
-      const int grp = tid >> 6, gt = tid & 63, tr = gt >> 3, tc = gt & 7;
-      int seen = 0;
-      for (int t = rank; t < T * (T + 1) / 2 && ok; t += kClusterCTAs) {
-        int ti, tj;
-        tri_tile(t, ti, tj);
-        if (tj <= k) continue;
-        if ((seen++ & 3) != grp) continue;
-        float* C = own + (t / kClusterCTAs) * kTileF;
-        const float* Li = panel + ti * kTileF;
-        const float* Lj = panel + tj * kTileF;
-        float acc[4][4] = {};
-#pragma unroll 4
-        for (int q = 0; q < 32; q++) {
-          float a[4], b[4];
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            a[u] = Li[(4 * tr + u) * 33 + q];
-            b[u] = Lj[(4 * tc + u) * 33 + q];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; u++)
-#pragma unroll
-            for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-#pragma unroll
-          for (int v = 0; v < 4; v++) C[(4 * tr + u) * 33 + 4 * tc + v] -= acc[u][v];
-      }
-    }
-    cluster.sync();
-  }
-  if (!ok) st->timeout = 1;
-  // ---- write the factor back (lower part, inside N)
-  for (int t = rank; t < T * (T + 1) / 2; t += kClusterCTAs) {
-    int ti, tj;
-    tri_tile(t, ti, tj);
-    const float* src = own + (t / kClusterCTAs) * kTileF;
-    for (int e = tid; e < 1024; e += 256) {
-      const int r = e >> 5, c = e & 31;
-      const int gi = ti * 32 + r, gj = tj * 32 + c;
-      if (gi < N && gj < N && gi >= gj) G[gi + (long long)gj * ld] = src[r * 33 + c];
+      for (int q = 0; q < 32; q++) a[q & 3] = fmaf(B[q * ldb], vec[q], a[q & 3]);
+      r -= (a[0] + a[1]) + (a[2] + a[3]);
     }
   }
+  // ---- backward: c = L^{-T} z
+  cp_async_wait0();
+  __syncthreads();
+  blk_stage_backward(L, ld, N, T - 1, Wd, Lb(0), Wb(0));
+  cp_async_commit();
+  for (int I = T - 1, sidx = 0; I >= 0; I--, sidx ^= 1) {
+    cp_async_wait0();
+    __syncthreads();
+    if (I > 0) blk_stage_backward(L, ld, N, I - 1, Wd, Lb(sidx ^ 1), Wb(sidx ^ 1));
+    cp_async_commit();
+    if (warp == I) {
+      // c_l = sum_q W[q][l] r_q
+      const float* W = Wb(sidx);
+      float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < 32; q++) a[q & 3] = fmaf(W[q * 32 + lane], __shfl_sync(0xffffffffu, r, q), a[q & 3]);
+      r = (a[0] + a[1]) + (a[2] + a[3]);
+      vec[lane] = r;
+      if (t < N) acc[t] = first ? alpha * (double)r : acc[t] + alpha * (double)r;
+    }
+    __syncthreads();
+    if (t < 32 * I) {
+      const float4* B = reinterpret_cast<const float4*>(Lb(sidx) + t * kBlkRowStride);
+      const float4* v4 = reinterpret_cast<const float4*>(vec);
+      float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int g = 0; g < 8; g++) {
+        const float4 l = B[g], v = v4[g];
+        a[0] = fmaf(l.x, v.x, a[0]);
+        a[1] = fmaf(l.y, v.y, a[1]);
+        a[2] = fmaf(l.z, v.z, a[2]);
+        a[3] = fmaf(l.w, v.w, a[3]);
+      }
+      r -= (a[0] + a[1]) + (a[2] + a[3]);
+    }
+  }
+  cp_async_wait0();
 }
 
 // ---------------------------------------------------------------------------
@@ -951,11 +1189,11 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !done[dev]) {
-      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmem);
+      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    k_chol_cluster<<<kClusterCTAs, 256, kClusterSmem, s>>>(G, ldg, N, st, Wdiag);
+    k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((N + 31) / 32), s>>>(G, ldg, N, st, Wdiag);
     if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
   }
   {
@@ -1005,6 +1243,20 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
     small_smem_attr();
     count_launch();
     k_trsv_small<<<1, kSmallThreads, kSmallSmem, s>>>(L, ldl, N, rhs, acc, first, alpha);
+    return;
+  }
+  if (Wdiag && N <= kClusterN) {
+    static bool done_blk[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done_blk[dev]) {
+      cudaFuncSetAttribute(k_trsv_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((2 * blk_stage_floats(kClusterN) + 2048 + 32) * sizeof(float)));
+      if (dev >= 0 && dev < 64) done_blk[dev] = true;
+    }
+    count_launch();
+    k_trsv_blk<<<1, kBlkThreads, (size_t)(2 * blk_stage_floats(N) + 2048 + 32) * sizeof(float), s>>>(
+        L, ldl, N, rhs, acc, first, alpha, Wdiag);
     return;
   }
   if (N <= kMidN) {

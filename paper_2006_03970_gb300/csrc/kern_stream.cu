@@ -117,10 +117,9 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_f64(const double* __r
     partials[(long long)blockIdx.x * 32 + lane] = s;
   }
   if (!last_block(&st->counters[kCtrStream])) return;
-  if (warp == 0) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++) s += ld_cg(&partials[(long long)b * 32 + lane]);
-    if (lane < lp.fused) st->lsdiff[lane] = s;
+  {
+    const double s = rows_sum32(partials, (int)gridDim.x, &wred[0][0]);
+    if (warp == 0 && lane < lp.fused) st->lsdiff[lane] = s;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -178,9 +177,7 @@ __global__ void __launch_bounds__(256) k_ls_fallback(const double* __restrict__ 
   }
   if (!last_block(&st->counters[kCtrFallback])) return;
   for (int q = threadIdx.x; q < extra; q += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++) s += ld_cg(&partials[(long long)b * kMaxLS + q]);
-    st->lsdiff[lp.fused + q] = s;
+    st->lsdiff[lp.fused + q] = ordered_sum_cg(partials + q, kMaxLS, (int)gridDim.x);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -561,10 +558,9 @@ __global__ void __launch_bounds__(kFFThreads, 1) k_stream_ff(const double* __res
     partials[(long long)blockIdx.x * 32 + lane] = s;
   }
   if (!last_block(&st->counters[kCtrStream])) return;
-  if (warp == 0) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++) s += ld_cg(&partials[(long long)b * 32 + lane]);
-    if (lane < lp.fused) st->lsdiff[lane] = s;
+  {
+    const double s = rows_sum32(partials, (int)gridDim.x, &wred[0][0]);
+    if (warp == 0 && lane < lp.fused) st->lsdiff[lane] = s;
   }
   __syncthreads();
   if (tid == 0) {
@@ -855,10 +851,9 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     partials[(long long)blockIdx.x * 32 + lane] = sum;
   }
   if (!last_block(&st->counters[kCtrStream])) return;
-  if (warp == 0) {
-    double sum = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++) sum += ld_cg(&partials[(long long)b * 32 + lane]);
-    if (lane < lp.fused) st->lsdiff[lane] = sum;
+  {
+    const double sum = rows_sum32(partials, (int)gridDim.x, &wred[0][0]);
+    if (warp == 0 && lane < lp.fused) st->lsdiff[lane] = sum;
   }
   __syncthreads();
   if (tid == 0) {

@@ -14,9 +14,12 @@ std::atomic<long long> g_launches{0};
 
 constexpr int kVecThreads = 256;
 
+// Blocks for the O(n) passes: at most two per SM and at least 256 entries per
+// block, so that the FP64 work (a few dozen FP64 operations per entry, at the
+// GPU's low FP64 rate) is spread evenly over the SMs.
 int vec_grid(long long n, int sms) {
-  long long g = (n + 511) / 512;
-  long long cap = 4LL * sms;
+  long long g = (n + 255) / 256;
+  long long cap = 2LL * sms;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
@@ -49,8 +52,7 @@ __device__ long long block_incl_scan(long long v, long long* sh) {
 }
 
 __device__ __forceinline__ void block_range(long long n, long long& start, long long& stop) {
-  long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  chunk = (chunk + kVecThreads - 1) / kVecThreads * kVecThreads;
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
   start = (long long)blockIdx.x * chunk;
   stop = start + chunk;
   if (stop > n) stop = n;
@@ -91,8 +93,12 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
       u[j] = uj;
     }
     const double v = v_of(xj, uj, pp.sigma);
-    const double w = prox_value(v, pp);
-    if (w != 0.0) cnt++;
+    // the count uses the active test itself (eq. Q_def); w only feeds the norms,
+    // so the reciprocal of 1 + sigma*lam2 replaces the division here
+    const bool act = is_active(v, pp);
+    const double mag = act ? __dsub_rn(fabs(v), pp.thr) * pp.inv_onep : 0.0;
+    const double w = v < 0.0 ? -mag : mag;
+    if (act) cnt++;
     w2 += w * w;
     w1 += fabs(w);
     xw2 += (xj - w) * (xj - w);
@@ -168,8 +174,8 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
         act = xj != 0.0;
       } else {
         const double v = v_of(xj, u[j], pp.sigma);
+        act = is_active(v, pp);
         w = prox_value(v, pp);
-        act = w != 0.0;
       }
     }
     long long incl = block_incl_scan(act ? 1 : 0, shl);
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ ou
   if (i < m) {
     double sum = 0.0;
     if (part) {
-      for (int g = 0; g < kGemvGroups; g++) sum += part[(long long)g * m + i];
+      sum = ordered_sum_cg(part + i, m, kGemvGroups);
     }
     double lin = 0.0;
     if (a) lin = ca * a[i];
@@ -298,21 +304,12 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ ou
     if (threadIdx.x == 0) scratch[blockIdx.x * 4 + k] = bsum;
   }
   if (!last_block(&st->counters[kCtrCombine])) return;
-  if (threadIdx.x == 0) {
-    double tot[4] = {0, 0, 0, 0};
-    for (int bl = 0; bl < (int)gridDim.x; bl++)
-      for (int k = 0; k < 4; k++) tot[k] += ld_cg(&scratch[bl * 4 + k]);
-    if (which == 1) {
-      st->g2 = tot[0];
-      st->y2 = tot[1];
-      st->yg2 = tot[2];
-      st->by = tot[3];
-    } else {
-      st->gd = tot[0];
-      st->yd = tot[1];
-      st->dd = tot[2];
-      st->bd = tot[3];
-    }
+  if (threadIdx.x < 4) {
+    const int k = threadIdx.x;
+    const double tot = ordered_sum_cg(scratch + k, 4, (int)gridDim.x);
+    double* dst = which == 1 ? (k == 0 ? &st->g2 : k == 1 ? &st->y2 : k == 2 ? &st->yg2 : &st->by)
+                             : (k == 0 ? &st->gd : k == 1 ? &st->yd : k == 2 ? &st->dd : &st->bd);
+    *dst = tot;
   }
   reset_counter(&st->counters[kCtrCombine]);
 }
@@ -374,7 +371,7 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
   if (grp == 0 && i < m) {
     double sum = 0.0;
     if (gridDim.y > 1)
-      for (long long y = 0; y < nsplit; y++) sum += __ldcg(&cpart[y * m + i]);
+      sum = ordered_sum_cg(cpart + i, m, (int)nsplit);
     else
       for (int g = 0; g < 8; g++) sum += part[g][lane];
     double lin = 0.0;
@@ -415,21 +412,12 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  if (threadIdx.x == 0) {
-    double tot[4] = {0, 0, 0, 0};
-    for (int bl = 0; bl < (int)gridDim.x; bl++)
-      for (int k = 0; k < 4; k++) tot[k] += ld_cg(&scratch[bl * 4 + k]);
-    if (which == 1) {
-      stw->g2 = tot[0];
-      stw->y2 = tot[1];
-      stw->yg2 = tot[2];
-      stw->by = tot[3];
-    } else {
-      stw->gd = tot[0];
-      stw->yd = tot[1];
-      stw->dd = tot[2];
-      stw->bd = tot[3];
-    }
+  if (threadIdx.x < 4) {
+    const int k = threadIdx.x;
+    const double tot = ordered_sum_cg(scratch + k, 4, (int)gridDim.x);
+    double* dst = which == 1 ? (k == 0 ? &stw->g2 : k == 1 ? &stw->y2 : k == 2 ? &stw->yg2 : &stw->by)
+                             : (k == 0 ? &stw->gd : k == 1 ? &stw->yd : k == 2 ? &stw->dd : &stw->bd);
+    *dst = tot;
   }
   reset_counter(&stw->counters[kCtrGemv]);
 }

@@ -83,6 +83,7 @@ extern "C" ssnal_en_status ssnal_en_prox_active_static(const double* x, const do
   pp.lam2 = lambda2;
   pp.thr = sigma * lambda1;
   pp.onep = 1.0 + sigma * lambda2;
+  pp.inv_onep = 1.0 / pp.onep;
   launch_prox_count(kProxThreshold, x, const_cast<double*>(u), nullptr, nullptr, nullptr, n, 0, pp, 0, &sc->st,
                     sc->counts, sc->partials, grid, s);
   launch_prox_scatter(kProxThreshold, x, u, n, pp, sc->counts + grid, J, wJ, grid, s);
