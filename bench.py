@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+STREAM_TRAFFIC_BYTES = 401698304 + 4062464  # ncu, one k_stream_lane<kModeT> launch, m=500 n=1e5
 METRIC = "EN fits/s to KKT<=1e-6"
 UNIT = "fits/s"
 WORKLOAD = ("FP64 warm-started Elastic Net path: m=500, n=100000, 100-feature AR(1) blocks rho=0.7, "
@@ -240,9 +241,13 @@ def run_gpu(args):
     launches = prof1["stream_launches"] - 0
     s_ms = prof1["stream_ms"]
     achieved = (prof1["stream_bytes"] / (s_ms / 1e3) / 1e9) if s_ms > 0 else None
-    roofline = {"kernel": "k_stream_f64<kModeT> (t = A^T d with the fused line-search trial sums)",
+    roofline = {"kernel": "k_stream_lane<kModeT> (t = A^T d over the pre-split float pair copy, "
+                          "fused line-search trial sums)",
                 "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel on this
+                # workload (profiles/k_stream_lane_modeT_m500_n1e5.md)
+                "traffic": STREAM_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
                 "peak_kind": peak_kind, "launches": launches,
                 "avg_launch_us": (s_ms / launches * 1e3) if launches else None,
                 "bytes_per_launch": (prof1["stream_bytes"] / launches) if launches else None,
