@@ -82,7 +82,12 @@ typedef struct {
                            keeps a float-pair copy of A (same size as A) made at create time.
                            3: as 0 but without the copy (entries split on the fly, slower).
                            2: FP64 FMAs always.
-                           1: reserved for the mixed path (low-precision storage of A). */
+                           1: mixed precision, for A stored as BF16 or FP32: the Newton-step passes
+                           t = A^T d sum the products in FP32; u = A^T y is recomputed in
+                           float-float before every SsN stopping test, so the KKT test, the
+                           x update and the duality gap use FP64-accurate values.
+                           With BF16 / FP32 storage and precision 0, 2 or 3 every pass over A
+                           is float-float (products of the stored values are exact). */
   int32_t refine_steps; /* 1: iterative-refinement steps of the Newton solve (FP64 residual through
                            the packed A_J, FP32 factor) */
   int32_t use_y0;       /* 0: y0 = A x0 - b; 1: take y0 from the y argument of ssnal_en_solve */
@@ -118,8 +123,11 @@ const char* ssnal_en_status_string(int32_t status);
 /* Creates a context for the matrix *A.  opts may be NULL (defaults).  stream is
  * a cudaStream_t (NULL = the legacy default stream).  Allocates the device
  * workspaces (vectors of length n and m, the A_J panel, the Newton matrix).
+ * F64, F32 and BF16 storage are supported (I8_GENO returns ENOTSUP in this
+ * build).  F64 storage is copied once into a float-pair form for the stream
+ * (precision 0, see ssnal_en_options); F32 / BF16 storage is streamed in place.
  * Errors: EINVAL (null pointers, m <= 0, n <= 0, lda < m, misaligned lda or
- * data, unknown dtype), ENOTSUP (m above 4096), ENOMEM, ECUDA. */
+ * data, unknown dtype), ENOTSUP (m above 4096, I8_GENO), ENOMEM, ECUDA. */
 ssnal_en_status ssnal_en_create(ssnal_en_ctx** ctx, const ssnal_en_matrix* A,
                                 const ssnal_en_options* opts, void* stream);
 
@@ -195,6 +203,13 @@ ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* ctx, double* phase_ms, int
 /* u = A^T y (the dual-to-primal stream, needed by Prop. 2 and eq. Q_def).
  * y device length m (FP64), u device length n (FP64). */
 ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* ctx, const double* y, double* u);
+
+/* t = A^T d accumulated as in the solver's Newton steps (the pass of Algorithm 1
+ * that feeds the line search of eq. line_search): in the mixed precision mode
+ * (precision = 1 with BF16 or FP32 storage) the products are summed in FP32,
+ * otherwise exactly as ssnal_en_op_at_y.  d device length m (FP64), t device
+ * length n (FP64).  Errors: EINVAL (null pointer), ECUDA. */
+ssnal_en_status ssnal_en_op_at_d(ssnal_en_ctx* ctx, const double* d, double* t);
 
 /* Prox and active set (eqs. prox_elastic, Q_def): v = x - sigma*u,
  * J = { j : |v_j| > sigma*lambda1 } in ascending order, w_J = prox_{sigma p}(v)_J.

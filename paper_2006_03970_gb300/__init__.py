@@ -20,7 +20,8 @@ __all__ = [
     "F64", "F32", "BF16", "I8_GENO", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
-    "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_prox_active", "ssnal_en_op_grad",
+    "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_at_d", "ssnal_en_op_prox_active",
+    "ssnal_en_op_grad",
     "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_profile_phases", "ssnal_en_prox_active_static",
     "STATIC_MAX_N", "Context",
 ]
@@ -68,6 +69,7 @@ class Result(ctypes.Structure):
 _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
+           "ssnal_en_op_at_d",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
            "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
 
@@ -96,6 +98,7 @@ def load_library(path: str | None = None):
     L.ssnal_en_path_host.argtypes = [vp, ctypes.POINTER(dbl), dbl, ctypes.POINTER(dbl), i32, vp,
                                      ctypes.POINTER(Result), ctypes.POINTER(i32)]
     L.ssnal_en_op_at_y.argtypes = [vp, vp, vp]
+    L.ssnal_en_op_at_d.argtypes = [vp, vp, vp]
     L.ssnal_en_op_prox_active.argtypes = [vp, vp, vp, dbl, dbl, dbl, vp, vp, ctypes.POINTER(i64)]
     L.ssnal_en_op_grad.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     L.ssnal_en_op_newton.argtypes = [vp, i64, dbl, vp, vp]
@@ -238,6 +241,10 @@ def ssnal_en_path_host(ctx, b_host: np.ndarray, alpha, c_grid, X_host: np.ndarra
 
 def ssnal_en_op_at_y(ctx, y, u):
     _check(load_library().ssnal_en_op_at_y(ctx, _ptr(y), _ptr(u)), "ssnal_en_op_at_y")
+
+
+def ssnal_en_op_at_d(ctx, d, t):
+    _check(load_library().ssnal_en_op_at_d(ctx, _ptr(d), _ptr(t)), "ssnal_en_op_at_d")
 
 
 def ssnal_en_op_prox_active(ctx, x, u, sigma, lambda1, lambda2, J, wJ) -> int:

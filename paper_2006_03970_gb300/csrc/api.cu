@@ -199,6 +199,13 @@ void free_all(ssnal_en_ctx* c) {
 // exists, float-float with on-the-fly splitting, or FP64 FMAs (precision = 2 or
 // entries outside the range of the split).
 void set_stream_kind(ssnal_en_ctx* c) {
+  if (c->dtype == SSNAL_EN_BF16 || c->dtype == SSNAL_EN_F32) {
+    // BF16 / FP32 storage: the lane stream over A itself (tensor map built at create)
+    c->stream_kind = kStreamLane;
+    c->A_stream = c->A;
+    c->lda_stream = c->lda;
+    return;
+  }
   if (!c->ff_ok || c->opt.precision == 2) {
     c->stream_kind = kStreamDfma;
     c->A_stream = c->A;
@@ -282,12 +289,33 @@ ssnal_en_status read_state(ssnal_en_ctx* c) {
 }
 
 // One pass over A with the arithmetic and layout chosen at create time.
+// Element type and accumulation of a lane-stream pass.  FP64 storage: the
+// pre-split copy in float-float.  BF16 / FP32 storage: float-float for u = A^T y
+// and max|A^T b| (the values the KKT test and the x update use); the Newton
+// passes t = A^T d accumulate in FP32 in the mixed precision mode.
+int lane_elt(const ssnal_en_ctx* c, int mode) {
+  const bool plain = c->opt.precision == 1 && mode == kModeT;
+  if (c->dtype == SSNAL_EN_BF16) return plain ? kLaneBf16 : kLaneBf16FF;
+  if (c->dtype == SSNAL_EN_F32) return plain ? kLaneF32 : kLaneF32FF;
+  return kLaneSplit;
+}
+
+// True when the Newton passes are accumulated in FP32: u then drifts from A^T y
+// by FP32 rounding and is recomputed before the KKT test.
+bool mixed_stream(const ssnal_en_ctx* c) {
+  return c->opt.precision == 1 && (c->dtype == SSNAL_EN_BF16 || c->dtype == SSNAL_EN_F32);
+}
+
+// BF16 parts per panel entry in the tensor-core SYRK: a BF16-stored A_J is
+// exact in one part (one product per pair of entries); FP64 / FP32 need three.
+int syrk_splits(const ssnal_en_ctx* c) { return c->dtype == SSNAL_EN_BF16 ? 1 : 3; }
+
 void run_stream(ssnal_en_ctx* c, int mode, const double* vec, double* out, const double* x, const double* u,
                 ProxParams pp) {
   const ssnal_en_options& o = c->opt;
   if (c->stream_kind == kStreamLane)
-    launch_stream_lane(mode, c->tmap, (int)c->m, c->n, vec, out, x, u, pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st,
-                       c->partials, c->sms, c->stream);
+    launch_stream_lane(mode, lane_elt(c, mode), c->tmap, (int)c->m, c->n, vec, out, x, u, pp, o.mu, o.beta, o.max_ls,
+                       o.ls_fused, c->st, c->partials, c->sms, c->stream);
   else
     launch_stream(mode, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, vec, out, x, u, pp, o.mu,
                   o.beta, o.max_ls, o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
@@ -367,8 +395,8 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
     // SMW (eq. smw_formula): G = kappa^{-1} I + A_J^T A_J, h = A_J^T g, q = G^{-1} h, d = A_J q - g
     const int N = (int)r;
     if (c->opt.syrk_tc)
-      launch_syrk_tc(c->P, c->ldp, m, (int)r, 0, 3, c->Xtc, c->tc_part, 1.0f, (float)(1.0 / kappa), c->G, c->ldg,
-                     c->st, c->sms, s);
+      launch_syrk_tc(c->P, c->ldp, m, (int)r, 0, syrk_splits(c), c->Xtc, c->tc_part, 1.0f, (float)(1.0 / kappa), c->G,
+                     c->ldg, c->st, c->sms, s);
     else
       launch_syrk_tn(c->P32, c->ldp32, m, r, 1.0 / kappa, c->G, c->ldg, s);
     launch_gemv_t(c->P, c->ldp, m, r, g, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
@@ -390,7 +418,8 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
   } else {
     // m x m form (eq. AJ_system): M = I + kappa A_J A_J^T, d = -M^{-1} g
     if (c->opt.syrk_tc)
-      launch_syrk_tc(c->P, c->ldp, m, (int)r, 1, 3, c->Xtc, c->tc_part, (float)kappa, 1.0f, c->G, c->ldg, c->st,
+      launch_syrk_tc(c->P, c->ldp, m, (int)r, 1, syrk_splits(c), c->Xtc, c->tc_part, (float)kappa, 1.0f, c->G, c->ldg,
+                     c->st,
                      c->sms, s);
     else
       launch_syrk_nt(c->P32, c->ldp32, m, r, kappa, c->G, c->ldg, s);
@@ -450,6 +479,7 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
     const double kappa = sigma / (1.0 + sigma * lam2);
     int apply = 0;
     int newton_here = 0;
+    bool fresh = true;  // u = A^T y to the stream's full accuracy (false after FP32-accumulated steps)
     for (;;) {
       if ((e = prox_gather_grad(c, kProxThreshold, x, c->bdev, pp, apply)) != SSNAL_EN_OK) return e;
       const DevState& h = *c->st_host;
@@ -461,7 +491,18 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
         break;
       }
       const double gn = sqrt(h.g2) / nb1;
-      if (!(gn > o.tol) || newton_here >= o.max_newton) break;
+      if (!(gn > o.tol) || newton_here >= o.max_newton) {
+        if (!fresh) {
+          // mixed precision: recompute u = A^T y in float-float before the SsN
+          // stopping test is trusted (the KKT residuals and the x update read u)
+          run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
+          CK(cudaGetLastError());
+          fresh = true;
+          continue;
+        }
+        break;
+      }
+      fresh = !mixed_stream(c);
       const int64_t r = h.r;
       if ((e = newton_direction(c, r, kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
       if ((e = stream_t(c, x, pp)) != SSNAL_EN_OK) return e;
@@ -563,7 +604,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   if ((A->lda * (int64_t)es) % 16 != 0 || ((uintptr_t)A->data) % 16 != 0) return SSNAL_EN_EINVAL;
   if (A->n >= (int64_t)0x7fffffff) return SSNAL_EN_ENOTSUP;
   if (A->m > kMaxM) return SSNAL_EN_ENOTSUP;
-  if (A->dtype != SSNAL_EN_F64) return SSNAL_EN_ENOTSUP;  // other storage types: not in this build yet
+  if (A->dtype == SSNAL_EN_I8_GENO) return SSNAL_EN_ENOTSUP;  // genotype codes: not in this build yet
   ssnal_en_options o;
   if (opts)
     o = *opts;
@@ -628,7 +669,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   if (s == SSNAL_EN_OK &&
       cudaMemsetAsync(c->tile_ctr, 0, sizeof(unsigned) * ((c->m + 31) / 32), c->stream) != cudaSuccess)
     s = SSNAL_EN_ECUDA;
-  if (s == SSNAL_EN_OK) {
+  if (s == SSNAL_EN_OK && c->dtype == SSNAL_EN_F64) {
     // one pass over A: may the stream use the float-float split?
     launch_check_range((const double*)c->A, c->lda, (int)c->m, c->n, &c->st->overflow, c->sms, c->stream);
     if (read_state(c) != SSNAL_EN_OK) s = SSNAL_EN_ECUDA;
@@ -636,7 +677,13 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   }
   if (s == SSNAL_EN_OK && cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
   if (s == SSNAL_EN_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
-  if (s == SSNAL_EN_OK && c->ff_ok && c->opt.precision != 3) {
+  if (s == SSNAL_EN_OK && c->dtype != SSNAL_EN_F64) {
+    // BF16 / FP32 storage: the lane stream reads A directly through a tensor map
+    c->tmap_ok = (tensor_map_bytes() <= sizeof(c->tmap) &&
+                  make_elt_tensor_map(c->tmap, c->A, c->dtype, c->lda, (int)c->m, c->n)) ? 1 : 0;
+    if (!c->tmap_ok) s = SSNAL_EN_ENOTSUP;
+  }
+  if (s == SSNAL_EN_OK && c->dtype == SSNAL_EN_F64 && c->ff_ok && c->opt.precision != 3) {
     // float-pair copy of A read by the stream (same bytes as A); without it the
     // stream splits each FP64 entry on the fly
     const int64_t mm = (c->m + 1) & ~1LL;
@@ -801,6 +848,20 @@ ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* c, const double* y, double* u) {
   if (!c || !y || !u) return SSNAL_EN_EINVAL;
   ProxParams pp = make_pp(1.0, 0.0, 0.0);
   run_stream(c, kModeU, y, u, nullptr, nullptr, pp);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_op_at_d(ssnal_en_ctx* c, const double* d, double* t) {
+  if (!c || !d || !t) return SSNAL_EN_EINVAL;
+  const ssnal_en_options& o = c->opt;
+  ProxParams pp = make_pp(1.0, 0.0, 0.0);
+  if (c->stream_kind == kStreamLane)  // the Newton pass's element type, without the trial sums
+    launch_stream_lane(kModeU, lane_elt(c, kModeT), c->tmap, (int)c->m, c->n, d, t, nullptr, nullptr, pp, o.mu,
+                       o.beta, o.max_ls, o.ls_fused, c->st, c->partials, c->sms, c->stream);
+  else
+    run_stream(c, kModeU, d, t, nullptr, nullptr, pp);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   return SSNAL_EN_OK;

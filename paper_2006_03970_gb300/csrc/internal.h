@@ -65,6 +65,8 @@ constexpr int kStreamDfma = 0;         // FP64 FMA per element
 constexpr int kStreamFloatFloat = 16;  // float-float on the FP32 pipe (entries 0 or in [2^-100, 2^100])
 constexpr int kStreamSplit = 17;       // same arithmetic on a pre-split float-pair copy of A (packed f32x2)
 constexpr int kStreamLane = 18;        // pre-split copy, lane per column, 2-D TMA tiles (tensor map)
+// element types of the lane stream (see kern_stream.cu)
+constexpr int kLaneSplit = 0, kLaneBf16FF = 1, kLaneBf16 = 2, kLaneF32FF = 3, kLaneF32 = 4;
 enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
 
 struct ProxParams {
@@ -135,7 +137,8 @@ int stream_grid(int sms);
 // Tensor map (opaque bytes, tensor_map_bytes() of them) over the pre-split copy.
 bool make_split_tensor_map(void* map_out, const void* split, int m, long long n);
 size_t tensor_map_bytes();
-void launch_stream_lane(int mode, const void* map, int m, long long n, const double* vec, double* out,
+bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda, int m, long long n);
+void launch_stream_lane(int mode, int elt, const void* map, int m, long long n, const double* vec, double* out,
                         const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls, int fused,
                         DevState* st, double* partials, int sms, cudaStream_t s);
 void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s);

@@ -11,6 +11,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "../../include/ssnal_en.h"
 #include "common.cuh"
 
 namespace ssnal {
@@ -663,6 +664,37 @@ constexpr int kLThreads = kLWarps * 32;
 constexpr int kLCols = 64;                   // columns per group: lane l owns columns l and l + 32
 constexpr int kLBoxBytes = kLCols * 128;     // 64 columns x 16 rows x 8 bytes
 
+// Stored element types the lane stream reads.  Every 2-D TMA box is 128 bytes
+// of one column (the inner dimension) by 64 columns; kEltRows rows per box.
+constexpr int kEltSplit = 0;    // pre-split FP64 copy: (hi, hi, lo, lo) per row pair, float-float
+constexpr int kEltBf16FF = 1;   // BF16, float-float accumulation (products of the exact values)
+constexpr int kEltBf16 = 2;     // BF16, FP32 accumulation
+constexpr int kEltF32FF = 3;    // FP32, float-float accumulation
+constexpr int kEltF32 = 4;      // FP32, FP32 accumulation
+__host__ __device__ constexpr int elt_rows(int elt) {
+  return elt == kEltSplit ? 16 : (elt == kEltBf16FF || elt == kEltBf16) ? 64 : 32;
+}
+// elements of the inner box dimension (128 bytes)
+__host__ __device__ constexpr int elt_box_inner(int elt) { return (elt == kEltBf16FF || elt == kEltBf16) ? 64 : 32; }
+__host__ __device__ constexpr bool elt_ff(int elt) { return elt == kEltSplit || elt == kEltBf16FF || elt == kEltF32FF; }
+
+// (S, L) += a * d on an element pair, a exact in FP32 (no low part)
+__device__ __forceinline__ void ff2_madd_exact(unsigned long long& S, unsigned long long& L, unsigned long long a,
+                                               unsigned long long dh, unsigned long long ndh, unsigned long long ndl) {
+  const unsigned long long p = f2mul(a, dh);
+  unsigned long long ne = f2fma(a, ndh, p);  // -(exact product error)
+  ne = f2fma(a, ndl, ne);
+  const unsigned long long s = f2add(S, p);
+  const unsigned long long z = f2sub(s, S);
+  const unsigned long long t = f2add(f2sub(S, f2sub(s, z)), f2sub(p, z));
+  S = s;
+  L = f2add(L, f2sub(t, ne));
+}
+// two BF16 values of one 32-bit word (memory order) as a packed FP32 pair
+__device__ __forceinline__ unsigned long long bf16x2_to_f32x2(unsigned w) {
+  return (unsigned long long)(w << 16) | ((unsigned long long)(w & 0xFFFF0000u) << 32);
+}
+
 struct LaneCfg {
   int stages;        // ring depth per warp
   int chunks;        // boxes per column group (16 rows each)
@@ -677,14 +709,16 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map
       : "memory");
 }
 
-template <int MODE>
+template <int MODE, int ELT>
 __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_constant__ CUtensorMap tmap, int m, long long n,
                                                               const double* __restrict__ vec, double* __restrict__ out,
                                                               const double* __restrict__ x,
                                                               const double* __restrict__ u, LsParams lp, DevState* st,
                                                               double* __restrict__ partials, LaneCfg cfg) {
   extern __shared__ __align__(1024) unsigned char smem_lane[];
-  const int mpad = (m + 63) & ~63;
+  constexpr int R = elt_rows(ELT);   // rows per box
+  constexpr int P = R / 16;          // row pairs per 16-byte chunk of a column
+  const int mpad = (m + 127) & ~127;
   unsigned char* ring = smem_lane;  // [kLWarps][stages][kLBoxBytes]
   float4* D4 = reinterpret_cast<float4*>(smem_lane + (size_t)kLWarps * cfg.stages * kLBoxBytes);
   float2* DL = reinterpret_cast<float2*>(D4 + mpad / 2);
@@ -742,7 +776,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     const int sidx = (int)(item % cfg.stages);
     const unsigned bar = smem_u32(wbars + sidx);
     mbar_expect_tx(bar, kLBoxBytes);
-    tma_load_2d(smem_u32(wring + (size_t)sidx * kLBoxBytes), &tmap, ch * 32,
+    tma_load_2d(smem_u32(wring + (size_t)sidx * kLBoxBytes), &tmap, ch * elt_box_inner(ELT),
                 (int)(((long long)blockIdx.x + q * gridDim.x) * kLCols), bar);
   };
   if (lane == 0)
@@ -765,17 +799,46 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
       }
       const int ch = warp + kLWarps * k;
       const unsigned char* colbase = wring + (size_t)sidx * kLBoxBytes + lane * 128;
-      const ulonglong2* D4p = reinterpret_cast<const ulonglong2*>(D4 + ch * 8);
-      const unsigned long long* DLp = reinterpret_cast<const unsigned long long*>(DL + ch * 8);
+      const ulonglong2* D4p = reinterpret_cast<const ulonglong2*>(D4 + ch * (R / 2));
+      const unsigned long long* DLp = reinterpret_cast<const unsigned long long*>(DL + ch * (R / 2));
 #pragma unroll
       for (int p = 0; p < 8; p++) {
         const int pp = (p + lane) & 7;
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(colbase + pp * 16);
-        const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(colbase + 32 * 128 + pp * 16);
-        const ulonglong2 d = D4p[pp];
-        const unsigned long long dl = DLp[pp];
-        ff2_madd(S2, L2, a.x, a.y, d.x, d.y, dl);
-        ff2_madd(S2b, L2b, b.x, b.y, d.x, d.y, dl);
+        if constexpr (ELT == kEltSplit) {
+          const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(colbase + pp * 16);
+          const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(colbase + 32 * 128 + pp * 16);
+          const ulonglong2 d = D4p[pp];
+          const unsigned long long dl = DLp[pp];
+          ff2_madd(S2, L2, a.x, a.y, d.x, d.y, dl);
+          ff2_madd(S2b, L2b, b.x, b.y, d.x, d.y, dl);
+        } else {
+          const uint4 a = *reinterpret_cast<const uint4*>(colbase + pp * 16);
+          const uint4 b = *reinterpret_cast<const uint4*>(colbase + 32 * 128 + pp * 16);
+          unsigned long long ap[P], bp[P];
+          if constexpr (P == 4) {  // 8 BF16 rows
+            ap[0] = bf16x2_to_f32x2(a.x); ap[1] = bf16x2_to_f32x2(a.y);
+            ap[2] = bf16x2_to_f32x2(a.z); ap[3] = bf16x2_to_f32x2(a.w);
+            bp[0] = bf16x2_to_f32x2(b.x); bp[1] = bf16x2_to_f32x2(b.y);
+            bp[2] = bf16x2_to_f32x2(b.z); bp[3] = bf16x2_to_f32x2(b.w);
+          } else {  // 4 FP32 rows
+            ap[0] = (unsigned long long)a.x | ((unsigned long long)a.y << 32);
+            ap[1] = (unsigned long long)a.z | ((unsigned long long)a.w << 32);
+            bp[0] = (unsigned long long)b.x | ((unsigned long long)b.y << 32);
+            bp[1] = (unsigned long long)b.z | ((unsigned long long)b.w << 32);
+          }
+#pragma unroll
+          for (int e = 0; e < P; e++) {
+            const ulonglong2 d = D4p[P * pp + e];
+            if constexpr (elt_ff(ELT)) {
+              const unsigned long long dl = DLp[P * pp + e];
+              ff2_madd_exact(S2, L2, ap[e], d.x, d.y, dl);
+              ff2_madd_exact(S2b, L2b, bp[e], d.x, d.y, dl);
+            } else {
+              S2 = f2fma(ap[e], d.x, S2);
+              S2b = f2fma(bp[e], d.x, S2b);
+            }
+          }
+        }
       }
       __syncwarp();
       if (lane == 0 && it + cfg.stages < total) {
@@ -878,13 +941,13 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
 constexpr size_t kLDynMax = 232448 - 12288;  // per-block limit minus the kernel's static shared memory
 
 static size_t lane_smem(int m, int stages) {
-  const int mpad = (m + 63) & ~63;
+  const int mpad = (m + 127) & ~127;
   return (size_t)kLWarps * stages * kLBoxBytes + (size_t)mpad * 12 + (size_t)kLWarps * stages * 8 + 1024;
 }
 
 static int lane_stages(int m) {
   const size_t budget = kLDynMax;  // dynamic shared memory left beside the static part
-  const int mpad = (m + 63) & ~63;
+  const int mpad = (m + 127) & ~127;
   int st = (int)((budget - (size_t)mpad * 12 - 1024) / ((size_t)kLWarps * kLBoxBytes + kLWarps * 8));
   if (st > 8) st = 8;
   return st;
@@ -916,9 +979,39 @@ bool make_split_tensor_map(void* map_out, const void* split, int m, long long n)
   return r == CUDA_SUCCESS;
 }
 
+// Tensor map over A stored as BF16 or FP32 (column-major, lda elements per
+// column, lda * element size a multiple of 16 bytes): boxes of 128 bytes of a
+// column x 64 columns, zero fill past row m.
+bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda, int m, long long n) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const bool bf16 = dtype == SSNAL_EN_BF16;
+  const size_t es = bf16 ? 2 : 4;
+  if ((lda * es) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(lda * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)kLCols};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out),
+                      bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<void*>(A), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
-template <int MODE>
+template <int MODE, int ELT>
 static void launch_lane(const void* map, int m, long long n, const double* vec, double* out, const double* x,
                         const double* u, LsParams lp, DevState* st, double* partials, int sms, cudaStream_t s) {
   static bool configured[64] = {};
@@ -926,32 +1019,45 @@ static void launch_lane(const void* map, int m, long long n, const double* vec, 
   cudaGetDevice(&dev);
   const int stages = lane_stages(m);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaFuncSetAttribute(k_stream_lane<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLDynMax);
+    cudaFuncSetAttribute(k_stream_lane<MODE, ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLDynMax);
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   LaneCfg cfg;
   cfg.stages = stages;
-  cfg.chunks = (((m + 1) & ~1) + 15) / 16;
+  cfg.chunks = ELT == kEltSplit ? (((m + 1) & ~1) + 15) / 16 : (m + elt_rows(ELT) - 1) / elt_rows(ELT);
   cfg.groups = (n + kLCols - 1) / kLCols;
   long long grid = cfg.groups;
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(map);
-  k_stream_lane<MODE><<<(int)grid, kLThreads, lane_smem(m, stages), s>>>(*tm, m, n, vec, out, x, u, lp, st, partials,
-                                                                         cfg);
+  k_stream_lane<MODE, ELT><<<(int)grid, kLThreads, lane_smem(m, stages), s>>>(*tm, m, n, vec, out, x, u, lp, st,
+                                                                              partials, cfg);
 }
 
-void launch_stream_lane(int mode, const void* map, int m, long long n, const double* vec, double* out,
+template <int ELT>
+static void launch_lane_modes(int mode, const void* map, int m, long long n, const double* vec, double* out,
+                              const double* x, const double* u, LsParams lp, DevState* st, double* partials, int sms,
+                              cudaStream_t s) {
+  if (mode == kModeU)
+    launch_lane<kModeU, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+  else if (mode == kModeT)
+    launch_lane<kModeT, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+  else
+    launch_lane<kModeGmax, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+}
+
+void launch_stream_lane(int mode, int elt, const void* map, int m, long long n, const double* vec, double* out,
                         const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls, int fused,
                         DevState* st, double* partials, int sms, cudaStream_t s) {
   LsParams lp{pp, mu, beta, max_ls, fused};
   count_launch();
-  if (mode == kModeU)
-    launch_lane<kModeU>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
-  else if (mode == kModeT)
-    launch_lane<kModeT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
-  else
-    launch_lane<kModeGmax>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+  switch (elt) {
+    case kEltBf16FF: launch_lane_modes<kEltBf16FF>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
+    case kEltBf16: launch_lane_modes<kEltBf16>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
+    case kEltF32FF: launch_lane_modes<kEltF32FF>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
+    case kEltF32: launch_lane_modes<kEltF32>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
+    default: launch_lane_modes<kEltSplit>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
+  }
 }
 
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,
