@@ -404,14 +404,14 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_chol_solve_small(c->G, c->ldg, N, c->st, c->h, c->q, 1.0, s);
     } else {
       wd = chol_factor(c->G, c->ldg, N, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
-      launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, wd, s);
+      launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, wd, c->st, s);
     }
     for (int it = 0; it < refine; it++) {
       // resr = h - kappa^{-1} q - A_J^T (A_J q)
       launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->tmpm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr,
                     nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
       launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
-      launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, wd, s);
+      launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, wd, c->st, s);
     }
     launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, which, yv, bv, g, c->st,
                   c->comb_scratch, c->cpart, c->tile_ctr, s);
@@ -427,14 +427,14 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_chol_solve_small(c->G, c->ldg, m, c->st, g, d, -1.0, s);
     } else {
       wd = chol_factor(c->G, c->ldg, m, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
-      launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, wd, s);
+      launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, wd, c->st, s);
     }
     for (int it = 0; it < refine; it++) {
       // tmpm = -g - d - kappa A_J (A_J^T d)
       launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
       launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
                     nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
-      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, wd, s);
+      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, wd, c->st, s);
     }
     if (dots)
       launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);

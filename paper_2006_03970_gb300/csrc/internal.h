@@ -118,7 +118,7 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
                              double alpha, cudaStream_t s);
 // acc = (first ? alpha c : acc + alpha c) with (L L^T) c = rhs
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
-                     double alpha, const float* Wdiag, cudaStream_t s);
+                     double alpha, const float* Wdiag, DevState* st, cudaStream_t s);
 
 // ---- tensor-core SYRK (kern_tc.cu)
 size_t syrk_tc_panel_elems(int R, int K, int nsplit);

@@ -1012,6 +1012,256 @@ __global__ void __launch_bounds__(kBlkThreads) k_trsv_blk(const float* __restric
 }
 
 // ---------------------------------------------------------------------------
+// Triangular solves with the inverse diagonal blocks W_II = L_II^{-1} for any N
+// up to kMaxM, spread over an 8-CTA cluster.  Row block I (32 rows) belongs to
+// warp I / 8 of CTA I mod 8; lane l of that warp owns row 32I + l.  Forward
+// pass: the owner of block J subtracts L[J, I] z_I for every I < J as soon as
+// z_I has arrived (its tile of L is loaded one step ahead into registers), then
+// forms z_J = W_JJ r_J and stores it into every CTA's shared memory with st.async,
+// completing on that CTA's mbarrier for block J.  The backward pass runs the
+// same way with L^T.  Only 32 values per block cross the cluster; each CTA reads
+// just its own rows of L (from L2).  Every wait is bounded (DevState::timeout).
+constexpr int kTrsvCL = 8;        // CTAs per cluster
+constexpr int kTrsvCLMaxT = 128;  // 4096 / 32 row blocks
+
+__device__ __forceinline__ void st_async_f32(unsigned addr, float v, unsigned bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+               "r"(__float_as_uint(v)), "r"(bar)
+               : "memory");
+}
+
+__global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
+    k_trsv_cluster(const float* __restrict__ L, long long ld, int N, const double* __restrict__ rhs,
+                   double* __restrict__ acc, int first, double alpha, const float* __restrict__ Wd, DevState* st) {
+  cgx::cluster_group cluster = cgx::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(16) float tcl[];
+  const int T = (N + 31) / 32;
+  float* zbuf = tcl;                 // T x 32: z_I (forward)
+  float* cbuf = tcl + T * 32;        // T x 32: c_I (backward)
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(tcl + 2 * T * 32);  // 2T: forward, backward
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = tid; k < 2 * T; k += blockDim.x) {
+    mbar_init(smem_u32(bars + k), 1);
+    mbar_expect_tx(smem_u32(bars + k), 128);  // the single arrival; the 128 bytes come from the owner
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  cluster.sync();
+  const int J = rank + kTrsvCL * warp;  // this warp's row block
+  bool ok = true;
+  if (J < T) {
+    const int row = 32 * J + lane;
+    const bool live = row < N;
+    float r = live ? (float)rhs[row] : 0.0f;
+    const float* Wb = Wd + (long long)J * 1024;
+    // ---- forward: z = L^{-1} rhs
+    float a[32], an[32];
+    auto load_row_tile = [&](float* dst, int I) {  // L[row, 32I .. 32I+31]
+#pragma unroll
+      for (int q = 0; q < 32; q++) dst[q] = live ? L[row + (long long)(32 * I + q) * ld] : 0.0f;
+    };
+    if (J > 0) load_row_tile(a, 0);
+    for (int I = 0; I < J; I++) {
+      if (I + 1 < J) load_row_tile(an, I + 1);
+      if (ok && !mbar_wait(smem_u32(bars + I), 0u)) ok = false;
+      const float4* z4 = reinterpret_cast<const float4*>(zbuf + I * 32);
+      float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+      for (int g = 0; g < 8; g++) {
+        const float4 z = z4[g];
+        s0 = fmaf(a[4 * g], z.x, s0);
+        s1 = fmaf(a[4 * g + 1], z.y, s1);
+        s0 = fmaf(a[4 * g + 2], z.z, s0);
+        s1 = fmaf(a[4 * g + 3], z.w, s1);
+      }
+      r -= s0 + s1;
+#pragma unroll
+      for (int q = 0; q < 32; q++) a[q] = an[q];
+    }
+    {
+      // z_J = W_JJ r_J: lane l takes row l of W, the entries of r from the other lanes
+      float w[32];
+#pragma unroll
+      for (int g = 0; g < 8; g++) {
+        const float4 v = reinterpret_cast<const float4*>(Wb + lane * 32)[g];
+        w[4 * g] = v.x; w[4 * g + 1] = v.y; w[4 * g + 2] = v.z; w[4 * g + 3] = v.w;
+      }
+      float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 32; q += 2) {
+        z0 = fmaf(w[q], __shfl_sync(0xffffffffu, r, q), z0);
+        z1 = fmaf(w[q + 1], __shfl_sync(0xffffffffu, r, q + 1), z1);
+      }
+      r = z0 + z1;
+    }
+    {
+      const unsigned dst = smem_u32(zbuf + J * 32 + lane), bar = smem_u32(bars + J);
+#pragma unroll 1
+      for (int c = 0; c < kTrsvCL; c++) st_async_f32(cluster_addr(dst, c), r, cluster_addr(bar, c));
+    }
+    // ---- backward: c = L^{-T} z
+    auto load_col_tile = [&](float* dst, int I) {  // L[32I .. 32I+31, row] (column `row` of L)
+      const int nrow = min(32, N - 32 * I);
+      if (live && nrow == 32) {
+#pragma unroll
+        for (int g = 0; g < 8; g++) {
+          const float4 v = *reinterpret_cast<const float4*>(L + 32 * I + 4 * g + (long long)row * ld);
+          dst[4 * g] = v.x; dst[4 * g + 1] = v.y; dst[4 * g + 2] = v.z; dst[4 * g + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; q++) dst[q] = (live && q < nrow) ? L[32 * I + q + (long long)row * ld] : 0.0f;
+      }
+    };
+    if (J < T - 1) load_col_tile(a, T - 1);
+    for (int I = T - 1; I > J; I--) {
+      if (I - 1 > J) load_col_tile(an, I - 1);
+      if (ok && !mbar_wait(smem_u32(bars + T + I), 0u)) ok = false;
+      const float4* c4 = reinterpret_cast<const float4*>(cbuf + I * 32);
+      float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+      for (int g = 0; g < 8; g++) {
+        const float4 cv = c4[g];
+        s0 = fmaf(a[4 * g], cv.x, s0);
+        s1 = fmaf(a[4 * g + 1], cv.y, s1);
+        s0 = fmaf(a[4 * g + 2], cv.z, s0);
+        s1 = fmaf(a[4 * g + 3], cv.w, s1);
+      }
+      r -= s0 + s1;
+#pragma unroll
+      for (int q = 0; q < 32; q++) a[q] = an[q];
+    }
+    {
+      // c_J = W_JJ^T r_J: lane l takes column l of W
+      float w[32];
+#pragma unroll
+      for (int q = 0; q < 32; q++) w[q] = Wb[q * 32 + lane];
+      float c0 = 0.0f, c1 = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 32; q += 2) {
+        c0 = fmaf(w[q], __shfl_sync(0xffffffffu, r, q), c0);
+        c1 = fmaf(w[q + 1], __shfl_sync(0xffffffffu, r, q + 1), c1);
+      }
+      r = c0 + c1;
+    }
+    if (live) acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
+    {
+      const unsigned dst = smem_u32(cbuf + J * 32 + lane), bar = smem_u32(bars + T + J);
+#pragma unroll 1
+      for (int c = 0; c < kTrsvCL; c++) st_async_f32(cluster_addr(dst, c), r, cluster_addr(bar, c));
+    }
+  }
+  // every value sent to this CTA has landed before it exits
+  for (int k = tid; k < 2 * T; k += blockDim.x)
+    if (ok && !mbar_wait(smem_u32(bars + k), 0u)) ok = false;
+  if (!ok) st->timeout = 1;
+  __syncthreads();
+  cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Newton systems above kClusterN: right-looking Cholesky over super-blocks of at
+// most kClusterN rows.  Each diagonal super-block is factored by k_chol_cluster
+// (which also leaves its inverse 32x32 diagonal blocks), the rows below it are
+// solved against it by k_trsm_blocks, and the trailing matrix is updated by
+// k_syrk_sub.  The 32x32 inverse diagonal blocks then cover the whole factor,
+// so the solves run in k_trsv_cluster.
+
+// X L^T = A for the R x nk block A = G[r0 .., k0 ..] (in place), L = the factored
+// super-block G[k0 .., k0 ..] with inverse diagonal blocks Wd: blocked forward
+// substitution, X_J = (A_J - sum_{I<J} X_I L_JI^T) W_JJ^T.  One CTA per 32 rows.
+__global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long long ld, int k0, int nk, int r0,
+                                                     int R, const float* __restrict__ Wd) {
+  extern __shared__ float tsm[];
+  const int ldx = nk + 1;  // odd: conflict-free column walks
+  float* Xs = tsm;                 // 32 x ldx: the rows of this CTA
+  float* Ls = Xs + 32 * ldx;       // 32 x ldx: block row J of L (columns < 32 J)
+  float* Ws = Ls + 32 * ldx;       // 32 x 33: W_JJ
+  float* Ys = Ws + 32 * 33;        // 32 x 33
+  const int tid = threadIdx.x;
+  const int rb = r0 + 32 * blockIdx.x, nr = min(32, R - 32 * (int)blockIdx.x);
+  for (int e = tid; e < 32 * nk; e += blockDim.x) {
+    const int r = e & 31, k = e >> 5;
+    Xs[r * ldx + k] = r < nr ? G[(rb + r) + (long long)(k0 + k) * ld] : 0.0f;
+  }
+  const int r = tid >> 3, cg = tid & 7;
+  const int Tk = nk / 32;
+  for (int J = 0; J < Tk; J++) {
+    for (int e = tid; e < 32 * 32 * J; e += blockDim.x) {
+      const int c = e & 31, k = e >> 5;
+      Ls[c * ldx + k] = G[(k0 + 32 * J + c) + (long long)(k0 + k) * ld];
+    }
+    for (int e = tid; e < 1024; e += blockDim.x) Ws[(e >> 5) * 33 + (e & 31)] = Wd[(long long)J * 1024 + e];
+    __syncthreads();
+    float y[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) y[e] = Xs[r * ldx + 32 * J + 4 * cg + e];
+    for (int k = 0; k < 32 * J; k++) {
+      const float x = Xs[r * ldx + k];
+#pragma unroll
+      for (int e = 0; e < 4; e++) y[e] = fmaf(-x, Ls[(4 * cg + e) * ldx + k], y[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) Ys[r * 33 + 4 * cg + e] = y[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      float a = 0.0f;
+#pragma unroll 8
+      for (int q = 0; q < 32; q++) a = fmaf(Ys[r * 33 + q], Ws[(4 * cg + e) * 33 + q], a);
+      Xs[r * ldx + 32 * J + 4 * cg + e] = a;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 32 * nk; e += blockDim.x) {
+    const int rr = e & 31, k = e >> 5;
+    if (rr < nr) G[(rb + rr) + (long long)(k0 + k) * ld] = Xs[rr * ldx + k];
+  }
+}
+
+// C -= X X^T on the lower triangle of the R x R block C = G[r0 .., r0 ..], with
+// X = G[r0 .., k0 .. k0 + nk): 64 x 64 output tiles, K staged 32 at a time.
+__global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long long ld, int r0, int R, int k0, int nk) {
+  __shared__ float As[64 * 33], Bs[64 * 33];
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int i0 = 64 * ti, j0 = 64 * tj;
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  float acc[4][4] = {};
+  for (int kc = 0; kc < nk; kc += 32) {
+    for (int e = tid; e < 64 * 32; e += blockDim.x) {
+      const int i = e & 63, k = e >> 6;
+      const bool kin = kc + k < nk;
+      As[i * 33 + k] = (i0 + i < R && kin) ? G[(r0 + i0 + i) + (long long)(k0 + kc + k) * ld] : 0.0f;
+      Bs[i * 33 + k] = (j0 + i < R && kin) ? G[(r0 + j0 + i) + (long long)(k0 + kc + k) * ld] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 32; k++) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        a[u] = As[(4 * tr + u) * 33 + k];
+        b[u] = Bs[(4 * tc + u) * 33 + k];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int gi = i0 + 4 * tr + u, gj = j0 + 4 * tc + v;
+      if (gi < R && gj < R && gi >= gj) G[(r0 + gi) + (long long)(r0 + gj) * ld] -= acc[u][v];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Larger Newton systems: blocked right-looking Cholesky in ONE cooperative
 // launch.  Phases (diagonal block, panel, trailing update) are separated by a
 // grid barrier with a bounded wait; all CTAs are co-resident (cooperative
@@ -1196,6 +1446,38 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((N + 31) / 32), s>>>(G, ldg, N, st, Wdiag);
     if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
   }
+  if (Wdiag && N <= kMaxM) {
+    // super-blocks of equal size (a multiple of 32, at most kClusterN)
+    static bool done_sb[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t trsm_smem_max = (size_t)(2 * 32 * (kClusterN + 1) + 2 * 32 * 33) * sizeof(float);
+    if (dev < 0 || dev >= 64 || !done_sb[dev]) {
+      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
+      cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem_max);
+      if (dev >= 0 && dev < 64) done_sb[dev] = true;
+    }
+    const int nb = (N + kClusterN - 1) / kClusterN;
+    const int B = ((N + nb - 1) / nb + 31) / 32 * 32;
+    bool launched = true;
+    for (int k0 = 0; k0 < N && launched; k0 += B) {
+      const int nk = N - k0 < B ? N - k0 : B;
+      float* Gkk = G + k0 + (long long)k0 * ldg;
+      count_launch();
+      k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((nk + 31) / 32), s>>>(Gkk, ldg, nk, st,
+                                                                             Wdiag + (long long)(k0 / 32) * 1024);
+      const int r0 = k0 + nk, R = N - r0;
+      if (R > 0) {
+        count_launch(2);
+        const size_t tsm = (size_t)(2 * 32 * (nk + 1) + 2 * 32 * 33) * sizeof(float);
+        k_trsm_blocks<<<(R + 31) / 32, 256, tsm, s>>>(G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024);
+        const int nt = (R + 63) / 64;
+        k_syrk_sub<<<nt * (nt + 1) / 2, 256, 0, s>>>(G, ldg, r0, R, k0, nk);
+      }
+      launched = cudaGetLastError() == cudaSuccess;
+    }
+    if (launched) return true;
+  }
   {
     // one cooperative launch; the grid barrier counters live in DevState
     int dev = 0, sms = 0, per_sm = 0;
@@ -1237,13 +1519,29 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 }
 
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
-                     double alpha, const float* Wdiag, cudaStream_t s) {
+                     double alpha, const float* Wdiag, DevState* st, cudaStream_t s) {
   if (N <= 0) return;
   if (N <= kSmallN) {
     small_smem_attr();
     count_launch();
     k_trsv_small<<<1, kSmallThreads, kSmallSmem, s>>>(L, ldl, N, rhs, acc, first, alpha);
     return;
+  }
+  if (Wdiag && N <= 32 * kTrsvCLMaxT) {
+    const int T = (N + 31) / 32;
+    const int warps = (T + kTrsvCL - 1) / kTrsvCL;
+    const size_t smem = (size_t)2 * T * 32 * sizeof(float) + (size_t)2 * T * 8;
+    static bool done_cl[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done_cl[dev]) {
+      cudaFuncSetAttribute(k_trsv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((size_t)2 * kTrsvCLMaxT * 32 * sizeof(float) + (size_t)2 * kTrsvCLMaxT * 8));
+      if (dev >= 0 && dev < 64) done_cl[dev] = true;
+    }
+    count_launch();
+    k_trsv_cluster<<<kTrsvCL, 32 * warps, smem, s>>>(L, ldl, N, rhs, acc, first, alpha, Wdiag, st);
+    if (cudaGetLastError() == cudaSuccess) return;
   }
   if (Wdiag && N <= kClusterN) {
     static bool done_blk[64] = {};
