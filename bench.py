@@ -262,6 +262,8 @@ def run_gpu(args):
                     "d2h_bytes_per_step": 8 * len(grid) * ctx.n},
             "gpu_launches": prof1["kernel_launches"] - prof0["kernel_launches"],
             "roofline": roofline}
+    if rank == 0 and world == 1 and not args.no_mixed:
+        line["mixed_vs_fp64"] = mixed_vs_fp64()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
@@ -273,6 +275,66 @@ def run_gpu(args):
     return 0
 
 
+def mixed_vs_fp64(steps=3):
+    """The precision configuration on one GPU: m=1000, n=1e6, 50-feature AR(1) blocks (rho 0.5),
+    generated in FP32 and standardized; 50 nonzeros +-U[1,3], snr 3, c = 0.3, alpha in {0.5, 0.9}.
+    The mixed form stores A as BF16 (2 GB; FP32-accumulated Newton passes, float-float refresh of
+    u = A^T y before each stopping test); the FP64 form stores the FP32 values as FP64 (8 GB).
+    Reported: fits/s of each form (CUDA events, inputs resident), the mixed/FP64 ratio, the
+    storage+solver error of the mixed solution against the FP64 path's, and the achieved GB/s of
+    the mixed Newton pass."""
+    import numpy as np
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    p = synth.config3()
+    bits = synth.to_bf16_bits(p.At)
+    ctx_m = pkg.Context(bits, dtype=pkg.BF16, options=pkg.ssnal_en_default_options(precision=1))
+    ctx_f = pkg.Context(p.At.astype(np.float64))
+    b = torch.as_tensor(p.b, dtype=torch.float64, device="cuda")
+    grid = np.array([0.3])
+    out = {"workload": "m=1000, n=1000000, 50-feature AR(1) blocks rho=0.5, FP32 generated and "
+                       "standardized, 50 nonzeros +-U[1,3], snr 3, c=0.3, seed 3",
+           "mixed": "A in BF16 (2 GB), FP32-accumulated Newton passes, float-float u refresh, "
+                    "BF16 tensor-core SYRK, FP32 Cholesky + FP64 refinement, FP64 KKT",
+           "fp64": "A in FP64 (8 GB), float-float passes over the pre-split copy",
+           "cases": []}
+    stream = torch.cuda.current_stream()
+    for alpha in (0.5, 0.9):
+        case = {"alpha": alpha}
+        xs = {}
+        for name, ctx in (("mixed", ctx_m), ("fp64", ctx_f)):
+            X = torch.zeros((1, ctx.n), dtype=torch.float64, device="cuda")
+            pkg.ssnal_en_path(ctx.ctx, b, alpha, grid, X)
+            torch.cuda.synchronize()
+            pkg.ssnal_en_profile(ctx.ctx, True, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ok = 0
+            for _ in range(steps):
+                st, res, done = pkg.ssnal_en_path(ctx.ctx, b, alpha, grid, X)
+                ok += _count_fits(res, done)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = pkg.ssnal_en_profile(ctx.ctx, False, False)
+            ms = e0.elapsed_time(e1) / steps
+            r = res[0]
+            case[name] = {"fits_per_s": (ok / steps) / (ms / 1e3), "ms_per_fit": ms, "kkt1": r.kkt1,
+                          "kkt3": r.kkt3, "al_iters": r.al_iters, "newton_iters": r.newton_iters,
+                          "active": r.active,
+                          "stream_gbs": (prof["stream_bytes"] / (prof["stream_ms"] / 1e3) / 1e9)
+                          if prof["stream_ms"] > 0 else None}
+            xs[name] = X[0].cpu().numpy()
+        case["mixed_over_fp64"] = case["mixed"]["fits_per_s"] / case["fp64"]["fits_per_s"]
+        xm, xf = xs["mixed"], xs["fp64"]
+        case["x_rel_err_mixed_vs_fp64"] = float(np.abs(xm - xf).max() / max(np.abs(xf).max(), 1e-300))
+        case["support_mixed_fp64"] = [int(np.count_nonzero(xm)), int(np.count_nonzero(xf))]
+        out["cases"].append(case)
+    ctx_m.close()
+    ctx_f.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -280,6 +342,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the BF16-vs-FP64 precision comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -42,7 +42,8 @@ typedef enum {
   SSNAL_EN_F64 = 0,      /* double */
   SSNAL_EN_F32 = 1,      /* float */
   SSNAL_EN_BF16 = 2,     /* bfloat16 bit patterns (uint16) */
-  SSNAL_EN_I8_GENO = 3   /* int8 codes; entry = (code - col_mean[j]) * col_scale[j] */
+  SSNAL_EN_I8_GENO = 3   /* int8 codes; entry = (code - col_mean[j]) * col_scale[j], evaluated in FP64
+                            from the FP32 mean and scale (standardization applied on the fly) */
 } ssnal_en_dtype;
 
 typedef enum {
@@ -82,11 +83,11 @@ typedef struct {
                            keeps a float-pair copy of A (same size as A) made at create time.
                            3: as 0 but without the copy (entries split on the fly, slower).
                            2: FP64 FMAs always.
-                           1: mixed precision, for A stored as BF16 or FP32: the Newton-step passes
+                           1: mixed precision, for A stored as BF16, FP32 or I8_GENO: the Newton-step passes
                            t = A^T d sum the products in FP32; u = A^T y is recomputed in
                            float-float before every SsN stopping test, so the KKT test, the
                            x update and the duality gap use FP64-accurate values.
-                           With BF16 / FP32 storage and precision 0, 2 or 3 every pass over A
+                           With BF16 / FP32 / I8_GENO storage and precision 0, 2 or 3 every pass over A
                            is float-float (products of the stored values are exact). */
   int32_t refine_steps; /* 1: iterative-refinement steps of the Newton solve (FP64 residual through
                            the packed A_J, FP32 factor) */
@@ -123,11 +124,12 @@ const char* ssnal_en_status_string(int32_t status);
 /* Creates a context for the matrix *A.  opts may be NULL (defaults).  stream is
  * a cudaStream_t (NULL = the legacy default stream).  Allocates the device
  * workspaces (vectors of length n and m, the A_J panel, the Newton matrix).
- * F64, F32 and BF16 storage are supported (I8_GENO returns ENOTSUP in this
- * build).  F64 storage is copied once into a float-pair form for the stream
- * (precision 0, see ssnal_en_options); F32 / BF16 storage is streamed in place.
+ * F64 storage is copied once into a float-pair form for the stream (precision 0,
+ * see ssnal_en_options); F32, BF16 and I8_GENO storage is streamed in place
+ * (I8_GENO needs col_mean and col_scale; lda * element size a multiple of 16).
  * Errors: EINVAL (null pointers, m <= 0, n <= 0, lda < m, misaligned lda or
- * data, unknown dtype), ENOTSUP (m above 4096, I8_GENO), ENOMEM, ECUDA. */
+ * data, unknown dtype, I8_GENO without mean/scale), ENOTSUP (m above 4096), ENOMEM,
+ * ECUDA. */
 ssnal_en_status ssnal_en_create(ssnal_en_ctx** ctx, const ssnal_en_matrix* A,
                                 const ssnal_en_options* opts, void* stream);
 
@@ -206,7 +208,7 @@ ssnal_en_status ssnal_en_op_at_y(ssnal_en_ctx* ctx, const double* y, double* u);
 
 /* t = A^T d accumulated as in the solver's Newton steps (the pass of Algorithm 1
  * that feeds the line search of eq. line_search): in the mixed precision mode
- * (precision = 1 with BF16 or FP32 storage) the products are summed in FP32,
+ * (precision = 1 with BF16, FP32 or I8_GENO storage) the products are summed in FP32,
  * otherwise exactly as ssnal_en_op_at_y.  d device length m (FP64), t device
  * length n (FP64).  Errors: EINVAL (null pointer), ECUDA. */
 ssnal_en_status ssnal_en_op_at_d(ssnal_en_ctx* ctx, const double* d, double* t);

@@ -199,8 +199,8 @@ void free_all(ssnal_en_ctx* c) {
 // exists, float-float with on-the-fly splitting, or FP64 FMAs (precision = 2 or
 // entries outside the range of the split).
 void set_stream_kind(ssnal_en_ctx* c) {
-  if (c->dtype == SSNAL_EN_BF16 || c->dtype == SSNAL_EN_F32) {
-    // BF16 / FP32 storage: the lane stream over A itself (tensor map built at create)
+  if (c->dtype != SSNAL_EN_F64) {
+    // BF16 / FP32 / genotype storage: the lane stream over A itself (tensor map built at create)
     c->stream_kind = kStreamLane;
     c->A_stream = c->A;
     c->lda_stream = c->lda;
@@ -297,13 +297,14 @@ int lane_elt(const ssnal_en_ctx* c, int mode) {
   const bool plain = c->opt.precision == 1 && mode == kModeT;
   if (c->dtype == SSNAL_EN_BF16) return plain ? kLaneBf16 : kLaneBf16FF;
   if (c->dtype == SSNAL_EN_F32) return plain ? kLaneF32 : kLaneF32FF;
+  if (c->dtype == SSNAL_EN_I8_GENO) return plain ? kLaneI8 : kLaneI8FF;
   return kLaneSplit;
 }
 
 // True when the Newton passes are accumulated in FP32: u then drifts from A^T y
 // by FP32 rounding and is recomputed before the KKT test.
 bool mixed_stream(const ssnal_en_ctx* c) {
-  return c->opt.precision == 1 && (c->dtype == SSNAL_EN_BF16 || c->dtype == SSNAL_EN_F32);
+  return c->opt.precision == 1 && c->dtype != SSNAL_EN_F64;
 }
 
 // BF16 parts per panel entry in the tensor-core SYRK: a BF16-stored A_J is
@@ -315,7 +316,7 @@ void run_stream(ssnal_en_ctx* c, int mode, const double* vec, double* out, const
   const ssnal_en_options& o = c->opt;
   if (c->stream_kind == kStreamLane)
     launch_stream_lane(mode, lane_elt(c, mode), c->tmap, (int)c->m, c->n, vec, out, x, u, pp, o.mu, o.beta, o.max_ls,
-                       o.ls_fused, c->st, c->partials, c->sms, c->stream);
+                       o.ls_fused, c->st, c->partials, c->sms, c->stream, c->col_mean, c->col_scale);
   else
     launch_stream(mode, c->stream_kind, c->A_stream, c->lda_stream, (int)c->m, c->n, vec, out, x, u, pp, o.mu,
                   o.beta, o.max_ls, o.ls_fused, c->st, c->partials, c->grid_stream, c->stream);
@@ -356,7 +357,7 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
                     c->vpartials, c->grid_vec, s);
   launch_prox_scatter(mode, x, c->u, c->n, pp, c->counts + c->grid_vec, c->J, c->wJ, c->grid_vec, s);
   launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, -1, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms,
-                s);
+                s, c->col_mean, c->col_scale);
   launch_grad(c, mode, b, -1);
   }
   CK(cudaGetLastError());
@@ -369,7 +370,7 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
     if ((st = grow_panel(c, r)) != SSNAL_EN_OK) return st;
     CK(cudaMemsetAsync(&c->st->overflow, 0, sizeof(int32_t), s));
     launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32,
-                  c->sms, s);
+                  c->sms, s, c->col_mean, c->col_scale);
     launch_grad(c, mode, b, r);
     CK(cudaGetLastError());
     if ((st = read_state(c)) != SSNAL_EN_OK) return st;
@@ -604,7 +605,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   if ((A->lda * (int64_t)es) % 16 != 0 || ((uintptr_t)A->data) % 16 != 0) return SSNAL_EN_EINVAL;
   if (A->n >= (int64_t)0x7fffffff) return SSNAL_EN_ENOTSUP;
   if (A->m > kMaxM) return SSNAL_EN_ENOTSUP;
-  if (A->dtype == SSNAL_EN_I8_GENO) return SSNAL_EN_ENOTSUP;  // genotype codes: not in this build yet
+  if (A->dtype == SSNAL_EN_I8_GENO && (!A->col_mean || !A->col_scale)) return SSNAL_EN_EINVAL;
   ssnal_en_options o;
   if (opts)
     o = *opts;
@@ -859,7 +860,7 @@ ssnal_en_status ssnal_en_op_at_d(ssnal_en_ctx* c, const double* d, double* t) {
   ProxParams pp = make_pp(1.0, 0.0, 0.0);
   if (c->stream_kind == kStreamLane)  // the Newton pass's element type, without the trial sums
     launch_stream_lane(kModeU, lane_elt(c, kModeT), c->tmap, (int)c->m, c->n, d, t, nullptr, nullptr, pp, o.mu,
-                       o.beta, o.max_ls, o.ls_fused, c->st, c->partials, c->sms, c->stream);
+                       o.beta, o.max_ls, o.ls_fused, c->st, c->partials, c->sms, c->stream, c->col_mean, c->col_scale);
   else
     run_stream(c, kModeU, d, t, nullptr, nullptr, pp);
   CK(cudaGetLastError());
@@ -892,7 +893,8 @@ ssnal_en_status ssnal_en_op_grad(ssnal_en_ctx* c, const int32_t* J, const double
   cudaStream_t s = c->stream;
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   const int m = (int)c->m;
-  launch_gather(c->A, c->dtype, c->lda, m, J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms, s);
+  launch_gather(c->A, c->dtype, c->lda, m, J, c->st, r, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms, s, c->col_mean,
+                c->col_scale);
   launch_gemv_n(c->P, c->ldp, m, wJ, c->st, r, c->rcap, g, y, 1.0, b, 1.0, -1.0, 0, nullptr, nullptr, nullptr, c->st,
                 c->comb_scratch, c->cpart, c->tile_ctr, s);
   CK(cudaGetLastError());

@@ -66,7 +66,8 @@ constexpr int kStreamFloatFloat = 16;  // float-float on the FP32 pipe (entries 
 constexpr int kStreamSplit = 17;       // same arithmetic on a pre-split float-pair copy of A (packed f32x2)
 constexpr int kStreamLane = 18;        // pre-split copy, lane per column, 2-D TMA tiles (tensor map)
 // element types of the lane stream (see kern_stream.cu)
-constexpr int kLaneSplit = 0, kLaneBf16FF = 1, kLaneBf16 = 2, kLaneF32FF = 3, kLaneF32 = 4;
+constexpr int kLaneSplit = 0, kLaneBf16FF = 1, kLaneBf16 = 2, kLaneF32FF = 3, kLaneF32 = 4, kLaneI8FF = 5,
+              kLaneI8 = 6;
 enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
 
 struct ProxParams {
@@ -84,7 +85,8 @@ void launch_prox_scatter(int mode, const double* x, const double* u, long long n
 void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sms, cudaStream_t s);
 void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t* J, const DevState* st,
                    long long r_host, long long rcap, double* P, long long ldp, float* P32, long long ldp32,
-                   int sms, cudaStream_t s);
+                   int sms, cudaStream_t s, const float* cmean = nullptr,
+                   const float* cscale = nullptr);
 void launch_gemv_n_partial(const double* P, long long ldp, int m, const double* coef, const DevState* st,
                            long long r_host, long long rcap, double* part, cudaStream_t s);
 // out = ca*a + cb*b + cs*sum_groups(part); norms selected by `which` (see kern_vec.cu)
@@ -140,7 +142,8 @@ size_t tensor_map_bytes();
 bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda, int m, long long n);
 void launch_stream_lane(int mode, int elt, const void* map, int m, long long n, const double* vec, double* out,
                         const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls, int fused,
-                        DevState* st, double* partials, int sms, cudaStream_t s);
+                        DevState* st, double* partials, int sms, cudaStream_t s, const float* cmean = nullptr,
+                        const float* cscale = nullptr);
 void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s);
 void launch_check_range(const double* A, long long lda, int m, long long n, int* bad, int sms, cudaStream_t s);
 

@@ -724,21 +724,28 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   auto panel_tile = [&](int k, int i) { return panel + ((k % nbuf) * T + i) * 1024; };
   auto pbar = [&](int k) { return pbar0 + 8u * (unsigned)(k % nbuf); };
 
-  // ---- load the owned tiles (identity padding beyond N); consecutive threads
-  //      read consecutive rows of a column
+  // ---- load the owned tiles with 4-byte async copies (all in flight at once;
+  //      consecutive threads read consecutive rows of a column), zero outside
+  //      N x N; then the identity on the padded diagonal.  The strict upper
+  //      triangle of a diagonal tile is copied too and never read.
   for (int sl = 0; sl < nslots; sl++) {
     const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
     float* dst = own + sl * kTileF;
     for (int e = tid; e < 1024; e += 256) {
       const int r = e & 31, c = e >> 5;
       const int gi = ti * 32 + r, gj = tj * 32 + c;
-      float v;
-      if (gi < N && gj < N)
-        v = (gi >= gj) ? G[gi + (long long)gj * ld] : 0.0f;
-      else
-        v = (gi == gj) ? 1.0f : 0.0f;
-      dst[r * 33 + c] = v;
+      const bool in = gi < N && gj < N;
+      const unsigned d = smem_u32(dst + r * 33 + c);
+      const float* src = in ? G + gi + (long long)gj * ld : G;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
     }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  for (int sl = 0; sl < nslots; sl++) {
+    const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+    if (ti == tj && tid < 32 && ti * 32 + tid >= N) own[sl * kTileF + tid * 33 + tid] = 1.0f;
   }
   // panel-column ownership of column j: the CTAs owning a tile (i, j), i > j
   auto receivers_of = [&](int j) {
@@ -1171,36 +1178,47 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 // X L^T = A for the R x nk block A = G[r0 .., k0 ..] (in place), L = the factored
 // super-block G[k0 .., k0 ..] with inverse diagonal blocks Wd: blocked forward
 // substitution, X_J = (A_J - sum_{I<J} X_I L_JI^T) W_JJ^T.  One CTA per 32 rows.
+// Block row J of L is staged k-major (32 consecutive rows per column of L) with
+// cp.async, all chunks in flight at once, so one 128-bit load gives 4 rows.
 __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long long ld, int k0, int nk, int r0,
                                                      int R, const float* __restrict__ Wd) {
-  extern __shared__ float tsm[];
+  extern __shared__ __align__(16) float tsm[];
   const int ldx = nk + 1;  // odd: conflict-free column walks
-  float* Xs = tsm;                 // 32 x ldx: the rows of this CTA
-  float* Ls = Xs + 32 * ldx;       // 32 x ldx: block row J of L (columns < 32 J)
-  float* Ws = Ls + 32 * ldx;       // 32 x 33: W_JJ
-  float* Ys = Ws + 32 * 33;        // 32 x 33
+  float* Ls = tsm;                 // (nk - 32) x 32: block row J of L, column k at Ls + 32 k
+  float* Ws = Ls + 32 * nk;        // 32 x 32: W_JJ, row-major
+  float* Xs = Ws + 1024;           // 32 x ldx: the rows of this CTA
+  float* Ys = Xs + 32 * ldx;       // 32 x 33
   const int tid = threadIdx.x;
   const int rb = r0 + 32 * blockIdx.x, nr = min(32, R - 32 * (int)blockIdx.x);
-  for (int e = tid; e < 32 * nk; e += blockDim.x) {
+  for (int e = tid; e < 32 * nk; e += blockDim.x) {  // 4-byte async copies: all in flight at once
     const int r = e & 31, k = e >> 5;
-    Xs[r * ldx + k] = r < nr ? G[(rb + r) + (long long)(k0 + k) * ld] : 0.0f;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(Xs + r * ldx + k);
+    const float* src = G + (r < nr ? (rb + r) : rb) + (long long)(k0 + k) * ld;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(r < nr ? 4 : 0) : "memory");
   }
   const int r = tid >> 3, cg = tid & 7;
   const int Tk = nk / 32;
   for (int J = 0; J < Tk; J++) {
-    for (int e = tid; e < 32 * 32 * J; e += blockDim.x) {
-      const int c = e & 31, k = e >> 5;
-      Ls[c * ldx + k] = G[(k0 + 32 * J + c) + (long long)(k0 + k) * ld];
+    // stage L[k0 + 32J .. +31, k0 .. k0 + 32J) and W_JJ (16-byte chunks, all in flight)
+    for (int e = tid; e < 8 * 32 * J; e += blockDim.x) {
+      const int c4 = e & 7, k = e >> 3;
+      cp_async16(Ls + 32 * k + 4 * c4, G + (k0 + 32 * J + 4 * c4) + (long long)(k0 + k) * ld, 16);
     }
-    for (int e = tid; e < 1024; e += blockDim.x) Ws[(e >> 5) * 33 + (e & 31)] = Wd[(long long)J * 1024 + e];
+    for (int e = tid; e < 256; e += blockDim.x) cp_async16(Ws + 4 * e, Wd + (long long)J * 1024 + 4 * e, 16);
+    cp_async_commit();
+    cp_async_wait0();
     __syncthreads();
     float y[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) y[e] = Xs[r * ldx + 32 * J + 4 * cg + e];
+#pragma unroll 4
     for (int k = 0; k < 32 * J; k++) {
       const float x = Xs[r * ldx + k];
-#pragma unroll
-      for (int e = 0; e < 4; e++) y[e] = fmaf(-x, Ls[(4 * cg + e) * ldx + k], y[e]);
+      const float4 l = reinterpret_cast<const float4*>(Ls + 32 * k)[cg];
+      y[0] = fmaf(-x, l.x, y[0]);
+      y[1] = fmaf(-x, l.y, y[1]);
+      y[2] = fmaf(-x, l.z, y[2]);
+      y[3] = fmaf(-x, l.w, y[3]);
     }
 #pragma unroll
     for (int e = 0; e < 4; e++) Ys[r * 33 + 4 * cg + e] = y[e];
@@ -1209,7 +1227,7 @@ __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long
     for (int e = 0; e < 4; e++) {
       float a = 0.0f;
 #pragma unroll 8
-      for (int q = 0; q < 32; q++) a = fmaf(Ys[r * 33 + q], Ws[(4 * cg + e) * 33 + q], a);
+      for (int q = 0; q < 32; q++) a = fmaf(Ys[r * 33 + q], Ws[(4 * cg + e) * 32 + q], a);
       Xs[r * ldx + 32 * J + 4 * cg + e] = a;
     }
     __syncthreads();
@@ -1230,12 +1248,18 @@ __global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long lo
   const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
   float acc[4][4] = {};
   for (int kc = 0; kc < nk; kc += 32) {
-    for (int e = tid; e < 64 * 32; e += blockDim.x) {
+    for (int e = tid; e < 64 * 32; e += blockDim.x) {  // 4-byte async copies, zero fill outside
       const int i = e & 63, k = e >> 6;
-      const bool kin = kc + k < nk;
-      As[i * 33 + k] = (i0 + i < R && kin) ? G[(r0 + i0 + i) + (long long)(k0 + kc + k) * ld] : 0.0f;
-      Bs[i * 33 + k] = (j0 + i < R && kin) ? G[(r0 + j0 + i) + (long long)(k0 + kc + k) * ld] : 0.0f;
+      const bool kin = kc + k < nk, ain = i0 + i < R && kin, bin = j0 + i < R && kin;
+      const float* sa = ain ? G + (r0 + i0 + i) + (long long)(k0 + kc + k) * ld : G;
+      const float* sb = bin ? G + (r0 + j0 + i) + (long long)(k0 + kc + k) * ld : G;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(As + i * 33 + k)), "l"(sa),
+                   "r"(ain ? 4 : 0) : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(Bs + i * 33 + k)), "l"(sb),
+                   "r"(bin ? 4 : 0) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < 32; k++) {
@@ -1451,7 +1475,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     static bool done_sb[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    const size_t trsm_smem_max = (size_t)(2 * 32 * (kClusterN + 1) + 2 * 32 * 33) * sizeof(float);
+    const size_t trsm_smem_max = (size_t)(32 * kClusterN + 1024 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float);
     if (dev < 0 || dev >= 64 || !done_sb[dev]) {
       cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
       cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem_max);
@@ -1469,7 +1493,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       const int r0 = k0 + nk, R = N - r0;
       if (R > 0) {
         count_launch(2);
-        const size_t tsm = (size_t)(2 * 32 * (nk + 1) + 2 * 32 * 33) * sizeof(float);
+        const size_t tsm = (size_t)(32 * nk + 1024 + 32 * (nk + 1) + 32 * 33) * sizeof(float);
         k_trsm_blocks<<<(R + 31) / 32, 256, tsm, s>>>(G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024);
         const int nt = (R + 63) / 64;
         k_syrk_sub<<<nt * (nt + 1) / 2, 256, 0, s>>>(G, ldg, r0, R, k0, nk);

@@ -671,12 +671,20 @@ constexpr int kEltBf16FF = 1;   // BF16, float-float accumulation (products of t
 constexpr int kEltBf16 = 2;     // BF16, FP32 accumulation
 constexpr int kEltF32FF = 3;    // FP32, float-float accumulation
 constexpr int kEltF32 = 4;      // FP32, FP32 accumulation
+constexpr int kEltI8FF = 5;     // int8 genotype codes, float-float accumulation
+constexpr int kEltI8 = 6;       // int8 genotype codes, FP32 accumulation
+// The genotype entries are (code - mean_j) * scale_j: the stream sums code * y
+// and applies mean and scale per column, sum_i a_ij y_i = scale_j (sum_i c_ij y_i
+// - mean_j sum_i y_i).
 __host__ __device__ constexpr int elt_rows(int elt) {
-  return elt == kEltSplit ? 16 : (elt == kEltBf16FF || elt == kEltBf16) ? 64 : 32;
+  return elt == kEltSplit ? 16 : (elt == kEltBf16FF || elt == kEltBf16) ? 64 : (elt == kEltI8FF || elt == kEltI8) ? 128 : 32;
 }
+__host__ __device__ constexpr bool elt_i8(int elt) { return elt == kEltI8FF || elt == kEltI8; }
 // elements of the inner box dimension (128 bytes)
-__host__ __device__ constexpr int elt_box_inner(int elt) { return (elt == kEltBf16FF || elt == kEltBf16) ? 64 : 32; }
-__host__ __device__ constexpr bool elt_ff(int elt) { return elt == kEltSplit || elt == kEltBf16FF || elt == kEltF32FF; }
+__host__ __device__ constexpr int elt_box_inner(int elt) { return elt_rows(elt) == 16 ? 32 : elt_rows(elt); }
+__host__ __device__ constexpr bool elt_ff(int elt) {
+  return elt == kEltSplit || elt == kEltBf16FF || elt == kEltF32FF || elt == kEltI8FF;
+}
 
 // (S, L) += a * d on an element pair, a exact in FP32 (no low part)
 __device__ __forceinline__ void ff2_madd_exact(unsigned long long& S, unsigned long long& L, unsigned long long a,
@@ -689,6 +697,14 @@ __device__ __forceinline__ void ff2_madd_exact(unsigned long long& S, unsigned l
   const unsigned long long t = f2add(f2sub(S, f2sub(s, z)), f2sub(p, z));
   S = s;
   L = f2add(L, f2sub(t, ne));
+}
+// bytes k and k + 1 of w (int8 codes, memory order) as a packed FP32 pair of
+// (code + 128) + 2^23; the caller subtracts 2^23 + 128 (exact)
+__device__ __forceinline__ unsigned long long i8x2_biased(unsigned w, int k) {
+  const unsigned x = w ^ 0x80808080u;  // code + 128 in 0..255
+  const unsigned lo = __byte_perm(x, 0x4B000000u, 0x7540u + (unsigned)k);
+  const unsigned hi = __byte_perm(x, 0x4B000000u, 0x7540u + (unsigned)k + 1u);
+  return (unsigned long long)lo | ((unsigned long long)hi << 32);
 }
 // two BF16 values of one 32-bit word (memory order) as a packed FP32 pair
 __device__ __forceinline__ unsigned long long bf16x2_to_f32x2(unsigned w) {
@@ -714,7 +730,9 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
                                                               const double* __restrict__ vec, double* __restrict__ out,
                                                               const double* __restrict__ x,
                                                               const double* __restrict__ u, LsParams lp, DevState* st,
-                                                              double* __restrict__ partials, LaneCfg cfg) {
+                                                              double* __restrict__ partials, LaneCfg cfg,
+                                                              const float* __restrict__ cmean,
+                                                              const float* __restrict__ cscale) {
   extern __shared__ __align__(1024) unsigned char smem_lane[];
   constexpr int R = elt_rows(ELT);   // rows per box
   constexpr int P = R / 16;          // row pairs per 16-byte chunk of a column
@@ -760,6 +778,13 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     DL[k] = make_float2(-l[0], -l[1]);
   }
   __syncthreads();
+
+  double ysum = 0.0;  // sum_i vec_i (genotype mean correction)
+  if constexpr (elt_i8(ELT)) {
+    double a = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) a += vec[i];
+    ysum = block_sum(a, red);
+  }
 
   // ---- work split: the CTA owns column groups g = blockIdx.x + q * gridDim.x;
   // warp w streams row chunks w, w + 8, ... of each group through its own ring.
@@ -820,6 +845,16 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
             ap[2] = bf16x2_to_f32x2(a.z); ap[3] = bf16x2_to_f32x2(a.w);
             bp[0] = bf16x2_to_f32x2(b.x); bp[1] = bf16x2_to_f32x2(b.y);
             bp[2] = bf16x2_to_f32x2(b.z); bp[3] = bf16x2_to_f32x2(b.w);
+          } else if constexpr (P == 8) {  // 16 int8 codes: exact (code + 128 + 2^23) - (2^23 + 128)
+            const unsigned long long bias = 0x4B0000804B000080ull;  // (8388736.0f, 8388736.0f)
+            const unsigned aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              ap[2 * q] = f2sub(i8x2_biased(aw[q], 0), bias);
+              ap[2 * q + 1] = f2sub(i8x2_biased(aw[q], 2), bias);
+              bp[2 * q] = f2sub(i8x2_biased(bw[q], 0), bias);
+              bp[2 * q + 1] = f2sub(i8x2_biased(bw[q], 2), bias);
+            }
           } else {  // 4 FP32 rows
             ap[0] = (unsigned long long)a.x | ((unsigned long long)a.y << 32);
             ap[1] = (unsigned long long)a.z | ((unsigned long long)a.w << 32);
@@ -863,7 +898,10 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
       for (int w = 1; w < kLWarps; w++) ff_merge(Sm, Lm, part[q & 1][w][cc].x, part[q & 1][w][cc].y);
       const long long j = ((long long)blockIdx.x + q * gridDim.x) * kLCols + cc;
       const bool mine = j < n;
-      const double t = ((double)Sm + (double)Lm) * unscale;
+      double t = ((double)Sm + (double)Lm) * unscale;
+      if constexpr (elt_i8(ELT)) {
+        if (mine) t = (double)cscale[j] * (t - (double)cmean[j] * ysum);
+      }
       if (mine) out[j] = t;
       if (MODE == kModeGmax && mine) amax = fmax(amax, fabs(t));
       if (MODE == kModeT) {
@@ -995,15 +1033,16 @@ bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda,
     }
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  const bool bf16 = dtype == SSNAL_EN_BF16;
-  const size_t es = bf16 ? 2 : 4;
+  const bool bf16 = dtype == SSNAL_EN_BF16, i8 = dtype == SSNAL_EN_I8_GENO;
+  const size_t es = i8 ? 1 : bf16 ? 2 : 4;
   if ((lda * es) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return false;
   cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
   cuuint64_t strides[1] = {(cuuint64_t)(lda * es)};
   cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)kLCols};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out),
-                      bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      i8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                         : bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                       const_cast<void*>(A), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -1013,7 +1052,8 @@ size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
 template <int MODE, int ELT>
 static void launch_lane(const void* map, int m, long long n, const double* vec, double* out, const double* x,
-                        const double* u, LsParams lp, DevState* st, double* partials, int sms, cudaStream_t s) {
+                        const double* u, LsParams lp, DevState* st, double* partials, int sms, cudaStream_t s,
+                        const float* cmean, const float* cscale) {
   static bool configured[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1031,33 +1071,38 @@ static void launch_lane(const void* map, int m, long long n, const double* vec, 
   if (grid < 1) grid = 1;
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(map);
   k_stream_lane<MODE, ELT><<<(int)grid, kLThreads, lane_smem(m, stages), s>>>(*tm, m, n, vec, out, x, u, lp, st,
-                                                                              partials, cfg);
+                                                                              partials, cfg, cmean, cscale);
 }
 
 template <int ELT>
 static void launch_lane_modes(int mode, const void* map, int m, long long n, const double* vec, double* out,
                               const double* x, const double* u, LsParams lp, DevState* st, double* partials, int sms,
-                              cudaStream_t s) {
+                              cudaStream_t s, const float* cmean, const float* cscale) {
   if (mode == kModeU)
-    launch_lane<kModeU, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    launch_lane<kModeU, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s, cmean, cscale);
   else if (mode == kModeT)
-    launch_lane<kModeT, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    launch_lane<kModeT, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s, cmean, cscale);
   else
-    launch_lane<kModeGmax, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s);
+    launch_lane<kModeGmax, ELT>(map, m, n, vec, out, x, u, lp, st, partials, sms, s, cmean, cscale);
 }
 
 void launch_stream_lane(int mode, int elt, const void* map, int m, long long n, const double* vec, double* out,
                         const double* x, const double* u, ProxParams pp, double mu, double beta, int max_ls, int fused,
-                        DevState* st, double* partials, int sms, cudaStream_t s) {
+                        DevState* st, double* partials, int sms, cudaStream_t s, const float* cmean,
+                        const float* cscale) {
   LsParams lp{pp, mu, beta, max_ls, fused};
   count_launch();
+#define SSNAL_LANE(E) launch_lane_modes<E>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s, cmean, cscale)
   switch (elt) {
-    case kEltBf16FF: launch_lane_modes<kEltBf16FF>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
-    case kEltBf16: launch_lane_modes<kEltBf16>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
-    case kEltF32FF: launch_lane_modes<kEltF32FF>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
-    case kEltF32: launch_lane_modes<kEltF32>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
-    default: launch_lane_modes<kEltSplit>(mode, map, m, n, vec, out, x, u, lp, st, partials, sms, s); break;
+    case kEltBf16FF: SSNAL_LANE(kEltBf16FF); break;
+    case kEltBf16: SSNAL_LANE(kEltBf16); break;
+    case kEltF32FF: SSNAL_LANE(kEltF32FF); break;
+    case kEltF32: SSNAL_LANE(kEltF32); break;
+    case kEltI8FF: SSNAL_LANE(kEltI8FF); break;
+    case kEltI8: SSNAL_LANE(kEltI8); break;
+    default: SSNAL_LANE(kEltSplit); break;
   }
+#undef SSNAL_LANE
 }
 
 void launch_stream(int mode, int dtype, const void* A, long long lda, int m, long long n, const double* vec,

@@ -201,15 +201,24 @@ __global__ void k_set_x(double* __restrict__ x, const double* __restrict__ u, lo
 // Element loaders for the gather: value of A(i, col) as double.
 struct LoadF64 {
   const double* __restrict__ A;
-  __device__ double operator()(long long off) const { return __ldg(A + off); }
+  __device__ double operator()(long long, long long off) const { return __ldg(A + off); }
 };
 struct LoadF32 {
   const float* A;
-  __device__ double operator()(long long off) const { return (double)A[off]; }
+  __device__ double operator()(long long, long long off) const { return (double)A[off]; }
 };
 struct LoadBF16 {
   const __nv_bfloat16* A;
-  __device__ double operator()(long long off) const { return (double)__bfloat162float(A[off]); }
+  __device__ double operator()(long long, long long off) const { return (double)__bfloat162float(A[off]); }
+};
+// genotype codes: entry (code - mean_j) * scale_j, evaluated in FP64
+struct LoadI8 {
+  const int8_t* A;
+  const float* mean;
+  const float* scale;
+  __device__ double operator()(long long col, long long off) const {
+    return ((double)A[off] - (double)mean[col]) * (double)scale[col];
+  }
 };
 
 // Gather of A_J: P[:, k] = A[:, J[k]] (FP64) and P32[:, k] = float(P[:, k]).
@@ -228,12 +237,12 @@ __global__ void __launch_bounds__(256) k_gather(Load ld, long long lda, int m, c
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long tw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long k = gw; k < r; k += tw) {
-    const long long src = (long long)J[k] * lda;
+    const long long col = J[k], src = col * lda;
     double* dst = P + k * ldp;
     float* dst32 = P32 + k * ldp32;
 #pragma unroll 4
     for (int i = lane; i < m; i += 32) {
-      const double v = ld(src + i);
+      const double v = ld(col, src + i);
       dst[i] = v;
       dst32[i] = (float)v;
     }
@@ -474,7 +483,7 @@ void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sm
 
 void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t* J, const DevState* st,
                    long long r_host, long long rcap, double* P, long long ldp, float* P32, long long ldp32, int sms,
-                   cudaStream_t s) {
+                   cudaStream_t s, const float* cmean, const float* cscale) {
   int grid = 2 * sms;
   count_launch();
   int* ovf = const_cast<int*>(&st->overflow);
@@ -482,8 +491,11 @@ void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t
     k_gather<<<grid, 256, 0, s>>>(LoadF64{(const double*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
   else if (dtype == 1)
     k_gather<<<grid, 256, 0, s>>>(LoadF32{(const float*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
-  else
+  else if (dtype == 2)
     k_gather<<<grid, 256, 0, s>>>(LoadBF16{(const __nv_bfloat16*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32,
+                                  ldp32, ovf);
+  else
+    k_gather<<<grid, 256, 0, s>>>(LoadI8{(const int8_t*)A, cmean, cscale}, lda, m, J, st, r_host, rcap, P, ldp, P32,
                                   ldp32, ovf);
 }
 

@@ -145,3 +145,69 @@ def test_bf16_path_matches_oracle_path():
             assert np.all(Xg[k] == 0.0)
         else:
             assert np.abs(Xg[k] - rk.x).max() <= 1e-3 * xmax
+
+
+# ---------------------------------------------------------------- int8 genotype codes
+def genotype_problem(m, n, seed, k=6, snr=2.0):
+    codes, mean, scale = synth.genotype_matrix(m, n, seed=seed)
+    As = (codes.astype(np.float64) - mean.astype(np.float64)[:, None]) * scale.astype(np.float64)[:, None]
+    rng = np.random.default_rng(seed + 1)
+    k = min(k, n)
+    x = np.zeros(n)
+    idx = rng.choice(n, size=k, replace=False)
+    x[idx] = rng.choice([-1.0, 1.0], size=k) * rng.uniform(0.5, 2.0, size=k)
+    Ax = As.T @ x
+    b = Ax + np.sqrt(Ax.var() / snr) * rng.normal(size=m)
+    return codes, mean, scale, As, b
+
+
+def genotype_context(codes, mean, scale, precision):
+    m = codes.shape[1]
+    A, _ = pkg.device_matrix(codes, pkg.I8_GENO)
+    cm, cs = dev(mean, torch.float32), dev(scale, torch.float32)
+    return pkg.Context(A, m=m, dtype=pkg.I8_GENO, options=pkg.ssnal_en_default_options(precision=precision),
+                       col_mean=cm, col_scale=cs)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 40), (127, 129), (128, 300), (300, 5000), (2000, 511)])
+def test_stream_genotype_codes(m, n):
+    codes, mean, scale, As, _ = genotype_problem(m, n, seed=m + n)
+    rng = np.random.default_rng(m)
+    y = rng.normal(size=m)
+    ref = As @ y
+    s = np.abs(scale.astype(np.float64))
+    mag = s * (np.abs(codes.astype(np.float64)) @ np.abs(y) + np.abs(mean.astype(np.float64)) * np.abs(y).sum())
+    ctx = genotype_context(codes, mean, scale, 0)
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(y), u)
+    # float-float code * y sums, then scale * (sum - mean * sum(y)) in FP64
+    bound = (2.0 ** -44 + m * 2.0 ** -46) * mag + 1e-300
+    assert np.all(np.abs(u.cpu().numpy() - ref) <= bound)
+    ctx.set_options(pkg.ssnal_en_default_options(precision=1))
+    t = torch.empty(n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_d(ctx.ctx, dev(y), t)
+    assert np.all(np.abs(t.cpu().numpy() - ref) <= (m + 4) * 2.0 ** -24 * mag + 1e-300)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("m,n,alpha,c,seed", [(150, 4000, 0.7, 0.3, 51), (400, 3000, 0.95, 0.2, 52)])
+def test_fit_genotype_codes(precision, m, n, alpha, c, seed):
+    codes, mean, scale, As, b = genotype_problem(m, n, seed)
+    lam1, lam2 = R.lambdas(As, b, alpha, c)
+    ctx = genotype_context(codes, mean, scale, precision)
+    x, y, res = ctx.solve(b, lam1, lam2)
+    xg = x.cpu().numpy()
+    ctx.close()
+    ro = R.solve(As, b, lam1, lam2)
+    assert res.status == pkg.OK and ro.converged
+    assert res.kkt1 <= 1e-6 and res.kkt3 <= 1e-6
+    xmax = np.abs(ro.x).max()
+    P_or = C.primal_objective(As, b, ro.x, lam1, lam2)
+    P_gpu = C.primal_objective(As, b, xg, lam1, lam2)
+    if precision == 0:
+        assert abs(P_gpu - P_or) <= 1e-9 * max(1.0, abs(P_or))
+        assert np.abs(xg - ro.x).max() <= 1e-6 * xmax
+    else:
+        assert abs(P_gpu - P_or) <= 1e-6 * max(1.0, abs(P_or))
+        assert np.abs(xg - ro.x).max() <= 1e-3 * xmax
