@@ -264,6 +264,8 @@ def run_gpu(args):
             "roofline": roofline}
     if rank == 0 and world == 1 and not args.no_mixed:
         line["mixed_vs_fp64"] = mixed_vs_fp64()
+    if rank == 0 and world == 1 and not args.no_batch:
+        line["batched"] = batched_fits()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
@@ -335,6 +337,52 @@ def mixed_vs_fp64(steps=3):
     return out
 
 
+def batched_fits(count=512):
+    """The batched configuration: 512 independent fits, m log-uniform in [50, 500], n log-uniform in
+    [1e3, 5e4], A iid N(0,1) standardized and stored in FP32, max(5, m/20) nonzeros, snr 5,
+    alpha 0.7, c ~ U[0.2, 0.8] (seed 4).  All matrices are resident; each timed batch starts from
+    x = 0.  Reported: fits/s of ssnal_en_solve_batch (tuned worker count) and, for comparison,
+    of the same instances solved one after another."""
+    import numpy as np
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    probs = synth.config4_instances(count)
+    ctxs, bs, xs, lams = [], [], [], []
+    for p in probs:
+        ctxs.append(pkg.Context(p.At, dtype=pkg.F32))
+        aty = np.abs(p.At.astype(np.float64) @ p.b).max()
+        lams.append((p.alpha * p.c * aty / p.alpha, (1 - p.alpha) / p.alpha * p.c * aty))
+        bs.append(torch.as_tensor(p.b, dtype=torch.float64, device="cuda"))
+        xs.append(torch.zeros(p.At.shape[0], dtype=torch.float64, device="cuda"))
+    inst = [(c.ctx, b, l1, l2, x, None) for c, b, (l1, l2), x in zip(ctxs, bs, lams, xs)]
+
+    def reset():
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+
+    reset()
+    pkg.ssnal_en_solve_batch(inst, 0)  # warm-up (and tuning)
+    reset()
+    t0 = time.perf_counter()
+    st, res, used = pkg.ssnal_en_solve_batch(inst, 0)
+    dt = time.perf_counter() - t0
+    ok = sum(1 for r in res if r.status == 0 and r.kkt1 <= TOL and r.kkt3 <= TOL)
+    reset()
+    t0 = time.perf_counter()
+    for c, b, (l1, l2), x in zip(ctxs, bs, lams, xs):
+        pkg.ssnal_en_solve(c.ctx, b, l1, l2, x)
+    dts = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    mn = sum(p.At.shape[0] * p.At.shape[1] for p in probs)
+    return {"workload": f"{count} independent fits, m log-uniform [50,500], n log-uniform [1e3,5e4], FP32 "
+                        f"storage ({mn * 4 / 1e9:.2f} GB), alpha 0.7, c ~ U[0.2,0.8], seed 4",
+            "fits_per_s": ok / dt, "seconds": dt, "converged": ok, "workers": used,
+            "sequential_fits_per_s": count / dts}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,6 +391,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the BF16-vs-FP64 precision comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -198,6 +198,33 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t rese
 ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* ctx, double* phase_ms, int64_t* phase_count);
 
 /* ---------------------------------------------------------------------------
+ * Many independent fits at once (Algorithm 1 per instance).
+ * ------------------------------------------------------------------------- */
+
+/* One fit of a batch: the context of its matrix, its right-hand side and its
+ * penalties, as for ssnal_en_solve. */
+typedef struct {
+  ssnal_en_ctx* ctx;  /* borrowed; every instance of a batch has its own context */
+  const double* b;    /* device, length m of ctx */
+  double lambda1, lambda2;
+  double* x;          /* device, length n of ctx: in = warm start, out = solution */
+  double* y;          /* device, length m, or NULL */
+} ssnal_en_instance;
+
+/* Solves count independent instances concurrently: `workers` host threads, each
+ * with its own CUDA stream, take instances in index order from a shared queue
+ * and run ssnal_en_solve on them, so small fits overlap on the device.
+ * workers = 0 tunes the thread count on the batch itself (4, 8, 16 or 32, by the
+ * m*n processed per second on successive chunks).  Each instance's result equals
+ * that of ssnal_en_solve on its own.  The device is synchronised on entry; all
+ * outputs are complete on return.  out: host array of count results (each with
+ * its own status); workers_used (host, may be NULL) receives the thread count.
+ * Returns OK when every instance converged, else the first non-OK status.
+ * Errors: EINVAL (null pointers, bad lambdas, a context used twice), ECUDA. */
+ssnal_en_status ssnal_en_solve_batch(ssnal_en_instance* inst, int64_t count, int32_t workers,
+                                     ssnal_en_result* out, int32_t* workers_used);
+
+/* ---------------------------------------------------------------------------
  * Single steps of the hot path, exposed for tests and for callers that build
  * their own loops.  Each runs the same kernels the solver uses.
  * ------------------------------------------------------------------------- */

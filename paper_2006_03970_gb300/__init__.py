@@ -20,6 +20,7 @@ __all__ = [
     "F64", "F32", "BF16", "I8_GENO", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
+    "ssnal_en_solve_batch", "Instance",
     "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_at_d", "ssnal_en_op_prox_active",
     "ssnal_en_op_grad",
     "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_profile_phases", "ssnal_en_prox_active_static",
@@ -55,6 +56,11 @@ class Options(ctypes.Structure):
                 ("ls_fused", ctypes.c_int32), ("syrk_tc", ctypes.c_int32), ("max_active", ctypes.c_int64)]
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("b", ctypes.c_void_p), ("lambda1", ctypes.c_double),
+                ("lambda2", ctypes.c_double), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("al_iters", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("ls_trials", ctypes.c_int32), ("active", ctypes.c_int64), ("kkt1", ctypes.c_double),
@@ -69,7 +75,7 @@ class Result(ctypes.Structure):
 _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
-           "ssnal_en_op_at_d",
+           "ssnal_en_op_at_d", "ssnal_en_solve_batch",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
            "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
 
@@ -93,6 +99,8 @@ def load_library(path: str | None = None):
     L.ssnal_en_destroy.restype = None
     L.ssnal_en_set_options.argtypes = [vp, ctypes.POINTER(Options)]
     L.ssnal_en_solve.argtypes = [vp, vp, dbl, dbl, vp, vp, ctypes.POINTER(Result)]
+    L.ssnal_en_solve_batch.argtypes = [ctypes.POINTER(Instance), ctypes.c_int64, i32, ctypes.POINTER(Result),
+                                       ctypes.POINTER(i32)]
     L.ssnal_en_path.argtypes = [vp, vp, dbl, ctypes.POINTER(dbl), i32, vp, ctypes.POINTER(Result),
                                 ctypes.POINTER(i32)]
     L.ssnal_en_path_host.argtypes = [vp, ctypes.POINTER(dbl), dbl, ctypes.POINTER(dbl), i32, vp,
@@ -208,6 +216,19 @@ def ssnal_en_solve(ctx, b, lambda1, lambda2, x, y=None):
                                        ctypes.byref(res))
     _check(st, "ssnal_en_solve", allow=(OK, ENOCONV))
     return st, res
+
+
+def ssnal_en_solve_batch(instances, workers: int = 0):
+    """instances: sequence of (ctx, b, lambda1, lambda2, x, y-or-None) with FP64 device tensors.
+    Returns (status, [Result], workers_used)."""
+    arr = (Instance * len(instances))()
+    for k, (ctx, b, l1, l2, x, y) in enumerate(instances):
+        arr[k] = Instance(ctx, _ptr(b), float(l1), float(l2), _ptr(x), _ptr(y))
+    res = (Result * len(instances))()
+    used = ctypes.c_int32(0)
+    st = load_library().ssnal_en_solve_batch(arr, len(instances), int(workers), res, ctypes.byref(used))
+    _check(st, "ssnal_en_solve_batch", allow=(OK, ENOCONV))
+    return st, list(res), used.value
 
 
 def ssnal_en_path(ctx, b, alpha, c_grid, X=None):

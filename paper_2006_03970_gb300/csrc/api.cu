@@ -561,6 +561,17 @@ ssnal_en_status check_options(const ssnal_en_options* o) {
 
 }  // namespace
 
+namespace ssnal {
+// The stream a context enqueues on; the batch and serving drivers give each
+// worker thread its own stream for the duration of one solve.
+cudaStream_t ctx_set_stream(ssnal_en_ctx* c, cudaStream_t s) {
+  cudaStream_t old = c->stream;
+  c->stream = s;
+  return old;
+}
+double ctx_mn(const ssnal_en_ctx* c) { return (double)c->m * (double)c->n; }
+}  // namespace ssnal
+
 extern "C" {
 
 void ssnal_en_default_options(ssnal_en_options* o) {

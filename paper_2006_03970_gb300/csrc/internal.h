@@ -7,6 +7,8 @@
 
 #include <atomic>
 
+struct ssnal_en_ctx;
+
 namespace ssnal {
 
 // Number of kernels this library has launched (all contexts).
@@ -146,5 +148,9 @@ void launch_stream_lane(int mode, int elt, const void* map, int m, long long n, 
                         const float* cscale = nullptr);
 void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s);
 void launch_check_range(const double* A, long long lda, int m, long long n, int* bad, int sms, cudaStream_t s);
+
+// api.cu: switch the stream of a context (returns the previous one)
+cudaStream_t ctx_set_stream(ssnal_en_ctx* c, cudaStream_t s);
+double ctx_mn(const ssnal_en_ctx* c);  // m * n of the context's matrix
 
 }  // namespace ssnal

@@ -47,6 +47,7 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(pkg.Matrix) == 3 * 8 + 2 * 4 + 3 * 8
     assert ctypes.sizeof(pkg.Options) == 6 * 8 + 8 * 4 + 8
     assert ctypes.sizeof(pkg.Result) == 4 * 4 + 8 + 8 * 8
+    assert ctypes.sizeof(pkg.Instance) == 6 * 8
 
 
 def test_default_options_without_gpu(lib):
