@@ -225,6 +225,42 @@ ssnal_en_status ssnal_en_solve_batch(ssnal_en_instance* inst, int64_t count, int
                                      ssnal_en_result* out, int32_t* workers_used);
 
 /* ---------------------------------------------------------------------------
+ * Serving: resident matrices, requests admitted while others run.
+ * ------------------------------------------------------------------------- */
+
+typedef struct ssnal_en_server ssnal_en_server; /* opaque */
+
+/* Starts a server over nmat resident matrices (descriptors copied; the device
+ * data stays owned by the caller and must outlive the server) with `workers`
+ * worker threads, each with its own CUDA stream.  A worker creates one context
+ * per matrix it serves (options opts, NULL = defaults) and keeps it for later
+ * requests on that matrix.  Requests are admitted in arrival order as workers
+ * free up and while the estimated device bytes of the contexts in use stay
+ * within max_bytes (0 = no bound; one request is always admitted).  FP64
+ * matrices get a float-pair copy per worker context (see ssnal_en_create); the
+ * other storage types are read in place.  Errors: EINVAL, ENOMEM, ECUDA. */
+ssnal_en_status ssnal_en_server_create(ssnal_en_server** srv, const ssnal_en_matrix* mats, int32_t nmat,
+                                       const ssnal_en_options* opts, int32_t workers, int64_t max_bytes);
+
+/* Queues one fit on matrix `mat` (eq. EN_pb with penalties lambda1, lambda2,
+ * started from x = 0): b_host is host memory of length m, copied before
+ * return.  *ticket identifies the request.  Errors: EINVAL. */
+ssnal_en_status ssnal_en_server_submit(ssnal_en_server* srv, int32_t mat, const double* b_host, double lambda1,
+                                       double lambda2, int64_t* ticket);
+
+/* Result of a request: with wait != 0 blocks until it is done.  When done,
+ * *done = 1, x_host (host, length n, may be NULL) receives the solution, *out
+ * (may be NULL) the result (its status is the solve's), times (host, 3, may be
+ * NULL) the seconds since server start at submission, start and completion, and
+ * the ticket is released.  Errors: EINVAL (unknown ticket). */
+ssnal_en_status ssnal_en_server_poll(ssnal_en_server* srv, int64_t ticket, int32_t wait, double* x_host,
+                                     ssnal_en_result* out, double* times, int32_t* done);
+
+/* Stops the workers after their current solves (queued requests are dropped)
+ * and frees the server's contexts.  NULL is a no-op. */
+void ssnal_en_server_destroy(ssnal_en_server* srv);
+
+/* ---------------------------------------------------------------------------
  * Single steps of the hot path, exposed for tests and for callers that build
  * their own loops.  Each runs the same kernels the solver uses.
  * ------------------------------------------------------------------------- */

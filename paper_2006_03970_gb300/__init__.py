@@ -20,7 +20,8 @@ __all__ = [
     "F64", "F32", "BF16", "I8_GENO", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
-    "ssnal_en_solve_batch", "Instance",
+    "ssnal_en_solve_batch", "Instance", "Server", "ssnal_en_server_create", "ssnal_en_server_submit",
+    "ssnal_en_server_poll", "ssnal_en_server_destroy",
     "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_at_d", "ssnal_en_op_prox_active",
     "ssnal_en_op_grad",
     "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_profile_phases", "ssnal_en_prox_active_static",
@@ -75,7 +76,8 @@ class Result(ctypes.Structure):
 _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
-           "ssnal_en_op_at_d", "ssnal_en_solve_batch",
+           "ssnal_en_op_at_d", "ssnal_en_solve_batch", "ssnal_en_server_create", "ssnal_en_server_submit",
+           "ssnal_en_server_poll", "ssnal_en_server_destroy",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
            "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
 
@@ -101,6 +103,13 @@ def load_library(path: str | None = None):
     L.ssnal_en_solve.argtypes = [vp, vp, dbl, dbl, vp, vp, ctypes.POINTER(Result)]
     L.ssnal_en_solve_batch.argtypes = [ctypes.POINTER(Instance), ctypes.c_int64, i32, ctypes.POINTER(Result),
                                        ctypes.POINTER(i32)]
+    L.ssnal_en_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Matrix), i32, ctypes.POINTER(Options), i32,
+                                         ctypes.c_int64]
+    L.ssnal_en_server_submit.argtypes = [vp, i32, ctypes.POINTER(dbl), dbl, dbl, ctypes.POINTER(ctypes.c_int64)]
+    L.ssnal_en_server_poll.argtypes = [vp, ctypes.c_int64, i32, ctypes.POINTER(dbl), ctypes.POINTER(Result),
+                                       ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.ssnal_en_server_destroy.argtypes = [vp]
+    L.ssnal_en_server_destroy.restype = None
     L.ssnal_en_path.argtypes = [vp, vp, dbl, ctypes.POINTER(dbl), i32, vp, ctypes.POINTER(Result),
                                 ctypes.POINTER(i32)]
     L.ssnal_en_path_host.argtypes = [vp, ctypes.POINTER(dbl), dbl, ctypes.POINTER(dbl), i32, vp,
@@ -229,6 +238,75 @@ def ssnal_en_solve_batch(instances, workers: int = 0):
     st = load_library().ssnal_en_solve_batch(arr, len(instances), int(workers), res, ctypes.byref(used))
     _check(st, "ssnal_en_solve_batch", allow=(OK, ENOCONV))
     return st, list(res), used.value
+
+
+def ssnal_en_server_create(mats, workers=8, options: Options | None = None, max_bytes=0):
+    """mats: list of (device tensor (n, lda), m, dtype, col_mean, col_scale).  Returns a handle."""
+    arr = (Matrix * len(mats))()
+    for k, (A, m, dtype, cm, cs) in enumerate(mats):
+        arr[k] = Matrix(m=m, n=A.shape[0], lda=A.shape[1], dtype=dtype, reserved=0, data=A.data_ptr(),
+                        col_mean=cm.data_ptr() if cm is not None else None,
+                        col_scale=cs.data_ptr() if cs is not None else None)
+    h = ctypes.c_void_p()
+    _check(load_library().ssnal_en_server_create(ctypes.byref(h), arr, len(mats),
+                                                  ctypes.byref(options) if options else None, int(workers),
+                                                  int(max_bytes)), "ssnal_en_server_create")
+    return h
+
+
+def ssnal_en_server_submit(srv, mat, b_host, lambda1, lambda2) -> int:
+    b = np.ascontiguousarray(b_host, dtype=np.float64)
+    t = ctypes.c_int64(0)
+    _check(load_library().ssnal_en_server_submit(srv, int(mat), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                  float(lambda1), float(lambda2), ctypes.byref(t)),
+           "ssnal_en_server_submit")
+    return t.value
+
+
+def ssnal_en_server_poll(srv, ticket, n, wait=True):
+    """Returns None if not done, else (x (n,), Result, (t_submit, t_start, t_done))."""
+    x = np.empty(n, dtype=np.float64)
+    res = Result()
+    times = (ctypes.c_double * 3)()
+    done = ctypes.c_int32(0)
+    _check(load_library().ssnal_en_server_poll(srv, int(ticket), int(bool(wait)),
+                                                x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                ctypes.byref(res), times, ctypes.byref(done)),
+           "ssnal_en_server_poll")
+    if not done.value:
+        return None
+    return x, res, tuple(times)
+
+
+def ssnal_en_server_destroy(srv):
+    load_library().ssnal_en_server_destroy(srv)
+
+
+class Server:
+    """Serving loop over resident matrices.  ``mats`` as for ssnal_en_server_create; the
+    device tensors must stay alive for the server's lifetime."""
+
+    def __init__(self, mats, workers=8, options: Options | None = None, max_bytes=0):
+        self._keep = mats
+        self.n = [A.shape[0] for A, _, _, _, _ in mats]
+        self.h = ssnal_en_server_create(mats, workers, options, max_bytes)
+
+    def submit(self, mat, b_host, lambda1, lambda2) -> int:
+        return ssnal_en_server_submit(self.h, mat, b_host, lambda1, lambda2)
+
+    def poll(self, ticket, mat, wait=True):
+        return ssnal_en_server_poll(self.h, ticket, self.n[mat], wait)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ssnal_en_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ssnal_en_path(ctx, b, alpha, c_grid, X=None):
