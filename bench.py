@@ -266,6 +266,8 @@ def run_gpu(args):
         line["mixed_vs_fp64"] = mixed_vs_fp64()
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched"] = batched_fits()
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["serving"] = serve_workload(args.serve_requests, args.serve_matrices)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
@@ -383,6 +385,82 @@ def batched_fits(count=512):
             "sequential_fits_per_s": count / dts}
 
 
+def serve_workload(per_rate=400, n_small=16, workers=16, seed=5):
+    """The serving configuration: a resident genotype-like A (m=2000, n=500000 int8 codes
+    ~ Binomial(2, p_j), p_j ~ U(0.05, 0.5), standardized on the fly by per-column FP32 mean and
+    scale) plus `n_small` resident FP32 matrices from the precision workload's generator (m
+    log-uniform in [200, 1000], n log-uniform in [1e4, 2e5], 50-feature blocks rho 0.5).  Each
+    request: its own x* (30 nonzeros +-U[0.5, 2]), b = A x* + noise at snr 2, alpha ~ U[0.5, 1),
+    c ~ U[0.1, 0.8]; its matrix is the genotype one with probability 1/2, else uniform over the
+    others.  The server runs the mixed form (precision 1) with `workers` worker streams.  First a
+    burst of `per_rate` requests gives the saturation throughput; then Poisson arrivals at
+    {0.25, 0.5, 0.75, 0.9, 1.1} x that rate, `per_rate` requests each, give latency percentiles
+    (submission to completion, host transfers included)."""
+    import math
+    import numpy as np
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    rng = np.random.Generator(np.random.PCG64(seed))
+    codes, mean, scale = synth.genotype_matrix(2000, 500_000, seed=seed)
+    Ag, mg = pkg.device_matrix(codes, pkg.I8_GENO)
+    mats = [(Ag, mg, pkg.I8_GENO, torch.as_tensor(mean, device="cuda"), torch.as_tensor(scale, device="cuda"))]
+    host_cols = [lambda idx: (codes[idx].astype(np.float64) - mean[idx, None]) * scale[idx, None]]
+    sizes = [(2000, 500_000)]
+    for k in range(n_small):
+        m = int(round(math.exp(rng.uniform(math.log(200), math.log(1000)))))
+        n = int(round(math.exp(rng.uniform(math.log(1e4), math.log(2e5)))))
+        q = synth.make_problem(m, n, k=1, seed=seed * 1_000_000 + k, block=50, rho=0.5, dtype=np.float32)
+        A, mm = pkg.device_matrix(q.At, pkg.F32)
+        mats.append((A, mm, pkg.F32, None, None))
+        At = q.At
+        host_cols.append(lambda idx, At=At: At[idx].astype(np.float64))
+        sizes.append((m, n))
+
+    def request():
+        k = 0 if rng.uniform() < 0.5 else int(rng.integers(1, len(mats)))
+        m, n = sizes[k]
+        idx = rng.choice(n, size=30, replace=False)
+        xs = rng.choice([-1.0, 1.0], size=30) * rng.uniform(0.5, 2.0, size=30)
+        ax = host_cols[k](idx).T @ xs
+        b = ax + math.sqrt(ax.var() / 2.0) * rng.standard_normal(m)
+        return k, b, float(rng.uniform(0.5, 1.0)), float(rng.uniform(0.1, 0.8))
+
+    srv = pkg.Server(mats, workers=workers, options=pkg.ssnal_en_default_options(precision=1))
+
+    def run(reqs, arrivals=None):
+        t0 = time.perf_counter()
+        tickets = []
+        for i, (k, b, alpha, c) in enumerate(reqs):
+            if arrivals is not None:
+                wait = t0 + arrivals[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            tickets.append((srv.submit_scaled(k, b, alpha, c), k))
+        got = [srv.poll(t, k, wait=True) for t, k in tickets]
+        lat = np.array([g[2][2] - g[2][0] for g in got])
+        span = max(g[2][2] for g in got) - min(g[2][0] for g in got)
+        ok = sum(1 for g in got if g[1].status == 0 and g[1].kkt1 <= TOL and g[1].kkt3 <= TOL)
+        return {"requests": len(reqs), "converged": ok, "fits_per_s": ok / span,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+    run([request() for _ in range(min(per_rate, 64))])  # warm-up: worker contexts
+    burst = run([request() for _ in range(per_rate)])
+    sat = burst["fits_per_s"]
+    sweep = []
+    for f in (0.25, 0.5, 0.75, 0.9, 1.1):
+        reqs = [request() for _ in range(per_rate)]
+        arrivals = np.cumsum(rng.exponential(1.0 / (f * sat), size=per_rate))
+        r = run(reqs, arrivals)
+        r["offered_fraction_of_saturation"] = f
+        sweep.append(r)
+    srv.close()
+    return {"workload": f"resident genotype A 2000x500000 int8 (1 GB) + {n_small} FP32 matrices "
+                        f"(m in [200,1000], n in [1e4,2e5]); requests 50% genotype, alpha ~ U[0.5,1), "
+                        f"c ~ U[0.1,0.8], x* 30 nonzeros, snr 2; mixed form, {workers} worker streams",
+            "saturation": burst, "poisson_sweep": sweep}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,6 +470,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the BF16-vs-FP64 precision comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-requests", type=int, default=400, help="requests per arrival rate (serving)")
+    ap.add_argument("--serve-matrices", type=int, default=16, help="resident FP32 matrices (serving)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -248,6 +248,13 @@ ssnal_en_status ssnal_en_server_create(ssnal_en_server** srv, const ssnal_en_mat
 ssnal_en_status ssnal_en_server_submit(ssnal_en_server* srv, int32_t mat, const double* b_host, double lambda1,
                                        double lambda2, int64_t* ticket);
 
+/* As ssnal_en_server_submit with the penalties of the paper's experiments
+ * (Sec. 4.1): lambda1 = c ||A^T b||_inf and lambda2 = (1 - alpha)/alpha * c ||A^T b||_inf,
+ * ||A^T b||_inf computed on the device at the start of the solve.  alpha in
+ * (0, 1], c >= 0.  Errors: EINVAL. */
+ssnal_en_status ssnal_en_server_submit_scaled(ssnal_en_server* srv, int32_t mat, const double* b_host, double alpha,
+                                              double c, int64_t* ticket);
+
 /* Result of a request: with wait != 0 blocks until it is done.  When done,
  * *done = 1, x_host (host, length n, may be NULL) receives the solution, *out
  * (may be NULL) the result (its status is the solve's), times (host, 3, may be

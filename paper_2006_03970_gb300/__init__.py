@@ -77,7 +77,7 @@ _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
            "ssnal_en_op_at_d", "ssnal_en_solve_batch", "ssnal_en_server_create", "ssnal_en_server_submit",
-           "ssnal_en_server_poll", "ssnal_en_server_destroy",
+           "ssnal_en_server_submit_scaled", "ssnal_en_server_poll", "ssnal_en_server_destroy",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
            "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
 
@@ -106,6 +106,8 @@ def load_library(path: str | None = None):
     L.ssnal_en_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Matrix), i32, ctypes.POINTER(Options), i32,
                                          ctypes.c_int64]
     L.ssnal_en_server_submit.argtypes = [vp, i32, ctypes.POINTER(dbl), dbl, dbl, ctypes.POINTER(ctypes.c_int64)]
+    L.ssnal_en_server_submit_scaled.argtypes = [vp, i32, ctypes.POINTER(dbl), dbl, dbl,
+                                                ctypes.POINTER(ctypes.c_int64)]
     L.ssnal_en_server_poll.argtypes = [vp, ctypes.c_int64, i32, ctypes.POINTER(dbl), ctypes.POINTER(Result),
                                        ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.ssnal_en_server_destroy.argtypes = [vp]
@@ -263,6 +265,16 @@ def ssnal_en_server_submit(srv, mat, b_host, lambda1, lambda2) -> int:
     return t.value
 
 
+def ssnal_en_server_submit_scaled(srv, mat, b_host, alpha, c) -> int:
+    b = np.ascontiguousarray(b_host, dtype=np.float64)
+    t = ctypes.c_int64(0)
+    _check(load_library().ssnal_en_server_submit_scaled(srv, int(mat),
+                                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                         float(alpha), float(c), ctypes.byref(t)),
+           "ssnal_en_server_submit_scaled")
+    return t.value
+
+
 def ssnal_en_server_poll(srv, ticket, n, wait=True):
     """Returns None if not done, else (x (n,), Result, (t_submit, t_start, t_done))."""
     x = np.empty(n, dtype=np.float64)
@@ -293,6 +305,9 @@ class Server:
 
     def submit(self, mat, b_host, lambda1, lambda2) -> int:
         return ssnal_en_server_submit(self.h, mat, b_host, lambda1, lambda2)
+
+    def submit_scaled(self, mat, b_host, alpha, c) -> int:
+        return ssnal_en_server_submit_scaled(self.h, mat, b_host, alpha, c)
 
     def poll(self, ticket, mat, wait=True):
         return ssnal_en_server_poll(self.h, ticket, self.n[mat], wait)

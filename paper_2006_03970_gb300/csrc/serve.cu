@@ -31,6 +31,8 @@ struct Request {
   int32_t mat = 0;
   std::vector<double> b;
   double lambda1 = 0.0, lambda2 = 0.0;
+  bool scaled = false;     // penalties given as (alpha, c) relative to ||A^T b||_inf
+  double alpha = 1.0, c = 0.0;
   std::vector<double> x;
   ssnal_en_result res{};
   bool done = false;
@@ -120,7 +122,12 @@ void worker_main(ssnal_en_server* S) {
         st = SSNAL_EN_ECUDA;
     }
     if (st == SSNAL_EN_OK) {
-      st = ssnal_en_solve(sl.ctx, sl.b, q->lambda1, q->lambda2, sl.x, nullptr, &q->res);
+      if (q->scaled) {
+        int32_t ndone = 0;
+        st = ssnal_en_path(sl.ctx, sl.b, q->alpha, &q->c, 1, sl.x, &q->res, &ndone);
+      } else {
+        st = ssnal_en_solve(sl.ctx, sl.b, q->lambda1, q->lambda2, sl.x, nullptr, &q->res);
+      }
       q->x.resize((size_t)A.n);
       if (cudaMemcpyAsync(q->x.data(), sl.x, sizeof(double) * A.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess)
@@ -180,6 +187,28 @@ ssnal_en_status ssnal_en_server_submit(ssnal_en_server* S, int32_t mat, const do
   q->b.assign(b_host, b_host + S->mats[mat].m);
   q->lambda1 = lambda1;
   q->lambda2 = lambda2;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    q->ticket = S->next_ticket++;
+    q->t_submit = S->now();
+    S->tickets[q->ticket] = q;
+    S->queue.push_back(q);
+  }
+  S->cv_work.notify_one();
+  *ticket = q->ticket;
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status ssnal_en_server_submit_scaled(ssnal_en_server* S, int32_t mat, const double* b_host, double alpha,
+                                              double c, int64_t* ticket) {
+  if (!S || !b_host || !ticket || mat < 0 || mat >= (int32_t)S->mats.size()) return SSNAL_EN_EINVAL;
+  if (!(alpha > 0.0 && alpha <= 1.0) || !std::isfinite(c) || c < 0) return SSNAL_EN_EINVAL;
+  auto q = std::make_shared<Request>();
+  q->mat = mat;
+  q->b.assign(b_host, b_host + S->mats[mat].m);
+  q->scaled = true;
+  q->alpha = alpha;
+  q->c = c;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     q->ticket = S->next_ticket++;
