@@ -251,3 +251,44 @@ def path(At, b, alpha, c_grid, max_active=0, opts: Options | None = None):
         if max_active and np.count_nonzero(x) >= max_active:
             break
     return out
+
+
+# --------------------------------------------------------------------------- parameter tuning
+def en_degrees_of_freedom(At, x, lam2):
+    """Elastic Net degrees of freedom of a solution (Sec. 3.4, after eq. gcv_bic):
+    nu = tr( A_J (A_J^T A_J + lam2 I_r)^{-1} A_J^T ), J the active set of x.  Written out with a
+    dense solve; nu = 0 for an empty active set."""
+    At = np.asarray(At, dtype=np.float64)
+    J = np.flatnonzero(x)
+    if J.size == 0:
+        return 0.0
+    AJ = At[J].T                                        # m x r
+    G = AJ.T @ AJ + lam2 * np.eye(J.size)
+    H = AJ @ np.linalg.solve(G, AJ.T)                   # the hat-like matrix
+    return float(np.trace(H))
+
+
+def debiased_rss(At, b, x):
+    """Residual sum of squares after the de-biasing of Sec. 3.4: ordinary least squares on the
+    active set of x, rss = || b - A_J x_ols ||^2 (lstsq; zero when the fit interpolates)."""
+    At = np.asarray(At, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    J = np.flatnonzero(x)
+    if J.size == 0:
+        return float(b @ b)
+    AJ = At[J].T
+    coef, *_ = np.linalg.lstsq(AJ, b, rcond=None)
+    r = b - AJ @ coef
+    return float(r @ r)
+
+
+def tuning_criteria(At, b, x, lam2):
+    """(nu, rss, gcv, e-bic) of eq. gcv_bic for one solution:
+    gcv = rss / m / (1 - nu/m)^2,  e-bic = log(rss / m) + (nu / m) (log m + log n)."""
+    At = np.asarray(At, dtype=np.float64)
+    n, m = At.shape
+    nu = en_degrees_of_freedom(At, x, lam2)
+    rss = debiased_rss(At, b, x)
+    gcv = (rss / m) / (1.0 - nu / m) ** 2 if nu != m else np.inf
+    ebic = np.log(rss / m) + (nu / m) * (np.log(m) + np.log(n)) if rss > 0 else -np.inf
+    return nu, rss, gcv, ebic
