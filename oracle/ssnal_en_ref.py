@@ -255,7 +255,7 @@ def path(At, b, alpha, c_grid, max_active=0, opts: Options | None = None):
 
 # --------------------------------------------------------------------------- parameter tuning
 def en_degrees_of_freedom(At, x, lam2):
-    """Elastic Net degrees of freedom of a solution (Sec. 3.4, after eq. gcv_bic):
+    """Elastic Net degrees of freedom of a solution (Sec. 3.3, after eq. gcv_bic):
     nu = tr( A_J (A_J^T A_J + lam2 I_r)^{-1} A_J^T ), J the active set of x.  Written out with a
     dense solve; nu = 0 for an empty active set."""
     At = np.asarray(At, dtype=np.float64)
@@ -269,7 +269,7 @@ def en_degrees_of_freedom(At, x, lam2):
 
 
 def debiased_rss(At, b, x):
-    """Residual sum of squares after the de-biasing of Sec. 3.4: ordinary least squares on the
+    """Residual sum of squares after the de-biasing of Sec. 3.3: ordinary least squares on the
     active set of x, rss = || b - A_J x_ols ||^2 (lstsq; zero when the fit interpolates)."""
     At = np.asarray(At, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)

@@ -1,4 +1,4 @@
-"""Pins of the tuning criteria of the oracle (Sec. 3.4, eq. gcv_bic) against closed forms."""
+"""Pins of the tuning criteria of the oracle (Sec. 3.3, eq. gcv_bic) against closed forms."""
 import numpy as np
 import pytest
 
