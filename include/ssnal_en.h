@@ -198,6 +198,31 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t rese
 ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* ctx, double* phase_ms, int64_t* phase_count);
 
 /* ---------------------------------------------------------------------------
+ * Parameter tuning along a path (Sec. 3.3, eq. gcv_bic).
+ * ------------------------------------------------------------------------- */
+
+/* Criteria of one solution x of the path, J its active set, r = |J|:
+ *   nu   = tr(A_J (A_J^T A_J + lambda2 I)^{-1} A_J^T)  (EN degrees of freedom),
+ *   rss  = ||b - A_J x_ols||^2, x_ols the least-squares fit on J (de-biasing),
+ *   gcv  = rss / m / (1 - nu / m)^2,   ebic = log(rss / m) + (nu / m)(log m + log n). */
+typedef struct {
+  double nu, rss, gcv, ebic;
+  int64_t active;
+} ssnal_en_tune_point;
+
+/* Runs ssnal_en_path (same arguments; X is required here) and evaluates the
+ * criteria at each computed point: nu from the Cholesky factor of the r x r (or
+ * m x m when r > m) matrix as min(r, m) - lambda2 tr(G^{-1}), rss through the
+ * SMW Newton solve with kappa = infinity (r < m; rss = 0 when r >= m).  nu is
+ * NaN when min(r, m) exceeds 640 and lambda2 > 0 (not supported), rss is NaN
+ * when the least-squares normal matrix is not positive definite in FP32.
+ * crit: host array of K.  best_gcv / best_ebic (host, may be NULL): index of the
+ * smallest finite criterion, or -1.  Errors: as ssnal_en_path. */
+ssnal_en_status ssnal_en_tune(ssnal_en_ctx* ctx, const double* b, double alpha, const double* c_grid, int32_t K,
+                              double* X, ssnal_en_result* out, ssnal_en_tune_point* crit, int32_t* best_gcv,
+                              int32_t* best_ebic, int32_t* n_done);
+
+/* ---------------------------------------------------------------------------
  * Many independent fits at once (Algorithm 1 per instance).
  * ------------------------------------------------------------------------- */
 

@@ -21,8 +21,8 @@ __all__ = [
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
     "ssnal_en_solve_batch", "Instance", "Server", "ssnal_en_server_create", "ssnal_en_server_submit",
-    "ssnal_en_server_poll", "ssnal_en_server_destroy",
-    "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_at_d", "ssnal_en_op_prox_active",
+    "ssnal_en_server_poll", "ssnal_en_server_destroy", "ssnal_en_server_submit_scaled", "ssnal_en_tune",
+    "TunePoint", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_at_d", "ssnal_en_op_prox_active",
     "ssnal_en_op_grad",
     "ssnal_en_op_newton", "ssnal_en_profile", "ssnal_en_profile_phases", "ssnal_en_prox_active_static",
     "STATIC_MAX_N", "Context",
@@ -62,6 +62,11 @@ class Instance(ctypes.Structure):
                 ("lambda2", ctypes.c_double), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p)]
 
 
+class TunePoint(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("rss", ctypes.c_double), ("gcv", ctypes.c_double),
+                ("ebic", ctypes.c_double), ("active", ctypes.c_int64)]
+
+
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("al_iters", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("ls_trials", ctypes.c_int32), ("active", ctypes.c_int64), ("kkt1", ctypes.c_double),
@@ -77,7 +82,7 @@ _LIB = None
 EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_create", "ssnal_en_destroy",
            "ssnal_en_set_options", "ssnal_en_solve", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y",
            "ssnal_en_op_at_d", "ssnal_en_solve_batch", "ssnal_en_server_create", "ssnal_en_server_submit",
-           "ssnal_en_server_submit_scaled", "ssnal_en_server_poll", "ssnal_en_server_destroy",
+           "ssnal_en_server_submit_scaled", "ssnal_en_server_poll", "ssnal_en_server_destroy", "ssnal_en_tune",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
            "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
 
@@ -111,6 +116,9 @@ def load_library(path: str | None = None):
     L.ssnal_en_server_poll.argtypes = [vp, ctypes.c_int64, i32, ctypes.POINTER(dbl), ctypes.POINTER(Result),
                                        ctypes.POINTER(dbl), ctypes.POINTER(i32)]
     L.ssnal_en_server_destroy.argtypes = [vp]
+    L.ssnal_en_tune.argtypes = [vp, vp, dbl, ctypes.POINTER(dbl), i32, vp, ctypes.POINTER(Result),
+                                ctypes.POINTER(TunePoint), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(i32)]
     L.ssnal_en_server_destroy.restype = None
     L.ssnal_en_path.argtypes = [vp, vp, dbl, ctypes.POINTER(dbl), i32, vp, ctypes.POINTER(Result),
                                 ctypes.POINTER(i32)]
@@ -322,6 +330,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def ssnal_en_tune(ctx, b, alpha, c_grid, X):
+    """Path plus gcv / e-bic at each point (Sec. 3.3).  X: FP64 device tensor (K, n).
+    Returns (status, [Result], [TunePoint], best_gcv, best_ebic, n_done)."""
+    grid = np.ascontiguousarray(c_grid, dtype=np.float64)
+    K = len(grid)
+    res = (Result * max(K, 1))()
+    crit = (TunePoint * max(K, 1))()
+    bg, be, done = ctypes.c_int32(-1), ctypes.c_int32(-1), ctypes.c_int32(0)
+    st = load_library().ssnal_en_tune(ctx, _ptr(b), float(alpha), grid.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      K, _ptr(X), res, crit, ctypes.byref(bg), ctypes.byref(be), ctypes.byref(done))
+    _check(st, "ssnal_en_tune", allow=(OK, ENOCONV))
+    return st, list(res)[:done.value], list(crit)[:done.value], bg.value, be.value, done.value
 
 
 def ssnal_en_path(ctx, b, alpha, c_grid, X=None):

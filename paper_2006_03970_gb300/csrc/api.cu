@@ -62,6 +62,8 @@ struct ssnal_en_ctx {
   float* G = nullptr;
   int64_t ldg = 0;
   float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
+  float* tuneS = nullptr;  // tuning: factor and identity for tr(G^{-1}) (2 Np x Np), allocated on first use
+  double* tune_dev = nullptr;  // tuning: per-column-block partial sums and the result
   void* Xtc = nullptr;     // BF16 split panels of the tensor-core SYRK (capacity rcap)
   float* tc_part = nullptr;
   double* Xdev = nullptr;  // path_host output staging
@@ -189,6 +191,8 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->P32);
   dev_free(c->G);
   dev_free(c->Wdiag);
+  dev_free(c->tuneS);
+  dev_free(c->tune_dev);
   dev_free(c->Xtc);
   dev_free(c->tc_part);
   dev_free(c->Xdev);
@@ -794,6 +798,95 @@ ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, co
   c->opt = saved;
   CK(cudaStreamSynchronize(s));
   return worst;
+}
+
+// Model-selection criteria along a path (Sec. 3.3, eq. gcv_bic).
+ssnal_en_status ssnal_en_tune(ssnal_en_ctx* c, const double* b, double alpha, const double* c_grid, int32_t K,
+                              double* X, ssnal_en_result* out, ssnal_en_tune_point* crit, int32_t* best_gcv,
+                              int32_t* best_ebic, int32_t* n_done) {
+  if (best_gcv) *best_gcv = -1;
+  if (best_ebic) *best_ebic = -1;
+  if (n_done) *n_done = 0;
+  if (!c || !b || !c_grid || !X || !out || !crit || K < 0) return SSNAL_EN_EINVAL;
+  int32_t done = 0;
+  ssnal_en_status e = ssnal_en_path(c, b, alpha, c_grid, K, X, out, &done);
+  if (e != SSNAL_EN_OK && e != SSNAL_EN_ENOCONV) return e;
+  if (n_done) *n_done = done;
+  cudaStream_t s = c->stream;
+  const int64_t m = c->m, n = c->n;
+  // ||b||^2 for the empty model
+  launch_combine(c->tmpm, c->bdev, 1.0, nullptr, 0.0, nullptr, 0.0, (int)m, 1, c->bdev, c->bdev, nullptr, c->st,
+                 c->comb_scratch, s);
+  if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+  const double bb = c->st_host->g2;
+  double best_g = INFINITY, best_e = INFINITY;
+  for (int k = 0; k < done; k++) {
+    ssnal_en_tune_point& P = crit[k];
+    memset(&P, 0, sizeof(P));
+    const double* xk = X + (int64_t)k * n;
+    const double lam2 = out[k].lambda2;
+    ProxParams pp = make_pp(c->opt.sigma0, out[k].lambda1, lam2);
+    // J = support of x_k and the panel A_J (y := A_J x_J - b as a by-product)
+    if ((e = prox_gather_grad(c, kProxSupport, xk, c->bdev, pp, 0)) != SSNAL_EN_OK) return e;
+    const int64_t r = c->st_host->r;
+    P.active = r;
+    const int64_t N = r < m ? r : m;
+    // degrees of freedom: nu = N - lam2 tr(G^{-1}), G = A_J^T A_J + lam2 I (r <= m) or A_J A_J^T + lam2 I
+    double nu = NAN;
+    if (r == 0) {
+      nu = 0.0;
+    } else if (!(lam2 > 0.0)) {
+      nu = (double)N;  // full column (or row) rank assumed: the trace of a projection
+    } else {
+      const int64_t Np = (N + 31) / 32 * 32;
+      if (Np <= 640) {
+        if (c->tune_dev == nullptr && dev_alloc(&c->tune_dev, 64 + 1) != SSNAL_EN_OK) return SSNAL_EN_ENOMEM;
+        if (c->tuneS == nullptr && dev_alloc(&c->tuneS, (size_t)2 * 640 * 640) != SSNAL_EN_OK) return SSNAL_EN_ENOMEM;
+        const long long ldS = 2 * Np;
+        if (r <= m)
+          launch_syrk_tc(c->P, c->ldp, (int)m, (int)r, 0, syrk_splits(c), c->Xtc, c->tc_part, 1.0f, (float)lam2,
+                         c->tuneS, ldS, c->st, c->sms, s);
+        else
+          launch_syrk_tc(c->P, c->ldp, (int)m, (int)r, 1, syrk_splits(c), c->Xtc, c->tc_part, 1.0f, (float)lam2,
+                         c->tuneS, ldS, c->st, c->sms, s);
+        if (inv_trace(c->tuneS, ldS, (int)N, c->st, c->Wdiag, c->tune_dev, c->tune_dev + 64, s)) {
+          double tr = 0.0;
+          CK(cudaMemcpyAsync(&tr, c->tune_dev + 64, sizeof(double), cudaMemcpyDeviceToHost, s));
+          if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+          tr -= (double)(Np - N);
+          if (!c->st_host->chol_fail) nu = (double)N - lam2 * tr;
+        }
+      }
+    }
+    // de-biased fit: ordinary least squares on J, rss = ||b - A_J x_ols||^2 (the SMW Newton
+    // solve with kappa = infinity gives d = A_J G0^{-1} A_J^T b - b with G0 = A_J^T A_J)
+    double rss = NAN;
+    if (r == 0) {
+      rss = bb;
+    } else if (r >= m) {
+      rss = 0.0;
+    } else {
+      if ((e = newton_direction(c, r, INFINITY, c->bdev, c->d, c->bdev, c->bdev, 1)) != SSNAL_EN_OK) return e;
+      if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+      if (!c->st_host->chol_fail) rss = c->st_host->dd;
+    }
+    P.nu = nu;
+    P.rss = rss;
+    const double md = (double)m;
+    P.gcv = (rss / md) / ((1.0 - nu / md) * (1.0 - nu / md));
+    P.ebic = log(rss / md) + (nu / md) * (log(md) + log((double)n));
+    if (std::isfinite(P.gcv) && P.gcv < best_g) {
+      best_g = P.gcv;
+      if (best_gcv) *best_gcv = k;
+    }
+    if (std::isfinite(P.ebic) && P.ebic < best_e) {
+      best_e = P.ebic;
+      if (best_ebic) *best_ebic = k;
+    }
+  }
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  CK(cudaStreamSynchronize(s));
+  return e;
 }
 
 ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* c, const double* b_host, double alpha, const double* c_grid,

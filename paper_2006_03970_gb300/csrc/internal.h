@@ -117,6 +117,11 @@ void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, doubl
 // when the factorisation produces them (the cluster kernel).  Returns whether
 // they were written.
 bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s);
+// *out = tr(G^{-1}) - (Np - N) + ... see kern_linalg.cu: factors the N x N SPD matrix in S (row
+// stride ldS >= 2 * round_up(N, 32)) and writes ||L^{-1}||_F^2 + (Np - N) to *out (device).
+// N <= 640; returns false otherwise or on a launch error.
+bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, double* partial, double* out,
+               cudaStream_t s);
 // N <= kSmallNewton: factor and solve one right-hand side in one launch (acc = c)
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
                              double alpha, cudaStream_t s);

@@ -1451,6 +1451,67 @@ static void small_smem_attr() {
   if (dev >= 0 && dev < 64) done[dev] = true;
 }
 
+// ---------------------------------------------------------------------------
+// Trace of the inverse of an SPD matrix for the degrees of freedom of the tuning
+// criteria (Sec. 3.3): with G = L L^T, tr(G^{-1}) = ||L^{-1}||_F^2.  The factor
+// and the identity are laid out in one buffer S (row stride ldS >= 2 Np, Np =
+// N rounded up to 32): S[0:Np, 0:Np] = L padded with the identity, S[Np:2Np,
+// 0:Np] = I; k_trsm_blocks then turns the bottom block into I L^{-T}, and
+// ||L^{-T}||_F^2 = ||L^{-1}||_F^2 + (Np - N) (the padded part contributes ones).
+
+// Identity padding of the factor (rows / columns N..Np-1) and the identity below it.
+__global__ void k_inv_trace_setup(float* __restrict__ S, long long ldS, int N, int Np) {
+  const long long total = (long long)Np * Np;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % Np), j = (int)(e / Np);  // row, column
+    const float id = (i == j) ? 1.0f : 0.0f;
+    S[Np + i + (long long)j * ldS] = id;             // bottom block: I
+    if (i >= N || j >= N) S[i + (long long)j * ldS] = id;
+  }
+}
+
+// Fixed-order sum of squares of the Np x Np block B (column-major, ld), one
+// partial per column block of 32; the last block adds the partials in order.
+__global__ void __launch_bounds__(256) k_frob2(const float* __restrict__ B, long long ld, int Np,
+                                               double* __restrict__ partial, double* __restrict__ out,
+                                               DevState* st) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int e = threadIdx.x; e < 32 * Np; e += blockDim.x) {
+    const int i = e % Np, j = 32 * blockIdx.x + e / Np;
+    const double v = (double)B[i + (long long)j * ld];
+    a = fma(v, v, a);
+  }
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = a;
+  if (!last_block(&st->counters[kCtrMisc])) return;
+  if (threadIdx.x == 0) *out = ordered_sum_cg(partial, 1, (int)gridDim.x);
+  reset_counter(&st->counters[kCtrMisc]);
+}
+
+bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, double* partial, double* out,
+               cudaStream_t s) {
+  const int Np = (N + 31) / 32 * 32;
+  if (N <= 0 || Np > kClusterN) return false;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !done[dev]) {
+    cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
+    cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((size_t)(32 * kClusterN + 1024 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float)));
+    if (dev >= 0 && dev < 64) done[dev] = true;
+  }
+  count_launch(4);
+  k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((N + 31) / 32), s>>>(S, ldS, N, st, Wdiag);
+  k_inv_trace_setup<<<64, 256, 0, s>>>(S, ldS, N, Np);
+  const size_t tsm = (size_t)(32 * Np + 1024 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
+  k_trsm_blocks<<<Np / 32, 256, tsm, s>>>(S, ldS, 0, Np, Np, Np, Wdiag);
+  k_frob2<<<Np / 32, 256, 0, s>>>(S + Np, ldS, Np, partial, out, st);
+  return cudaGetLastError() == cudaSuccess;
+}
+
 bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s) {
   if (N <= kSmallN) {
     small_smem_attr();

@@ -1,0 +1,56 @@
+"""Tuning criteria along a path (Sec. 3.3, eq. gcv_bic) against the oracle's definitions.
+
+The criteria are evaluated by the oracle on the GPU's own path solutions, so the comparison
+isolates the criteria kernels (degrees of freedom through the FP32 Cholesky factor's inverse,
+de-biased RSS through the refined least-squares solve)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2006_03970_gb300 as pkg  # noqa: E402
+from oracle import ssnal_en_ref as R  # noqa: E402
+from paper_2006_03970_gb300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_03970_gb300 import build
+    build.build()
+    pkg.load_library()
+
+
+@pytest.mark.parametrize("m,n,alpha,K,seed", [(150, 3000, 0.6, 10, 71), (60, 800, 0.9, 12, 72),
+                                              (300, 2000, 0.5, 8, 73)])
+def test_tuning_criteria_match_oracle(m, n, alpha, K, seed):
+    p = synth.make_problem(m, n, k=8, seed=seed, block=20, rho=0.5, snr=3.0, alpha=alpha)
+    grid = synth.path_grid(K, 0.05)
+    ctx = pkg.Context(p.At)
+    b = torch.as_tensor(p.b, device="cuda")
+    X = torch.zeros((K, n), dtype=torch.float64, device="cuda")
+    st, res, crit, bg, be, done = pkg.ssnal_en_tune(ctx.ctx, b, alpha, grid, X)
+    ctx.close()
+    assert done == K
+    Xh = X.cpu().numpy()
+    ref = [R.tuning_criteria(p.At, p.b, Xh[k], res[k].lambda2) for k in range(K)]
+    for k in range(K):
+        nu, rss, gcv, ebic = ref[k]
+        c = crit[k]
+        assert c.active == np.count_nonzero(Xh[k])
+        assert c.nu == pytest.approx(nu, rel=1e-5, abs=1e-6)
+        if c.active < m:
+            assert c.rss == pytest.approx(rss, rel=1e-7)
+            assert c.gcv == pytest.approx(gcv, rel=1e-5)
+            assert c.ebic == pytest.approx(ebic, rel=1e-6, abs=1e-6)
+    g = np.array([r[2] for r in ref])
+    e = np.array([r[3] for r in ref])
+    # the selected points agree unless the two best values are within the tolerance
+    gs = np.sort(g[np.isfinite(g)])
+    if gs.size > 1 and gs[1] - gs[0] > 1e-4 * abs(gs[0]):
+        assert bg == int(np.nanargmin(np.where(np.isfinite(g), g, np.inf)))
+    es = np.sort(e[np.isfinite(e)])
+    if es.size > 1 and es[1] - es[0] > 1e-4 * max(1.0, abs(es[0])):
+        assert be == int(np.nanargmin(np.where(np.isfinite(e), e, np.inf)))
