@@ -143,6 +143,16 @@ __device__ __forceinline__ double rows_sum32(const double* P, int nb, double* sc
   return t;
 }
 
+// ---- programmatic dependent launch: every kernel lets the next one in its stream
+// be launched at once, then waits until its own prerequisites have completed
+// (and their memory is visible) before touching any data.  This hides the
+// launch latency between consecutive kernels; kernels launched without the
+// attribute treat both instructions as no-ops.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---- mbarrier helpers.  Every wait is bounded: it gives up after about two
 // seconds of SM clock (or kSpinLimit rounds), so a protocol error cannot hang
 // the GPU; the caller raises DevState::timeout and leaves.
@@ -175,4 +185,25 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   }
   return false;
 }
+// Launches kernel k on stream s with programmatic stream serialization (see
+// pdl_entry); if the launch with the attribute is refused, launches plainly.
+template <typename... ExpT, typename... ActT>
+inline void launch_k(void (*k)(ExpT...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, ActT&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k, args...) != cudaSuccess) {
+    cudaGetLastError();
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, k, args...);
+  }
+}
+
 }  // namespace ssnal

@@ -25,6 +25,7 @@ __device__ __forceinline__ void tri_tile(int id, int& ti, int& tj) {
 // G[a, b] = diag*[a == b] + sum_i P[i, a] P[i, b] for a >= b (a, b < r).
 __global__ void __launch_bounds__(256) k_syrk_tn(const float* __restrict__ P, long long ldp, int m, int r,
                                                  float diag, float* __restrict__ G, long long ldg) {
+  pdl_entry();
   __shared__ float As[kT][kT + 1];
   __shared__ float Bs[kT][kT + 1];
   int ti, tj;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(256) k_syrk_tn(const float* __restrict__ P, lo
 // M[i, j] = [i == j] + kappa * sum_k P[i, k] P[j, k] for i >= j (i, j < m), K = r.
 __global__ void __launch_bounds__(256) k_syrk_nt(const float* __restrict__ P, long long ldp, int m, long long r,
                                                  float kappa, float* __restrict__ G, long long ldg) {
+  pdl_entry();
   __shared__ float As[kT][kT + 1];
   __shared__ float Bs[kT][kT + 1];
   int ti, tj;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(256) k_syrk_nt(const float* __restrict__ P, lo
 
 // Unblocked Cholesky of the nb x nb diagonal block at (kb, kb).
 __global__ void k_potrf_diag(float* __restrict__ G, long long ld, int kb, int nb, DevState* st) {
+  pdl_entry();
   __shared__ float a[kT][kT + 1];
   const int i = threadIdx.x, j = threadIdx.y;  // 32 x 32
   if (i < nb && j < nb && j <= i) a[i][j] = G[(kb + i) + (long long)(kb + j) * ld];
@@ -115,6 +118,7 @@ __global__ void k_potrf_diag(float* __restrict__ G, long long ld, int kb, int nb
 
 // Panel below the diagonal block: L21 = A21 L11^{-T}, one row per thread.
 __global__ void k_trsm_panel(float* __restrict__ G, long long ld, int kb, int nb, int N) {
+  pdl_entry();
   __shared__ float L[kT][kT + 1];
   for (int e = threadIdx.x; e < kT * kT; e += blockDim.x) {
     const int i = e % kT, j = e / kT;
@@ -139,6 +143,7 @@ __global__ void k_trsm_panel(float* __restrict__ G, long long ld, int kb, int nb
 
 // Trailing update A22 -= L21 L21^T on lower tiles of [k1, N).
 __global__ void __launch_bounds__(256) k_syrk_update(float* __restrict__ G, long long ld, int kb, int nb, int N) {
+  pdl_entry();
   __shared__ float As[kT][kT + 1];
   __shared__ float Bs[kT][kT + 1];
   int ti, tj;
@@ -176,6 +181,7 @@ constexpr int kTrsvThreads = 1024;
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv_llt(const float* __restrict__ L, long long ld, int N,
                                                            const double* __restrict__ rhs, double* __restrict__ acc,
                                                            int first, double alpha) {
+  pdl_entry();
   extern __shared__ float z[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
@@ -288,6 +294,7 @@ constexpr size_t kSmallSmem = (size_t)(kSmallN * (kSmallN + 1) + kSmallN) * size
 __global__ void __launch_bounds__(kSmallThreads) k_chol_small(float* __restrict__ G, long long ld, int N,
                                                               DevState* st, const double* __restrict__ rhs,
                                                               double* __restrict__ acc, double alpha) {
+  pdl_entry();
   extern __shared__ float sm_small[];
   float* Ls = sm_small;
   float* z = sm_small + kSmallN * (kSmallN + 1);
@@ -373,6 +380,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_small(float* __restrict_
 __global__ void __launch_bounds__(kSmallThreads) k_trsv_small(const float* __restrict__ L, long long ld, int N,
                                                               const double* __restrict__ rhs,
                                                               double* __restrict__ acc, int first, double alpha) {
+  pdl_entry();
   extern __shared__ float sm_small[];
   float* Ls = sm_small;
   float* z = sm_small + kSmallN * (kSmallN + 1);
@@ -436,6 +444,7 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
                                                           const double* __restrict__ rhs, double* __restrict__ acc,
                                                           int first, double alpha,
                                                           const float* __restrict__ Wdiag) {
+  pdl_entry();
   extern __shared__ __align__(16) float sm_mid[];
   const int ldb = (N + 3) & ~3;
   float* buf[2] = {sm_mid, sm_mid + 32 * ldb};
@@ -695,6 +704,7 @@ __device__ __forceinline__ void push_tile(unsigned src, unsigned dst, unsigned b
 
 __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag) {
+  pdl_entry();
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) float csm[];
@@ -942,6 +952,7 @@ __device__ __forceinline__ void blk_stage_backward(const float* __restrict__ L, 
 __global__ void __launch_bounds__(kBlkThreads) k_trsv_blk(const float* __restrict__ L, long long ld, int N,
                                                           const double* __restrict__ rhs, double* __restrict__ acc,
                                                           int first, double alpha, const float* __restrict__ Wd) {
+  pdl_entry();
   extern __shared__ __align__(16) float sm_blk[];
   const int T = (N + 31) / 32, ldb = (N + 3) & ~3, stage = blk_stage_floats(N);
   // staging buffer b: L part at sm_blk + b * stage, W_II at sm_blk + 2 * stage + b * 1024
@@ -1040,6 +1051,7 @@ __device__ __forceinline__ void st_async_f32(unsigned addr, float v, unsigned ba
 __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
     k_trsv_cluster(const float* __restrict__ L, long long ld, int N, const double* __restrict__ rhs,
                    double* __restrict__ acc, int first, double alpha, const float* __restrict__ Wd, DevState* st) {
+  pdl_entry();
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) float tcl[];
@@ -1182,6 +1194,7 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 // cp.async, all chunks in flight at once, so one 128-bit load gives 4 rows.
 __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long long ld, int k0, int nk, int r0,
                                                      int R, const float* __restrict__ Wd) {
+  pdl_entry();
   extern __shared__ __align__(16) float tsm[];
   const int ldx = nk + 1;  // odd: conflict-free column walks
   float* Ls = tsm;                 // (nk - 32) x 32: block row J of L, column k at Ls + 32 k
@@ -1241,6 +1254,7 @@ __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long
 // C -= X X^T on the lower triangle of the R x R block C = G[r0 .., r0 ..], with
 // X = G[r0 .., k0 .. k0 + nk): 64 x 64 output tiles, K staged 32 at a time.
 __global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long long ld, int r0, int R, int k0, int nk) {
+  pdl_entry();
   __shared__ float As[64 * 33], Bs[64 * 33];
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
@@ -1325,6 +1339,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, DevState* st) {
 
 __global__ void __launch_bounds__(kCoopThreads) k_chol_coop(float* __restrict__ G, long long ld, int N,
                                                             DevState* st, unsigned* bar) {
+  pdl_entry();
   __shared__ float Ld[kT][kT + 1];
   __shared__ float As[kT][kT + 1];
   __shared__ float Bs[kT][kT + 1];
@@ -1430,7 +1445,7 @@ void launch_syrk_tn(const float* P32, long long ldp32, int m, long long r, doubl
   int T = (int)((r + kT - 1) / kT);
   int blocks = T * (T + 1) / 2;
   if (blocks > 0) count_launch();
-  if (blocks > 0) k_syrk_tn<<<blocks, 256, 0, s>>>(P32, ldp32, m, (int)r, (float)diag, G, ldg);
+  if (blocks > 0) launch_k(k_syrk_tn, dim3(blocks), dim3(256), (size_t)(0), s, P32, ldp32, m, (int)r, (float)diag, G, ldg);
 }
 
 void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, double kappa, float* G, long long ldg,
@@ -1438,7 +1453,7 @@ void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, doubl
   int T = (m + kT - 1) / kT;
   int blocks = T * (T + 1) / 2;
   if (blocks > 0) count_launch();
-  if (blocks > 0) k_syrk_nt<<<blocks, 256, 0, s>>>(P32, ldp32, m, r, (float)kappa, G, ldg);
+  if (blocks > 0) launch_k(k_syrk_nt, dim3(blocks), dim3(256), (size_t)(0), s, P32, ldp32, m, r, (float)kappa, G, ldg);
 }
 
 static void small_smem_attr() {
@@ -1461,6 +1476,7 @@ static void small_smem_attr() {
 
 // Identity padding of the factor (rows / columns N..Np-1) and the identity below it.
 __global__ void k_inv_trace_setup(float* __restrict__ S, long long ldS, int N, int Np) {
+  pdl_entry();
   const long long total = (long long)Np * Np;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -1476,6 +1492,7 @@ __global__ void k_inv_trace_setup(float* __restrict__ S, long long ldS, int N, i
 __global__ void __launch_bounds__(256) k_frob2(const float* __restrict__ B, long long ld, int Np,
                                                double* __restrict__ partial, double* __restrict__ out,
                                                DevState* st) {
+  pdl_entry();
   __shared__ double red[32];
   double a = 0.0;
   for (int e = threadIdx.x; e < 32 * Np; e += blockDim.x) {
@@ -1504,11 +1521,11 @@ bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, doubl
     if (dev >= 0 && dev < 64) done[dev] = true;
   }
   count_launch(4);
-  k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((N + 31) / 32), s>>>(S, ldS, N, st, Wdiag);
-  k_inv_trace_setup<<<64, 256, 0, s>>>(S, ldS, N, Np);
+  launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(256), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
+  launch_k(k_inv_trace_setup, dim3(64), dim3(256), (size_t)(0), s, S, ldS, N, Np);
   const size_t tsm = (size_t)(32 * Np + 1024 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
-  k_trsm_blocks<<<Np / 32, 256, tsm, s>>>(S, ldS, 0, Np, Np, Np, Wdiag);
-  k_frob2<<<Np / 32, 256, 0, s>>>(S + Np, ldS, Np, partial, out, st);
+  launch_k(k_trsm_blocks, dim3(Np / 32), dim3(256), (size_t)(tsm), s, S, ldS, 0, Np, Np, Np, Wdiag);
+  launch_k(k_frob2, dim3(Np / 32), dim3(256), (size_t)(0), s, S + Np, ldS, Np, partial, out, st);
   return cudaGetLastError() == cudaSuccess;
 }
 
@@ -1516,7 +1533,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
   if (N <= kSmallN) {
     small_smem_attr();
     count_launch();
-    k_chol_small<<<1, kSmallThreads, kSmallSmem, s>>>(G, ldg, N, st, nullptr, nullptr, 1.0);
+    launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, nullptr, nullptr, 1.0);
     return false;
   }
   if (N <= kClusterN) {
@@ -1528,7 +1545,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((N + 31) / 32), s>>>(G, ldg, N, st, Wdiag);
+    launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(256), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag);
     if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
   }
   if (Wdiag && N <= kMaxM) {
@@ -1549,15 +1566,15 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       const int nk = N - k0 < B ? N - k0 : B;
       float* Gkk = G + k0 + (long long)k0 * ldg;
       count_launch();
-      k_chol_cluster<<<kClusterCTAs, 256, cluster_smem((nk + 31) / 32), s>>>(Gkk, ldg, nk, st,
+      launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(256), (size_t)(cluster_smem((nk + 31) / 32)), s, Gkk, ldg, nk, st,
                                                                              Wdiag + (long long)(k0 / 32) * 1024);
       const int r0 = k0 + nk, R = N - r0;
       if (R > 0) {
         count_launch(2);
         const size_t tsm = (size_t)(32 * nk + 1024 + 32 * (nk + 1) + 32 * 33) * sizeof(float);
-        k_trsm_blocks<<<(R + 31) / 32, 256, tsm, s>>>(G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024);
+        launch_k(k_trsm_blocks, dim3((R + 31) / 32), dim3(256), (size_t)(tsm), s, G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024);
         const int nt = (R + 63) / 64;
-        k_syrk_sub<<<nt * (nt + 1) / 2, 256, 0, s>>>(G, ldg, r0, R, k0, nk);
+        launch_k(k_syrk_sub, dim3(nt * (nt + 1) / 2), dim3(256), (size_t)(0), s, G, ldg, r0, R, k0, nk);
       }
       launched = cudaGetLastError() == cudaSuccess;
     }
@@ -1584,13 +1601,13 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
   for (int kb = 0; kb < N; kb += kCholNB) {
     const int nb = N - kb < kCholNB ? N - kb : kCholNB;
     count_launch();
-    k_potrf_diag<<<1, dim3(32, 32), 0, s>>>(G, ldg, kb, nb, st);
+    launch_k(k_potrf_diag, dim3(1), dim3(dim3(32, 32)), (size_t)(0), s, G, ldg, kb, nb, st);
     const int rem = N - kb - nb;
     if (rem > 0) {
       count_launch(2);
-      k_trsm_panel<<<(rem + 255) / 256, 256, 0, s>>>(G, ldg, kb, nb, N);
+      launch_k(k_trsm_panel, dim3((rem + 255) / 256), dim3(256), (size_t)(0), s, G, ldg, kb, nb, N);
       const int T = (rem + kT - 1) / kT;
-      k_syrk_update<<<T * (T + 1) / 2, 256, 0, s>>>(G, ldg, kb, nb, N);
+      launch_k(k_syrk_update, dim3(T * (T + 1) / 2), dim3(256), (size_t)(0), s, G, ldg, kb, nb, N);
     }
   }
   return false;
@@ -1600,7 +1617,7 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
                              double alpha, cudaStream_t s) {
   small_smem_attr();
   count_launch();
-  k_chol_small<<<1, kSmallThreads, kSmallSmem, s>>>(G, ldg, N, st, rhs, acc, alpha);
+  launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, rhs, acc, alpha);
 }
 
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
@@ -1609,7 +1626,7 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
   if (N <= kSmallN) {
     small_smem_attr();
     count_launch();
-    k_trsv_small<<<1, kSmallThreads, kSmallSmem, s>>>(L, ldl, N, rhs, acc, first, alpha);
+    launch_k(k_trsv_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, L, ldl, N, rhs, acc, first, alpha);
     return;
   }
   if (Wdiag && N <= 32 * kTrsvCLMaxT) {
@@ -1625,7 +1642,7 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
       if (dev >= 0 && dev < 64) done_cl[dev] = true;
     }
     count_launch();
-    k_trsv_cluster<<<kTrsvCL, 32 * warps, smem, s>>>(L, ldl, N, rhs, acc, first, alpha, Wdiag, st);
+    launch_k(k_trsv_cluster, dim3(kTrsvCL), dim3(32 * warps), (size_t)(smem), s, L, ldl, N, rhs, acc, first, alpha, Wdiag, st);
     if (cudaGetLastError() == cudaSuccess) return;
   }
   if (Wdiag && N <= kClusterN) {
@@ -1638,7 +1655,7 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
       if (dev >= 0 && dev < 64) done_blk[dev] = true;
     }
     count_launch();
-    k_trsv_blk<<<1, kBlkThreads, (size_t)(2 * blk_stage_floats(N) + 2048 + 32) * sizeof(float), s>>>(
+    launch_k(k_trsv_blk, dim3(1), dim3(kBlkThreads), (size_t)((size_t)(2 * blk_stage_floats(N) + 2048 + 32) * sizeof(float)), s, 
         L, ldl, N, rhs, acc, first, alpha, Wdiag);
     return;
   }
@@ -1655,11 +1672,11 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    k_trsv_mid<<<1, kMidThreads, smem, s>>>(L, ldl, N, rhs, acc, first, alpha, Wdiag);
+    launch_k(k_trsv_mid, dim3(1), dim3(kMidThreads), (size_t)(smem), s, L, ldl, N, rhs, acc, first, alpha, Wdiag);
     return;
   }
   count_launch();
-  k_trsv_llt<<<1, kTrsvThreads, (size_t)N * sizeof(float), s>>>(L, ldl, N, rhs, acc, first, alpha);
+  launch_k(k_trsv_llt, dim3(1), dim3(kTrsvThreads), (size_t)((size_t)N * sizeof(float)), s, L, ldl, N, rhs, acc, first, alpha);
 }
 
 }  // namespace ssnal

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kStreamThreads) k_stream_f64(const double* __r
                                                                const double* __restrict__ x,
                                                                const double* __restrict__ u, LsParams lp,
                                                                DevState* st, double* __restrict__ partials) {
+  pdl_entry();
   extern __shared__ double sv[];
   __shared__ double wred[kStreamThreads / 32][32];
   __shared__ double red[32];
@@ -148,6 +149,7 @@ constexpr int kFbChunk = 16;
 __global__ void __launch_bounds__(256) k_ls_fallback(const double* __restrict__ x, const double* __restrict__ u,
                                                      const double* __restrict__ t, long long n, LsParams lp,
                                                      DevState* st, double* __restrict__ partials) {
+  pdl_entry();
   __shared__ double red[32];
   if (st->ls_state != 1) return;
   const int extra = lp.max_ls - lp.fused;
@@ -316,6 +318,7 @@ __global__ void __launch_bounds__(kFFThreads, 1) k_stream_ff(const double* __res
                                                              double* __restrict__ out, const double* __restrict__ x,
                                                              const double* __restrict__ u, LsParams lp, DevState* st,
                                                              double* __restrict__ partials, FFCfg cfg) {
+  pdl_entry();
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stages = smem;
   float2* d2 = reinterpret_cast<float2*>(smem + (size_t)kFFStages * kFFStageBytes);
@@ -621,14 +624,15 @@ static void launch_ff(const double* A, long long lda, int m, long long n, const 
   FFCfg cfg = ff_config(m, n);
   long long grid = cfg.ntiles < sms ? cfg.ntiles : sms;
   if (grid < 1) grid = 1;
-  k_stream_ff<MODE, PRESPLIT>
-      <<<(int)grid, kFFThreads, ff_smem(m), s>>>(A, lda, m, n, vec, out, x, u, lp, st, partials, cfg);
+  launch_k(k_stream_ff<MODE, PRESPLIT>, dim3((int)grid), dim3(kFFThreads), (size_t)(ff_smem(m)), s, A, lda, m, n, vec,
+           out, x, u, lp, st, partials, cfg);
 }
 
 // One-time conversion of FP64 A into the float-float pair layout read by the
 // PRESPLIT stream: per column, row pair k is (hi(2k), hi(2k+1), lo(2k), lo(2k+1))
 // as four floats; rows >= m are zero.  Column stride: mm = m rounded up to even.
 __global__ void k_presplit(const double* __restrict__ A, long long lda, int m, long long n, float4* __restrict__ S) {
+  pdl_entry();
   const int pairs = (m + 1) / 2;
   const long long total = (long long)pairs * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -645,7 +649,7 @@ __global__ void k_presplit(const double* __restrict__ A, long long lda, int m, l
 
 void launch_presplit(const double* A, long long lda, int m, long long n, void* S, int sms, cudaStream_t s) {
   count_launch();
-  k_presplit<<<8 * sms, 256, 0, s>>>(A, lda, m, n, reinterpret_cast<float4*>(S));
+  launch_k(k_presplit, dim3(8 * sms), dim3(256), (size_t)(0), s, A, lda, m, n, reinterpret_cast<float4*>(S));
 }
 
 // ---------------------------------------------------------------------------
@@ -733,6 +737,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
                                                               double* __restrict__ partials, LaneCfg cfg,
                                                               const float* __restrict__ cmean,
                                                               const float* __restrict__ cscale) {
+  pdl_entry();
   extern __shared__ __align__(1024) unsigned char smem_lane[];
   constexpr int R = elt_rows(ELT);   // rows per box
   constexpr int P = R / 16;          // row pairs per 16-byte chunk of a column
@@ -1070,7 +1075,7 @@ static void launch_lane(const void* map, int m, long long n, const double* vec, 
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(map);
-  k_stream_lane<MODE, ELT><<<(int)grid, kLThreads, lane_smem(m, stages), s>>>(*tm, m, n, vec, out, x, u, lp, st,
+  launch_k(k_stream_lane<MODE, ELT>, dim3((int)grid), dim3(kLThreads), (size_t)(lane_smem(m, stages)), s, *tm, m, n, vec, out, x, u, lp, st,
                                                                               partials, cfg, cmean, cscale);
 }
 
@@ -1133,16 +1138,17 @@ void launch_stream(int mode, int dtype, const void* A, long long lda, int m, lon
     return;
   }
   if (mode == kModeU)
-    k_stream_f64<kModeU><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
+    launch_k(k_stream_f64<kModeU>, dim3(grid), dim3(kStreamThreads), (size_t)(smem), s, Ad, lda, m, n, vec, out, x, u, lp, st, partials);
   else if (mode == kModeT)
-    k_stream_f64<kModeT><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
+    launch_k(k_stream_f64<kModeT>, dim3(grid), dim3(kStreamThreads), (size_t)(smem), s, Ad, lda, m, n, vec, out, x, u, lp, st, partials);
   else
-    k_stream_f64<kModeGmax><<<grid, kStreamThreads, smem, s>>>(Ad, lda, m, n, vec, out, x, u, lp, st, partials);
+    launch_k(k_stream_f64<kModeGmax>, dim3(grid), dim3(kStreamThreads), (size_t)(smem), s, Ad, lda, m, n, vec, out, x, u, lp, st, partials);
 }
 
 // Flags entries of A (rows < m) that the float-float split cannot represent:
 // non-zero values outside [2^-100, 2^100], subnormals, infinities and NaN.
 __global__ void k_check_range(const double* __restrict__ A, long long lda, int m, long long n, int* bad) {
+  pdl_entry();
   const long long total = lda * n;
   int local = 0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
@@ -1158,7 +1164,7 @@ __global__ void k_check_range(const double* __restrict__ A, long long lda, int m
 
 void launch_check_range(const double* A, long long lda, int m, long long n, int* bad, int sms, cudaStream_t s) {
   count_launch();
-  k_check_range<<<4 * sms, 256, 0, s>>>(A, lda, m, n, bad);
+  launch_k(k_check_range, dim3(4 * sms), dim3(256), (size_t)(0), s, A, lda, m, n, bad);
 }
 
 void launch_ls_fallback(const double* x, const double* u, const double* t, long long n, ProxParams pp, double mu,
@@ -1166,7 +1172,7 @@ void launch_ls_fallback(const double* x, const double* u, const double* t, long 
   if (fused >= max_ls) return;
   LsParams lp{pp, mu, beta, max_ls, fused};
   count_launch();
-  k_ls_fallback<<<grid, 256, 0, s>>>(x, u, t, n, lp, st, partials);
+  launch_k(k_ls_fallback, dim3(grid), dim3(256), (size_t)(0), s, x, u, t, n, lp, st, partials);
 }
 
 }  // namespace ssnal

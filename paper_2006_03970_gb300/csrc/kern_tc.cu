@@ -63,6 +63,7 @@ __device__ __forceinline__ void tri_tile_tc(int id, int& ti, int& tj) {
 __global__ void __launch_bounds__(kTcThreads, 1) k_syrk_tc(const __nv_bfloat16* __restrict__ X, int R, int ldk,
                                                            TcPairs pairs, float alpha, float beta, float* out,
                                                            long long ldo, float* part, DevState* st) {
+  pdl_entry();
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ __align__(8) unsigned long long bars[kTcStages];
   __shared__ unsigned tmem_base;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_syrk_tc(const __nv_bfloat16* 
 // grid = (tiles, 64): block y handles columns 2y, 2y+1 of the tile.
 __global__ void k_syrk_tc_reduce(const float* __restrict__ part, int splits, int R, float alpha, float beta,
                                  float* __restrict__ out, long long ldo) {
+  pdl_entry();
   int ti, tj;
   tri_tile_tc(blockIdx.x, ti, tj);
   const int a0 = ti * 128, b0 = tj * 128;
@@ -220,6 +222,7 @@ __global__ void k_syrk_tc_reduce(const float* __restrict__ part, int splits, int
 // Entries with k >= K are zero up to ldk.
 __global__ void k_panel_bf16(const double* __restrict__ P, long long ldp, int m, int r, int trans, int nsplit,
                              __nv_bfloat16* __restrict__ X, int ldk) {
+  pdl_entry();
   __shared__ double tile[32][33];
   const int R = trans ? m : r, K = trans ? r : m;
   const size_t panel = (size_t)R * ldk;
@@ -275,7 +278,7 @@ void launch_syrk_tc(const double* P, long long ldp, int m, int r, int trans, int
   {
     dim3 grid((ldk + 31) / 32, (R + 31) / 32);
     count_launch();
-    k_panel_bf16<<<grid, 256, 0, s>>>(P, ldp, m, r, trans, nsplit, X, ldk);
+    launch_k(k_panel_bf16, dim3(grid), dim3(256), (size_t)(0), s, P, ldp, m, r, trans, nsplit, X, ldk);
   }
   TcPairs pr;
   if (nsplit == 3) {
@@ -306,10 +309,10 @@ void launch_syrk_tc(const double* P, long long ldp, int m, int r, int trans, int
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   count_launch();
-  k_syrk_tc<<<dim3(tiles, splits), kTcThreads, smem, s>>>(X, R, ldk, pr, alpha, beta, out, ldo, part, st);
+  launch_k(k_syrk_tc, dim3(dim3(tiles, splits)), dim3(kTcThreads), (size_t)(smem), s, X, R, ldk, pr, alpha, beta, out, ldo, part, st);
   if (splits > 1) {
     count_launch();
-    k_syrk_tc_reduce<<<dim3(tiles, 64), 256, 0, s>>>(part, splits, R, alpha, beta, out, ldo);
+    launch_k(k_syrk_tc_reduce, dim3(dim3(tiles, 64)), dim3(256), (size_t)(0), s, part, splits, R, alpha, beta, out, ldo);
   }
 }
 

@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
                                                             const double* __restrict__ d, long long n, int m,
                                                             ProxParams pp, int apply_update, DevState* st,
                                                             long long* counts, double* partials) {
+  pdl_entry();
   __shared__ double red[32];
   __shared__ long long shl[32];
   long long start, stop;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
                                                               const double* __restrict__ u, long long n,
                                                               ProxParams pp, const long long* __restrict__ offsets,
                                                               int32_t* __restrict__ J, double* __restrict__ wJ) {
+  pdl_entry();
   __shared__ long long shl[32];
   __shared__ long long tile_total;
   long long start, stop;
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
 // x <- prox_{sigma p}(x - sigma u): the multiplier update of eq. update_x
 // written through the Moreau decomposition.
 __global__ void k_set_x(double* __restrict__ x, const double* __restrict__ u, long long n, ProxParams pp) {
+  pdl_entry();
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
     x[j] = prox_value(v_of(x[j], u[j], pp.sigma), pp);
 }
@@ -228,6 +231,7 @@ template <class Load>
 __global__ void __launch_bounds__(256) k_gather(Load ld, long long lda, int m, const int32_t* __restrict__ J, const DevState* st,
                          long long r_host, long long rcap, double* __restrict__ P, long long ldp,
                          float* __restrict__ P32, long long ldp32, int* overflow) {
+  pdl_entry();
   const long long r = r_host >= 0 ? r_host : st->r;
   if (r > rcap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *overflow = 1;
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(kVecThreads) k_gemv_n_partial(const double* __
                                                                 const double* __restrict__ coef,
                                                                 const DevState* st, long long r_host,
                                                                 long long rcap, double* __restrict__ part) {
+  pdl_entry();
   const long long r = r_host >= 0 ? r_host : st->r;
   if (r > rcap) return;  // the gather raised the overflow flag; the host redoes this step
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,6 +282,7 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ ou
                                                          const double* __restrict__ bv,
                                                          const double* __restrict__ gv, DevState* st,
                                                          double* scratch) {
+  pdl_entry();
   __shared__ double red[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double o = 0.0;
@@ -337,6 +343,7 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
                                                 const double* __restrict__ bv, const double* __restrict__ gv,
                                                 DevState* stw, double* scratch, double* __restrict__ cpart,
                                                 unsigned* tile_ctr) {
+  pdl_entry();
   __shared__ double part[8][33];
   __shared__ double red[32];
   __shared__ bool tile_last;
@@ -435,6 +442,7 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
 __global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, long long r, const double* __restrict__ v,
                          double* __restrict__ out, const double* __restrict__ h, double ch,
                          const double* __restrict__ q, double cq, double cd) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long tw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -458,9 +466,9 @@ void launch_prox_count(int mode, const double* x, double* u, const double* t, do
                        double* partials, int grid, cudaStream_t s) {
   count_launch();
   if (mode == kProxSupport)
-    k_prox_count<kProxSupport><<<grid, kVecThreads, 0, s>>>(x, u, t, y, d, n, m, pp, 0, st, counts, partials);
+    launch_k(k_prox_count<kProxSupport>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, t, y, d, n, m, pp, 0, st, counts, partials);
   else
-    k_prox_count<kProxThreshold><<<grid, kVecThreads, 0, s>>>(x, u, t, y, d, n, m, pp, apply_update, st, counts,
+    launch_k(k_prox_count<kProxThreshold>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, t, y, d, n, m, pp, apply_update, st, counts,
                                                                partials);
 }
 
@@ -468,9 +476,9 @@ void launch_prox_scatter(int mode, const double* x, const double* u, long long n
                          const long long* offsets, int32_t* J, double* wJ, int grid, cudaStream_t s) {
   count_launch();
   if (mode == kProxSupport)
-    k_prox_scatter<kProxSupport><<<grid, kVecThreads, 0, s>>>(x, u, n, pp, offsets, J, wJ);
+    launch_k(k_prox_scatter<kProxSupport>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp, offsets, J, wJ);
   else
-    k_prox_scatter<kProxThreshold><<<grid, kVecThreads, 0, s>>>(x, u, n, pp, offsets, J, wJ);
+    launch_k(k_prox_scatter<kProxThreshold>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp, offsets, J, wJ);
 }
 
 void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sms, cudaStream_t s) {
@@ -478,7 +486,7 @@ void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sm
   if (g > 8LL * sms) g = 8LL * sms;
   if (g < 1) g = 1;
   count_launch();
-  k_set_x<<<(int)g, kVecThreads, 0, s>>>(x, u, n, pp);
+  launch_k(k_set_x, dim3((int)g), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp);
 }
 
 void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t* J, const DevState* st,
@@ -488,22 +496,24 @@ void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t
   count_launch();
   int* ovf = const_cast<int*>(&st->overflow);
   if (dtype == 0)
-    k_gather<<<grid, 256, 0, s>>>(LoadF64{(const double*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
+    launch_k(k_gather<LoadF64>, dim3(grid), dim3(256), (size_t)0, s, LoadF64{(const double*)A}, lda, m, J, st, r_host,
+             rcap, P, ldp, P32, ldp32, ovf);
   else if (dtype == 1)
-    k_gather<<<grid, 256, 0, s>>>(LoadF32{(const float*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32, ldp32, ovf);
+    launch_k(k_gather<LoadF32>, dim3(grid), dim3(256), (size_t)0, s, LoadF32{(const float*)A}, lda, m, J, st, r_host,
+             rcap, P, ldp, P32, ldp32, ovf);
   else if (dtype == 2)
-    k_gather<<<grid, 256, 0, s>>>(LoadBF16{(const __nv_bfloat16*)A}, lda, m, J, st, r_host, rcap, P, ldp, P32,
-                                  ldp32, ovf);
+    launch_k(k_gather<LoadBF16>, dim3(grid), dim3(256), (size_t)0, s, LoadBF16{(const __nv_bfloat16*)A}, lda, m, J, st,
+             r_host, rcap, P, ldp, P32, ldp32, ovf);
   else
-    k_gather<<<grid, 256, 0, s>>>(LoadI8{(const int8_t*)A, cmean, cscale}, lda, m, J, st, r_host, rcap, P, ldp, P32,
-                                  ldp32, ovf);
+    launch_k(k_gather<LoadI8>, dim3(grid), dim3(256), (size_t)0, s, LoadI8{(const int8_t*)A, cmean, cscale}, lda, m, J,
+             st, r_host, rcap, P, ldp, P32, ldp32, ovf);
 }
 
 void launch_gemv_n_partial(const double* P, long long ldp, int m, const double* coef, const DevState* st,
                            long long r_host, long long rcap, double* part, cudaStream_t s) {
   dim3 grid((m + kVecThreads - 1) / kVecThreads, kGemvGroups);
   count_launch();
-  k_gemv_n_partial<<<grid, kVecThreads, 0, s>>>(P, ldp, m, coef, st, r_host, rcap, part);
+  launch_k(k_gemv_n_partial, dim3(grid), dim3(kVecThreads), (size_t)(0), s, P, ldp, m, coef, st, r_host, rcap, part);
 }
 
 void launch_combine(double* out, const double* a, double ca, const double* b, double cb, const double* part,
@@ -511,7 +521,7 @@ void launch_combine(double* out, const double* a, double ca, const double* b, do
                     double* scratch, cudaStream_t s) {
   int grid = (m + kVecThreads - 1) / kVecThreads;
   count_launch();
-  k_combine<<<grid, kVecThreads, 0, s>>>(out, a, ca, b, cb, part, cs, m, which, y, bb, g, st, scratch);
+  launch_k(k_combine, dim3(grid), dim3(kVecThreads), (size_t)(0), s, out, a, ca, b, cb, part, cs, m, which, y, bb, g, st, scratch);
 }
 
 void launch_gemv_n(const double* P, long long ldp, int m, const double* coef, const DevState* st, long long r_host,
@@ -523,7 +533,7 @@ void launch_gemv_n(const double* P, long long ldp, int m, const double* coef, co
   (void)r_host;
   count_launch();
   dim3 grid((m + 31) / 32, (unsigned)split);
-  k_gemv_n<<<grid, 256, 0, s>>>(P, ldp, m, coef, st, r_host, rcap, out, a, ca, b, cb, cs, which, yv, bv, gv, stw,
+  launch_k(k_gemv_n, dim3(grid), dim3(256), (size_t)(0), s, P, ldp, m, coef, st, r_host, rcap, out, a, ca, b, cb, cs, which, yv, bv, gv, stw,
                                 scratch, cpart, tile_ctr);
 }
 
@@ -534,7 +544,7 @@ void launch_gemv_t(const double* P, long long ldp, int m, long long r, const dou
   long long blocks = (warps * 32 + 255) / 256;
   if (blocks > 4LL * sms) blocks = 4LL * sms;
   count_launch();
-  k_gemv_t<<<(int)blocks, 256, 0, s>>>(P, ldp, m, r, v, out, h, ch, q, cq, cd);
+  launch_k(k_gemv_t, dim3((int)blocks), dim3(256), (size_t)(0), s, P, ldp, m, r, v, out, h, ch, q, cq, cd);
 }
 
 }  // namespace ssnal
