@@ -45,6 +45,53 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return out;
 }
 
+// Deterministic multi-value block reduction.  FP64 arithmetic is slow on this
+// GPU (about two lanes per clock per SM: one warp-wide add holds the pipe for 16
+// cycles), so the adds are kept to a minimum.  Threads of the first nw warps store
+// their K values to shared memory; warp 0 adds them per lane (lane l takes
+// threads l, l + 32, ... in order) and reduces the 32 lane sums by transposition:
+// at each step the lanes of a pair exchange half of their values, about K +
+// log2(32 / K) adds per lane instead of 5 K for K separate warp sums.
+// Thread k < K of warp 0 returns total k.  red: K * 32 * nw doubles.
+template <int K>
+__device__ __forceinline__ double block_sum_k(const double (&v)[K], double* red, int nw) {
+  static_assert(K >= 1 && K <= 32, "1..32 values");
+  constexpr int KP = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nt = 32 * nw;
+  __syncthreads();  // red may still be read by an earlier call
+  if (tid < nt)
+#pragma unroll
+    for (int k = 0; k < K; k++) red[k * nt + tid] = v[k];
+  __syncthreads();
+  double out = 0.0;
+  if (tid < 32) {
+    double s[KP];
+#pragma unroll
+    for (int k = 0; k < KP; k++) {
+      double a = 0.0;
+      if (k < K)
+        for (int w = 0; w < nw; w++) a += red[k * nt + lane + 32 * w];
+      s[k] = a;
+    }
+#pragma unroll
+    for (int h = KP / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < h; i++) {
+        const double send = up ? s[i] : s[i + h];
+        const double keep = up ? s[i + h] : s[i];
+        s[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    // lane l now holds a partial of value l / (32 / KP); finish over the low bits
+#pragma unroll
+    for (int o = 16 / KP; o >= 1; o >>= 1) s[0] += __shfl_xor_sync(0xffffffffu, s[0], o);
+    out = __shfl_sync(0xffffffffu, s[0], (lane < K ? lane : 0) * (32 / KP));
+  }
+  return out;
+}
+
 __device__ __forceinline__ double block_max(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = (blockDim.x + 31) >> 5;
@@ -99,7 +146,14 @@ __device__ __forceinline__ double prox_value(double v, const ProxParams& pp) {
   return v < 0.0 ? -w : w;
 }
 
-__device__ __forceinline__ bool is_active(double v, const ProxParams& pp) { return fabs(v) > pp.thr; }
+// |v| > thr, compared on the bit patterns (thr >= 0; for finite values the
+// integer order of non-negative doubles is their numeric order), which keeps the
+// test off the FP64 pipe.
+__device__ __forceinline__ bool abs_gt(double v, double thr) {
+  return (unsigned long long)(__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL) >
+         (unsigned long long)__double_as_longlong(thr);
+}
+__device__ __forceinline__ bool is_active(double v, const ProxParams& pp) { return abs_gt(v, pp.thr); }
 
 // v = x - sigma*u with two roundings (no contraction into an FMA), the same
 // rounding sequence as the plain elementwise evaluation of the definition.
@@ -185,6 +239,33 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   }
   return false;
 }
+// ---- thread-block clusters: rank, size, distributed shared memory, barrier
+__device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ double ld_dsmem(unsigned addr) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_dsmem(unsigned addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Launches kernel k on stream s with programmatic stream serialization (see
 // pdl_entry); if the launch with the attribute is refused, launches plainly.
 template <typename... ExpT, typename... ActT>

@@ -558,6 +558,11 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
 // reciprocal diagonal, a staging copy of it, and the mbarriers.
 namespace cgx = cooperative_groups;
 constexpr int kClusterCTAs = 8;
+// Threads per CTA of k_chol_cluster: warps 0-3 keep the diagonal tiles (warp 0
+// factors), warps 4 and 8 share warp 0's scheduler and only take part in the
+// barriers, warps 5-7 and 9-11 do the trailing updates.
+constexpr int kCholThreads = 384;
+constexpr int kCholTrail = 6;  // trailing warps
 constexpr int kClusterN = 640;
 constexpr int kClusterT = kClusterN / 32;                 // 20 tiles per side
 constexpr int kClusterDoubleT = 16;                       // double-buffered panel up to this many tile rows
@@ -578,11 +583,6 @@ constexpr size_t cluster_smem_max() {
 static_assert(cluster_slots(kClusterT) <= 32, "one lane per owned slot");
 static_assert(cluster_smem_max() <= 232448 - 1024, "shared memory per CTA");
 
-__device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank) {
-  unsigned r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-  return r;
-}
 // bulk copy of `bytes` from this CTA's shared memory to (possibly) another
 // CTA's, completing `bytes` on that CTA's mbarrier
 __device__ __forceinline__ void bulk_s2c(unsigned dst, unsigned src, unsigned bytes, unsigned bar) {
@@ -590,8 +590,6 @@ __device__ __forceinline__ void bulk_s2c(unsigned dst, unsigned src, unsigned by
                "r"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
-__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
-__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ int tri_index(int i, int j) { return i * (i + 1) / 2 + j; }
 
@@ -619,12 +617,15 @@ __device__ __forceinline__ void tile_update_warp(float* C, const float* Pi, cons
     for (int v = 0; v < 8; v++) C[(4 * tr + u) * 33 + 8 * tc + v] -= acc[u][v];
 }
 
-// Factor the 32x32 tile D (row stride 33) in place, D = L L^T, by one warp:
-// lane l holds row l; in step q every lane publishes its entry of column q in
-// cb (64 floats, double-buffered) and reads the whole column back with
-// broadcast loads.  Entries above the diagonal collect products that are never
-// read.  Also writes U = L^T (row stride 32) and the reciprocal diagonal to
-// U[1024..].  Returns false if a pivot was not positive (it is replaced by 1).
+// Factor the 32x32 tile D (row stride 33) in place, D = L L^T, by one warp,
+// two pivots per round: lane l holds row l; in round q (pivots q, q+1) every
+// lane publishes its entries of columns q and q+1 in cb (2 x 32 floats,
+// double-buffered), factors the 2x2 pivot block from broadcast loads, forms
+// L_lq, L_l,q+1 and applies the rank-2 update as a Schur complement on the
+// unscaled columns, A_lc -= alpha_l A_cq + beta_l A_c,q+1, so that one broadcast
+// serves both pivots.  Entries above the diagonal collect products that are
+// never read.  Also writes U = L^T (row stride 32) and the reciprocal diagonal
+// to U[1024..].  Returns false if a pivot was not positive (it is replaced by 1).
 __device__ __forceinline__ bool factor_tile_warp(float* D, float* U, float* cb, int lane) {
   float row[32];
 #pragma unroll
@@ -632,28 +633,42 @@ __device__ __forceinline__ bool factor_tile_warp(float* D, float* U, float* cb, 
   bool bad = false;
   float rl = 1.0f;
 #pragma unroll
-  for (int q = 0; q < 32; q++) {
-    float* col = cb + (q & 1) * 32;
-    const float u = row[q];  // A_lq after the updates of steps < q
-    col[lane] = u;
+  for (int q = 0; q < 32; q += 2) {
+    float* col = cb + ((q >> 1) & 1) * 64;  // [0..31]: column q, [32..63]: column q+1
+    const float u0 = row[q], u1 = row[q + 1];  // A_lq, A_l,q+1 after the earlier rounds
+    col[lane] = u0;
+    col[32 + lane] = u1;
     __syncwarp();
-    float piv = col[q];
-    if (!(piv > 0.0f)) {
+    float a00 = col[q], a10 = col[q + 1], a11 = col[32 + q + 1];
+    if (!(a00 > 0.0f)) {
       bad = true;
-      piv = 1.0f;
+      a00 = 1.0f;
     }
-    const float t = u * __fdividef(1.0f, piv);
-    const float rs = rsqrtf(piv);
-    row[q] = u * rs;  // L_lq
-    if (lane == q) rl = rs;
+    const float r0 = rsqrtf(a00);
+    const float l10 = a10 * r0;
+    float d1 = fmaf(-l10, l10, a11);
+    if (!(d1 > 0.0f)) {
+      bad = true;
+      d1 = 1.0f;
+    }
+    const float r1 = rsqrtf(d1);
+    const float x0 = u0 * r0;                  // L_lq
+    const float x1 = fmaf(-x0, l10, u1) * r1;  // L_l,q+1
+    row[q] = x0;
+    row[q + 1] = x1;
+    if (lane == q) rl = r0;
+    if (lane == q + 1) rl = r1;
+    const float beta = x1 * r1;
+    const float alpha = r0 * fmaf(-beta, l10, x0);
 #pragma unroll
     for (int g = 0; g < 8; g++) {
-      if (4 * g + 3 > q) {  // A_lc -= A_lq A_cq / A_qq, c > q
-        const float4 v = reinterpret_cast<const float4*>(col)[g];
-        const float vv[4] = {v.x, v.y, v.z, v.w};
+      if (4 * g + 3 > q + 1) {
+        const float4 v0 = reinterpret_cast<const float4*>(col)[g];
+        const float4 v1 = reinterpret_cast<const float4*>(col + 32)[g];
+        const float c0[4] = {v0.x, v0.y, v0.z, v0.w}, c1[4] = {v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
         for (int e = 0; e < 4; e++)
-          if (4 * g + e > q) row[4 * g + e] = fmaf(-t, vv[e], row[4 * g + e]);
+          if (4 * g + e > q + 1) row[4 * g + e] = fmaf(-alpha, c0[e], fmaf(-beta, c1[e], row[4 * g + e]));
       }
     }
   }
@@ -665,6 +680,26 @@ __device__ __forceinline__ bool factor_tile_warp(float* D, float* U, float* cb, 
   }
   U[1024 + lane] = rl;
   return !bad;
+}
+
+// D -= P P^T on rows 8g .. 8g+7 of the lower triangle of the 32x32 tile D (row
+// stride 33) by one warp; P = L^T of one panel tile (row stride 32).  Same
+// operands and summation order per entry as tile_update_warp.
+__device__ __forceinline__ void diag_update_rows(float* D, const float* P, int g, int lane) {
+  const int r = 8 * g + (lane >> 2), c0 = 8 * (lane & 3);
+  float acc[8] = {};
+#pragma unroll 8
+  for (int q = 0; q < 32; q++) {
+    const float a = P[q * 32 + r];
+    const float4 b0 = reinterpret_cast<const float4*>(P + q * 32 + c0)[0];
+    const float4 b1 = reinterpret_cast<const float4*>(P + q * 32 + c0)[1];
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int e = 0; e < 8; e++) acc[e] = fmaf(a, bv[e], acc[e]);
+  }
+#pragma unroll
+  for (int e = 0; e < 8; e++)
+    if (c0 + e <= r) D[r * 33 + c0 + e] -= acc[e];
 }
 
 // Solve X L^T = A for one 32x32 panel tile A (row stride 33) by one warp, lane
@@ -694,17 +729,28 @@ __device__ __forceinline__ void panel_solve_warp(float* A, const float* U, int l
   for (int c = 0; c < 32; c++) A[c * 32 + lane] = x[c];
 }
 
-// Lanes 0..kClusterCTAs-1 of a warp push `bytes` from src (this CTA) to dst in
-// the CTAs of `mask`, completing on their mbarrier `bar`.  The data must have
-// been fenced for the async proxy and synchronised within the warp.
+// A warp pushes `bytes` from src (this CTA) to dst in the CTAs of `mask`,
+// completing on their mbarrier `bar`: the copy to CTA `first` (the next
+// consumer on the critical chain) is issued on its own, then lanes 0..7 issue
+// the others.  The data must have been fenced for the async proxy and
+// synchronised within the warp.
 __device__ __forceinline__ void push_tile(unsigned src, unsigned dst, unsigned bytes, unsigned bar, unsigned mask,
-                                          int lane) {
-  if (lane < kClusterCTAs && (mask >> lane & 1u)) bulk_s2c(cluster_addr(dst, lane), src, bytes, cluster_addr(bar, lane));
+                                          int first, int lane) {
+  if (lane == 0 && (mask >> first & 1u)) bulk_s2c(cluster_addr(dst, first), src, bytes, cluster_addr(bar, first));
+  __syncwarp();
+  if (lane < kClusterCTAs && lane != first && (mask >> lane & 1u))
+    bulk_s2c(cluster_addr(dst, lane), src, bytes, cluster_addr(bar, lane));
 }
 
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
+// Named barrier of the four diagonal warps (0-3) of a CTA.
+__device__ __forceinline__ void diag_quad_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThreads)
     k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag) {
   pdl_entry();
+  __shared__ __align__(16) float fcol[128];                  // column exchange of the diagonal factor
+  __shared__ __align__(8) unsigned long long tbar_s[2 * kClusterT];  // panel tile arrivals per (buffer, tile row)
+  __shared__ __align__(8) unsigned long long dbar_s;               // diagonal factor arrivals
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) float csm[];
@@ -714,10 +760,8 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   float* panel = own + cluster_slots(T) * kTileF;          // nbuf x T transposed panel tiles
   float* dbuf = panel + nbuf * T * 1024;                   // L^T of the next diagonal tile, 1/diag at [1024..]
   float* ustage = dbuf + kTileF;                           // the owner of a diagonal tile builds that buffer here
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ustage + kTileF);
-  const unsigned pbar0 = smem_u32(bars), dbar = smem_u32(bars + 2);  // panel arrivals per buffer, diagonal arrivals
+  const unsigned dbar = smem_u32(&dbar_s);
   __shared__ int slot_ij[32];                    // (i << 8) | j of the tile in each owned slot
-  __shared__ __align__(16) float fcol[64];       // column exchange of the diagonal factor
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned all = (1u << kClusterCTAs) - 1u;
   const int nslots = (T * (T + 1) / 2 - rank + kClusterCTAs - 1) / kClusterCTAs;
@@ -732,7 +776,13 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   const int my_i = lane < nslots ? slot_ij[lane] >> 8 : -1;
   const int my_j = lane < nslots ? slot_ij[lane] & 255 : -1;
   auto panel_tile = [&](int k, int i) { return panel + ((k % nbuf) * T + i) * 1024; };
-  auto pbar = [&](int k) { return pbar0 + 8u * (unsigned)(k % nbuf); };
+  // tile i of panel k arrives on tbar(k, i); its phase parity is tpar(k)
+  auto tbar = [&](int k, int i) { return smem_u32(&tbar_s[(k % nbuf) * kClusterT + i]); };
+  auto tpar = [&](int k) { return (unsigned)((k / nbuf) & 1); };
+  auto owner = [&](int i, int j) { return tri_index(i, j) % kClusterCTAs; };
+  // the first consumer of panel tile (i, k) on the critical chain: the owner of
+  // (k+1, k+1) for the first tile, else the owner of (i, k+1), which solves it next
+  auto first_of = [&](int i, int k) { return i == k + 1 ? owner(k + 1, k + 1) : owner(i, k + 1); };
 
   // ---- load the owned tiles with 4-byte async copies (all in flight at once;
   //      consecutive threads read consecutive rows of a column), zero outside
@@ -741,7 +791,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   for (int sl = 0; sl < nslots; sl++) {
     const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
     float* dst = own + sl * kTileF;
-    for (int e = tid; e < 1024; e += 256) {
+    for (int e = tid; e < 1024; e += blockDim.x) {
       const int r = e & 31, c = e >> 5;
       const int gi = ti * 32 + r, gj = tj * 32 + c;
       const bool in = gi < N && gj < N;
@@ -764,13 +814,16 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     return m;
   };
   if (tid == 0) {
-    mbar_init(pbar0, 1);
-    mbar_init(pbar0 + 8, 1);
+    for (int b = 0; b < nbuf; b++)
+      for (int i = 0; i < T; i++) mbar_init(smem_u32(&tbar_s[b * kClusterT + i]), 1);
     mbar_init(dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    // arm for the first diagonal push and the first panel
+    // arm for the first diagonal push and the first panel(s): panel k + nbuf is
+    // armed at the end of step k, once every tile of panel k has arrived
     if (receivers_of(0) >> rank & 1u) mbar_expect_tx(dbar, kTileBytes);
-    if (T > 1) mbar_expect_tx(pbar(0), (unsigned)(T - 1) * kPanelBytes);
+    for (int i = 1; i < T; i++) mbar_expect_tx(tbar(0, i), kPanelBytes);
+    if (nbuf == 2)
+      for (int i = 2; i < T; i++) mbar_expect_tx(tbar(1, i), kPanelBytes);
   }
   __syncthreads();
   cluster.sync();
@@ -783,7 +836,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     bad |= !factor_tile_warp(own, ustage, fcol, lane);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, receivers_of(0), lane);
+    push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, receivers_of(0), owner(1, 0), lane);
   }
   if (receivers_of(0) >> rank & 1u) {
     if (ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
@@ -796,7 +849,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
       panel_solve_warp(Ai, dbuf, lane);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      push_tile(smem_u32(Ai), smem_u32(panel_tile(0, i)), kPanelBytes, pbar(0), all, lane);
+      push_tile(smem_u32(Ai), smem_u32(panel_tile(0, i)), kPanelBytes, tbar(0, i), all, first_of(i, 0), lane);
     }
   }
 
@@ -804,72 +857,117 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     const int next = tri_index(k + 1, k + 1);
     const bool diag_here = next % kClusterCTAs == rank;
     const unsigned recv_next = receivers_of(k + 1);
+    const bool solve_here = (recv_next >> rank & 1u) != 0;
     // arm for the push of the next diagonal tile (the previous one was consumed)
-    if (tid == 0 && (recv_next >> rank & 1u)) mbar_expect_tx(dbar, kTileBytes);
-    // panel column k has arrived
-    if (ok && !mbar_wait(pbar(k), (unsigned)((k / nbuf) & 1))) ok = false;
-    // arm for panel column k+1 (its buffer's previous phase was consumed)
-    if (tid == 0 && k + 2 < T) mbar_expect_tx(pbar(k + 1), (unsigned)(T - k - 2) * kPanelBytes);
-    // ---- lookahead: warp 0 of the owner of (k+1, k+1) updates, factors and publishes it
-    if (diag_here && warp == 0) {
-      float* D = own + (next / kClusterCTAs) * kTileF;
-      const float* Pk = panel_tile(k, k + 1);
-      tile_update_warp(D, Pk, Pk, lane);
-      __syncwarp();
-      bad |= !factor_tile_warp(D, ustage, fcol, lane);
-      if (recv_next) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, recv_next, lane);
+    if (tid == 0 && solve_here) mbar_expect_tx(dbar, kTileBytes);
+    // ---- diagonal warps 0-3 (one per scheduler) keep the owned diagonal tiles and
+    //      synchronise only with each other.  In the owner of (k+1, k+1) they update
+    //      it with panel tile (k+1, k), eight rows each, as soon as that tile has
+    //      arrived; warp 0 factors and publishes it while warps 1-3 apply panel k
+    //      to the other owned diagonal tiles (elsewhere all four share those).
+    if (warp < 4) {
+      diag_quad_sync();  // the four are done with step k-1
+      if (diag_here) {
+        float* D = own + (next / kClusterCTAs) * kTileF;
+        if (ok && !mbar_wait(tbar(k, k + 1), tpar(k))) ok = false;
+        if (ok) diag_update_rows(D, panel_tile(k, k + 1), warp, lane);
+        diag_quad_sync();
+        if (warp == 0) {
+          bad |= !factor_tile_warp(D, ustage, fcol, lane);
+          if (recv_next) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, recv_next,
+                      k + 2 < T ? owner(k + 2, k + 1) : rank, lane);
+          }
+        }
       }
-    }
-    // ---- trailing update of the other owned tiles (i, j), k < j <= i, one warp
-    //      per tile; the next panel column k+1 first
-    if (!(diag_here && warp == 0) && ok) {
-      const int nw = diag_here ? kClusterCTAs - 1 : kClusterCTAs;
-      const int me = diag_here ? warp - 1 : warp;
-      int turn = 0;  // cycles through 0 .. nw-1 over the work list
-      for (int pass = 0; pass < 2; pass++) {
-        unsigned m = __ballot_sync(0xffffffffu, pass == 0 ? (my_j == k + 1 && my_i > k + 1) : (my_j > k + 1));
-        for (; m; m &= m - 1) {
-          const bool mine = turn == me;
-          turn = (turn + 1 == nw) ? 0 : turn + 1;
-          if (!mine) continue;
-          const int sl = __ffs(m) - 1;
-          const int ti = __shfl_sync(0xffffffffu, my_i, sl), tj = __shfl_sync(0xffffffffu, my_j, sl);
-          tile_update_warp(own + sl * kTileF, panel_tile(k, ti), panel_tile(k, tj), lane);
+      if (ok && !(diag_here && warp == 0)) {
+        const int nd = diag_here ? 3 : 4, me = diag_here ? warp - 1 : warp;
+        int e = 0;
+        for (unsigned m = __ballot_sync(0xffffffffu, my_i == my_j && my_i > k + 1); m; m &= m - 1, e++) {
+          if (e % nd != me) continue;
+          const int sl = __ffs(m) - 1, ti = __shfl_sync(0xffffffffu, my_i, sl);
+          if (ok && !mbar_wait(tbar(k, ti), tpar(k))) ok = false;
+          tile_update_warp(own + sl * kTileF, panel_tile(k, ti), panel_tile(k, ti), lane);
         }
       }
     }
-    __syncthreads();
-    // ---- solve the owned tiles of panel column k+1
-    if (recv_next >> rank & 1u) {
-      if (ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
-      dphase++;
-      unsigned m = __ballot_sync(0xffffffffu, my_j == k + 1 && my_i > k + 1);
-      for (int e = 0; m; e++, m &= m - 1) {
-        if ((e & 7) != warp) continue;
-        panel_solve_warp(own + (__ffs(m) - 1) * kTileF, dbuf, lane);
+    // ---- trailing warps 5-7, 9-11 (schedulers 1-3): owned off-diagonal slot s
+    //      belongs to trailing warp s % 6 for good, so all updates of a tile, its
+    //      solve and its push run in one warp's program order.  The tiles of panel column k+1 come first, each
+    //      solved once the diagonal factor has arrived and pushed at once.
+    unsigned mine = 0;    // slots of panel column k+1 this warp updated and solved
+    bool pushed = false;  // this warp has waited on the cluster barrier and pushed them
+    const int trail = warp >= 5 && warp != 8 ? (warp < 8 ? warp - 5 : warp - 6) : -1;
+    if (trail >= 0 && ok) {
+      const bool lane_mine = lane % kCholTrail == trail;
+      for (unsigned m = __ballot_sync(0xffffffffu, lane_mine && my_j == k + 1 && my_i > k + 1); m; m &= m - 1) {
+        const int sl = __ffs(m) - 1;
+        const int ti = __shfl_sync(0xffffffffu, my_i, sl);
+        if (ok && !mbar_wait(tbar(k, ti), tpar(k))) ok = false;
+        if (ok && !mbar_wait(tbar(k, k + 1), tpar(k))) ok = false;
+        tile_update_warp(own + sl * kTileF, panel_tile(k, ti), panel_tile(k, k + 1), lane);
+        mine |= 1u << sl;
+      }
+      if (mine) {
+        if (ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
+        for (unsigned m = mine; m; m &= m - 1) panel_solve_warp(own + (__ffs(m) - 1) * kTileF, dbuf, lane);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (nbuf == 2) {
+          // the buffer of panel k+1 held panel k-1, free once every thread has
+          // arrived after step k-1: wait for that phase here and push at once,
+          // ahead of this warp's share of the rest of the trailing update
+          cluster_wait();
+          pushed = true;
+          for (unsigned m = mine; m; m &= m - 1) {
+            const int sl = __ffs(m) - 1, i = __shfl_sync(0xffffffffu, my_i, sl);
+            push_tile(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, tbar(k + 1, i), all,
+                      first_of(i, k + 1), lane);
+          }
+        }
+      }
+      for (unsigned m = __ballot_sync(0xffffffffu, lane_mine && my_j > k + 1 && my_i != my_j); m; m &= m - 1) {
+        const int sl = __ffs(m) - 1;
+        const int ti = __shfl_sync(0xffffffffu, my_i, sl), tj = __shfl_sync(0xffffffffu, my_j, sl);
+        if (ok && !mbar_wait(tbar(k, ti), tpar(k))) ok = false;
+        if (ok && !mbar_wait(tbar(k, tj), tpar(k))) ok = false;
+        tile_update_warp(own + sl * kTileF, panel_tile(k, ti), panel_tile(k, tj), lane);
       }
     }
+    // warp 5: every tile of panel k has arrived; arm panel k + nbuf, which reuses
+    // the same barriers (before this warp's cluster arrive, hence before any push)
+    if (warp == 5) {
+      bool got = ok;
+      for (int i = k + 1 + lane; i < T; i += 32)
+        if (got && !mbar_wait(tbar(k, i), tpar(k))) got = false;
+      got = __all_sync(0xffffffffu, got);
+      if (!got) ok = false;
+      if (got && lane == 0)
+        for (int i = k + nbuf + 1; i < T; i++) mbar_expect_tx(tbar(k + nbuf, i), kPanelBytes);
+      __syncwarp();
+    }
+    if (solve_here) {
+      // warp 0 (tid 0 arms the next phase) makes sure this phase has completed
+      if (warp == 0 && ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
+      dphase++;
+    }
     // the buffer that panel k+1 goes to must be free: with two buffers it was
-    // read in step k-1 (the wait matches the arrive issued then); with one it
-    // is panel k itself, so every CTA must be done with this step
+    // read in step k-1 (the wait matches the arrive issued then; warps that
+    // pushed have waited already); with one it is panel k itself, so every CTA
+    // must be done with this step
     if (nbuf == 2) {
-      cluster_wait();
-      cluster_arrive();  // this CTA is done reading panel k
+      if (!pushed) cluster_wait();
+      cluster_arrive();  // this warp is done reading panel k
     } else {
       cluster.sync();
     }
-    if (recv_next >> rank & 1u) {
-      unsigned m = __ballot_sync(0xffffffffu, my_j == k + 1 && my_i > k + 1);
-      for (int e = 0; m; e++, m &= m - 1) {
-        if ((e & 7) != warp) continue;
+    if (!pushed)  // each warp pushes the tiles it solved (after its own proxy fence)
+      for (unsigned m = mine; m; m &= m - 1) {
         const int sl = __ffs(m) - 1, i = __shfl_sync(0xffffffffu, my_i, sl);
-        push_tile(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, pbar(k + 1), all, lane);
+        push_tile(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, tbar(k + 1, i), all,
+                  first_of(i, k + 1), lane);
       }
-    }
   }
   if (nbuf == 2) cluster_wait();
   if (bad) st->chol_fail = 1;
@@ -901,7 +999,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
   for (int sl = 0; sl < nslots; sl++) {
     const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
     const float* src = own + sl * kTileF;
-    for (int e = tid; e < 1024; e += 256) {
+    for (int e = tid; e < 1024; e += blockDim.x) {
       const int r = e & 31, c = e >> 5;
       const int gi = ti * 32 + r, gj = tj * 32 + c;
       if (gi < N && gj < N && gi >= gj) G[gi + (long long)gj * ld] = (ti == tj) ? src[r * 33 + c] : src[c * 32 + r];
@@ -1521,7 +1619,7 @@ bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, doubl
     if (dev >= 0 && dev < 64) done[dev] = true;
   }
   count_launch(4);
-  launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(256), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
+  launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
   launch_k(k_inv_trace_setup, dim3(64), dim3(256), (size_t)(0), s, S, ldS, N, Np);
   const size_t tsm = (size_t)(32 * Np + 1024 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
   launch_k(k_trsm_blocks, dim3(Np / 32), dim3(256), (size_t)(tsm), s, S, ldS, 0, Np, Np, Np, Wdiag);
@@ -1545,7 +1643,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(256), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag);
+    launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag);
     if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
   }
   if (Wdiag && N <= kMaxM) {
@@ -1566,7 +1664,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       const int nk = N - k0 < B ? N - k0 : B;
       float* Gkk = G + k0 + (long long)k0 * ldg;
       count_launch();
-      launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(256), (size_t)(cluster_smem((nk + 31) / 32)), s, Gkk, ldg, nk, st,
+      launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((nk + 31) / 32)), s, Gkk, ldg, nk, st,
                                                                              Wdiag + (long long)(k0 / 32) * 1024);
       const int r0 = k0 + nk, R = N - r0;
       if (R > 0) {

@@ -737,7 +737,10 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
                                                               double* __restrict__ partials, LaneCfg cfg,
                                                               const float* __restrict__ cmean,
                                                               const float* __restrict__ cscale) {
-  pdl_entry();
+  // A is never written while a solve runs: the first copies of every warp's ring
+  // are issued before waiting for the preceding kernel (programmatic dependent
+  // launch); the vectors are read only after the wait.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(1024) unsigned char smem_lane[];
   constexpr int R = elt_rows(ELT);   // rows per box
   constexpr int P = R / 16;          // row pairs per 16-byte chunk of a column
@@ -757,6 +760,28 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     dmax_bits = 0ull;
   }
   __syncthreads();
+  // ---- work split: the CTA owns column groups g = blockIdx.x + q * gridDim.x;
+  // warp w streams row chunks w, w + 8, ... of each group through its own ring.
+  // Per group, the warps' per-column partials are merged in shared memory.
+  __shared__ float2 part[2][kLWarps][kLCols];
+  const long long ngrp = (long long)blockIdx.x < cfg.groups ? (cfg.groups - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int nw = warp < cfg.chunks ? (cfg.chunks - warp + kLWarps - 1) / kLWarps : 0;  // chunks per group
+  const long long total = ngrp * nw;
+  unsigned char* wring = ring + (size_t)warp * cfg.stages * kLBoxBytes;
+  unsigned long long* wbars = bars + warp * cfg.stages;
+  auto issue = [&](long long item) {
+    const long long q = item / nw;
+    const int ch = warp + kLWarps * (int)(item % nw);
+    const int sidx = (int)(item % cfg.stages);
+    const unsigned bar = smem_u32(wbars + sidx);
+    mbar_expect_tx(bar, kLBoxBytes);
+    tma_load_2d(smem_u32(wring + (size_t)sidx * kLBoxBytes), &tmap, ch * elt_box_inner(ELT),
+                (int)(((long long)blockIdx.x + q * gridDim.x) * kLCols), bar);
+  };
+  if (lane == 0)
+    for (long long it = 0; it < total && it < cfg.stages; it++) issue(it);
+  __syncwarp();
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   // the vector, scaled by a power of two and split: D4[k] = (dh0, dh1, -dh0, -dh1), DL[k] = (-dl0, -dl1)
   unsigned long long mb = 0ull;
   for (int i = tid; i < m; i += blockDim.x) {
@@ -791,27 +816,6 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     ysum = block_sum(a, red);
   }
 
-  // ---- work split: the CTA owns column groups g = blockIdx.x + q * gridDim.x;
-  // warp w streams row chunks w, w + 8, ... of each group through its own ring.
-  // Per group, the warps' per-column partials are merged in shared memory.
-  __shared__ float2 part[2][kLWarps][kLCols];
-  const long long ngrp = (long long)blockIdx.x < cfg.groups ? (cfg.groups - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const int nw = warp < cfg.chunks ? (cfg.chunks - warp + kLWarps - 1) / kLWarps : 0;  // chunks per group
-  const long long total = ngrp * nw;
-  unsigned char* wring = ring + (size_t)warp * cfg.stages * kLBoxBytes;
-  unsigned long long* wbars = bars + warp * cfg.stages;
-  auto issue = [&](long long item) {
-    const long long q = item / nw;
-    const int ch = warp + kLWarps * (int)(item % nw);
-    const int sidx = (int)(item % cfg.stages);
-    const unsigned bar = smem_u32(wbars + sidx);
-    mbar_expect_tx(bar, kLBoxBytes);
-    tma_load_2d(smem_u32(wring + (size_t)sidx * kLBoxBytes), &tmap, ch * elt_box_inner(ELT),
-                (int)(((long long)blockIdx.x + q * gridDim.x) * kLCols), bar);
-  };
-  if (lane == 0)
-    for (long long it = 0; it < total && it < cfg.stages; it++) issue(it);
-  __syncwarp();
 
   double s_lane = 1.0;
   if (MODE == kModeT)

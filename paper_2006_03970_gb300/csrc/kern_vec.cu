@@ -6,6 +6,8 @@
 // Every reduction runs in a fixed order, so results are bitwise repeatable.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ssnal {
@@ -13,6 +15,9 @@ namespace ssnal {
 std::atomic<long long> g_launches{0};
 
 constexpr int kVecThreads = 256;
+// Blocks per thread in the last block's scan of the per-block counts (the O(n)
+// passes run at most kScanPer * kVecThreads blocks).
+constexpr int kScanPer = 4;
 
 // Blocks for the O(n) passes: at most two per SM and at least 256 entries per
 // block, so that the FP64 work (a few dozen FP64 operations per entry, at the
@@ -20,6 +25,7 @@ constexpr int kVecThreads = 256;
 int vec_grid(long long n, int sms) {
   long long g = (n + 255) / 256;
   long long cap = 2LL * sms;
+  if (cap > (long long)kScanPer * kVecThreads) cap = (long long)kScanPer * kVecThreads;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
@@ -61,8 +67,9 @@ __device__ __forceinline__ void block_range(long long n, long long& start, long 
 
 // Pass 1 of the prox / active-set step.  Optionally applies the accepted
 // line-search step first (u += s t, y += s d).  Per block: number of active
-// entries and partial norms; the last block scans the counts into offsets and
-// reduces the norms into the state.
+// entries and partial norms (one six-value block reduction); the last block
+// loads every block's results at once, scans the counts into offsets and
+// reduces the norms into the state, all in a fixed order.
 // counts: [0, grid) per-block counts, [grid, 2*grid] exclusive offsets.
 // partials: grid x 6 doubles.
 template <int MODE>
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
                                                             ProxParams pp, int apply_update, DevState* st,
                                                             long long* counts, double* partials) {
   pdl_entry();
-  __shared__ double red[32];
+  __shared__ double red[5 * kVecThreads];
   __shared__ long long shl[32];
   long long start, stop;
   block_range(n, start, stop);
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
   if (apply_update && blockIdx.x == 0) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = __dadd_rn(y[i], __dmul_rn(s, d[i]));
   }
-  long long cnt = 0;
+  unsigned cnt = 0;
   double w2 = 0, w1 = 0, xw2 = 0, vw2 = 0, pen = 0;
   for (long long j = start + threadIdx.x; j < stop; j += blockDim.x) {
     const double xj = x[j];
@@ -95,59 +102,84 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
     }
     const double v = v_of(xj, uj, pp.sigma);
     // the count uses the active test itself (eq. Q_def); w only feeds the norms,
-    // so the reciprocal of 1 + sigma*lam2 replaces the division here
-    const bool act = is_active(v, pp);
-    const double mag = act ? __dsub_rn(fabs(v), pp.thr) * pp.inv_onep : 0.0;
-    const double w = v < 0.0 ? -mag : mag;
-    if (act) cnt++;
-    w2 += w * w;
-    w1 += fabs(w);
-    xw2 += (xj - w) * (xj - w);
-    vw2 += (v - w) * (v - w);
-    const double e = fmax(fabs(uj) - pp.lam1, 0.0);
-    pen += e * e;
+    // so the reciprocal of 1 + sigma*lam2 replaces the division here.  Terms that
+    // are exactly zero (w = 0, x = 0, |u| <= lam1) are skipped: FP64 is slow here
+    if (is_active(v, pp)) {
+      cnt++;
+      const double mag = __dsub_rn(fabs(v), pp.thr) * pp.inv_onep;  // > 0
+      const double w = v < 0.0 ? -mag : mag;
+      w2 += w * w;
+      w1 += mag;
+      xw2 += (xj - w) * (xj - w);
+      vw2 += (v - w) * (v - w);
+    } else {  // w = 0
+      vw2 += v * v;
+      if (xj != 0.0) xw2 += xj * xj;
+    }
+    if (abs_gt(uj, pp.lam1)) {
+      const double e = fabs(uj) - pp.lam1;
+      pen += e * e;
+    }
   }
-  // block totals
-  long long tot = block_incl_scan(cnt, shl);
-  if (threadIdx.x == kVecThreads - 1) counts[blockIdx.x] = tot;
-  double q[5] = {w2, w1, xw2, vw2, pen};
-  for (int k = 0; k < 5; k++) {
-    double b = block_sum(q[k], red);
-    if (threadIdx.x == 0) partials[blockIdx.x * 6 + k] = b;
+  // block totals: the count in integers, the five norms in one FP64 reduction
+  {
+    __shared__ unsigned cred[kVecThreads / 32];
+    const unsigned wc = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0) cred[threadIdx.x >> 5] = wc;
+    const double q[5] = {w2, w1, xw2, vw2, pen};
+    const double tot = block_sum_k<5>(q, red, kVecThreads / 32);
+    if (MODE == kProxThreshold && threadIdx.x < 5) partials[blockIdx.x * 6 + threadIdx.x] = tot;
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      for (int w = 0; w < kVecThreads / 32; w++) c += cred[w];
+      counts[blockIdx.x] = c;
+    }
   }
   if (!last_block(&st->counters[kCtrProx])) return;
-  // ---- last block: exclusive offsets and reductions, fixed order
+  // ---- last block: thread t takes blocks [t*per, t*per + per); all its loads are
+  // issued before any is used
   const int G = gridDim.x;
   long long* offsets = counts + G;
-  long long carry = 0;
-  for (int base = 0; base < G; base += kVecThreads) {
-    int b = base + threadIdx.x;
-    long long c = (b < G) ? ld_cg(&counts[b]) : 0;
-    long long incl = block_incl_scan(c, shl);
-    if (b < G) offsets[b] = carry + incl - c;
-    __syncthreads();
-    if (threadIdx.x == kVecThreads - 1) shl[31] = incl;
-    __syncthreads();
-    carry += shl[31];
-    __syncthreads();
+  const int per = (G + kVecThreads - 1) / kVecThreads;  // <= kScanPer (the grid is capped)
+  const int b0 = min(G, (int)threadIdx.x * per), b1 = min(G, b0 + per);
+  long long cc[kScanPer];
+  double pv[kScanPer][5];
+#pragma unroll
+  for (int e = 0; e < kScanPer; e++) {
+    const int b = b0 + e;
+    const bool ok = b < b1;
+    cc[e] = ok ? __ldcg(&counts[b]) : 0;
+#pragma unroll
+    for (int k = 0; k < 5; k++) pv[e][k] = (ok && MODE == kProxThreshold) ? ld_cg(&partials[b * 6 + k]) : 0.0;
   }
-  if (threadIdx.x == 0) {
-    offsets[G] = carry;
-    st->r = carry;
+  long long csum = 0;
+#pragma unroll
+  for (int e = 0; e < kScanPer; e++) csum += cc[e];
+  const long long incl = block_incl_scan(csum, shl);
+  long long base = incl - csum;
+#pragma unroll
+  for (int e = 0; e < kScanPer; e++)
+    if (b0 + e < b1) {
+      offsets[b0 + e] = base;
+      base += cc[e];
+    }
+  if (threadIdx.x == kVecThreads - 1) {
+    offsets[G] = incl;
+    st->r = incl;
   }
   if (MODE == kProxThreshold) {
-    for (int k = 0; k < 5; k++) {
-      double acc = 0;
-      for (int b = threadIdx.x; b < G; b += kVecThreads) acc += ld_cg(&partials[b * 6 + k]);
-      double tsum = block_sum(acc, red);
-      if (threadIdx.x == 0) {
-        if (k == 0) st->w2 = tsum;
-        if (k == 1) st->w1 = tsum;
-        if (k == 2) st->xw2 = tsum;
-        if (k == 3) st->vw2 = tsum;
-        if (k == 4) st->dualpen = tsum;
-      }
-    }
+    double q[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int e = 0; e < kScanPer; e++)
+      if (e < per)
+#pragma unroll
+        for (int k = 0; k < 5; k++) q[k] += pv[e][k];
+    const double tot = block_sum_k<5>(q, red, kVecThreads / 32);
+    if (threadIdx.x == 0) st->w2 = tot;
+    if (threadIdx.x == 1) st->w1 = tot;
+    if (threadIdx.x == 2) st->xw2 = tot;
+    if (threadIdx.x == 3) st->vw2 = tot;
+    if (threadIdx.x == 4) st->dualpen = tot;
   }
   reset_counter(&st->counters[kCtrProx]);
 }
@@ -283,7 +315,7 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ ou
                                                          const double* __restrict__ gv, DevState* st,
                                                          double* scratch) {
   pdl_entry();
-  __shared__ double red[32];
+  __shared__ double red4[4 * kVecThreads];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double o = 0.0;
   if (i < m) {
@@ -314,9 +346,9 @@ __global__ void __launch_bounds__(kVecThreads) k_combine(double* __restrict__ ou
       q[3] = bi * o;
     }
   }
-  for (int k = 0; k < 4; k++) {
-    double bsum = block_sum(q[k], red);
-    if (threadIdx.x == 0) scratch[blockIdx.x * 4 + k] = bsum;
+  {
+    const double tot = block_sum_k<4>(q, red4, kVecThreads / 32);
+    if (threadIdx.x < 4) scratch[blockIdx.x * 4 + threadIdx.x] = tot;
   }
   if (!last_block(&st->counters[kCtrCombine])) return;
   if (threadIdx.x < 4) {
@@ -345,7 +377,7 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
                                                 unsigned* tile_ctr) {
   pdl_entry();
   __shared__ double part[8][33];
-  __shared__ double red[32];
+  __shared__ double red4[4 * 32];
   __shared__ bool tile_last;
   const long long r = r_host >= 0 ? r_host : st->r;
   if (r > rcap) return;  // the gather raised the overflow flag; the host redoes this step
@@ -413,9 +445,9 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
       q[3] = bi * o;
     }
   }
-  for (int k = 0; k < 4; k++) {
-    double bsum = block_sum(q[k], red);
-    if (threadIdx.x == 0) scratch[blockIdx.x * 4 + k] = bsum;
+  {
+    const double tot = block_sum_k<4>(q, red4, 1);  // warp 0 holds the rows
+    if (threadIdx.x < 4) scratch[blockIdx.x * 4 + threadIdx.x] = tot;
   }
   // only the row tiles' last blocks get here: count them against gridDim.x
   __shared__ bool am_last;
@@ -438,6 +470,111 @@ __global__ void __launch_bounds__(256) k_gemv_n(const double* __restrict__ P, lo
   reset_counter(&stw->counters[kCtrGemv]);
 }
 
+// The same GEMV, combine and scalar products on one thread-block cluster, for
+// panels that sit in L2 (m times the panel capacity <= 2^22).  The C CTAs split the r
+// columns into C equal contiguous chunks; CTA c sums P[i, k] coef[k] over its
+// chunk for every row (one row per thread per pass, kGemvClUnroll columns of
+// loads in flight) into its shared memory.  After a cluster barrier CTA c owns
+// rows [c*mr, (c+1)*mr): it adds the C partial sums of each row in CTA order
+// (distributed shared memory), applies the combine and reduces its rows' scalar
+// products, which CTA 0 sums in CTA order after a second barrier.  One launch,
+// no global atomics; the order depends on r and C only.
+constexpr int kGemvClThreads = 512;
+constexpr int kGemvClUnroll = 16;
+constexpr int kGemvClMax = 16;                  // largest cluster the kernel is launched with
+constexpr int kGemvClMaxRows = 16384;           // rows of the partial-sum vector in shared memory
+constexpr long long kGemvClMaxEntries = 1 << 22;  // m * rcap up to which the cluster kernel is used
+
+__global__ void __launch_bounds__(kGemvClThreads) k_gemv_cl(const double* __restrict__ P, long long ldp, int m,
+                                                            const double* __restrict__ coef, const DevState* st,
+                                                            long long r_host, long long rcap,
+                                                            double* __restrict__ out, const double* __restrict__ a,
+                                                            double ca, const double* __restrict__ b, double cb,
+                                                            double cs, int which, const double* __restrict__ yv,
+                                                            const double* __restrict__ bv,
+                                                            const double* __restrict__ gv, DevState* stw) {
+  pdl_entry();
+  extern __shared__ double cl_part[];  // m partial row sums of this CTA's columns
+  __shared__ double red[4 * kGemvClThreads];
+  __shared__ double scal[kGemvClMax][4];
+  const long long r = r_host >= 0 ? r_host : st->r;
+  if (r > rcap) return;  // the same r in every CTA: none reaches a barrier
+  const int C = (int)cluster_size(), c = (int)cluster_rank();
+  const int tid = threadIdx.x;
+  const long long per = (r + C - 1) / C;
+  const long long k0 = min(r, (long long)c * per), k1 = min(r, k0 + per);
+  for (int i0 = 0; i0 < m; i0 += kGemvClThreads) {
+    const int i = i0 + tid;
+    if (i >= m) break;
+    const double* p = P + i;
+    double acc = 0.0;
+    for (long long k = k0; k < k1; k += kGemvClUnroll) {
+      double pv[kGemvClUnroll], cv[kGemvClUnroll];
+#pragma unroll
+      for (int e = 0; e < kGemvClUnroll; e++) {
+        const bool ok = k + e < k1;
+        pv[e] = ok ? p[(k + e) * ldp] : 0.0;
+        cv[e] = ok ? coef[k + e] : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < kGemvClUnroll; e++) acc = fma(pv[e], cv[e], acc);
+    }
+    cl_part[i] = acc;
+  }
+  cluster_arrive();
+  cluster_wait();
+  const int mr = (m + C - 1) / C;
+  const int r0 = min(m, c * mr), r1 = min(m, r0 + mr);
+  double q[4] = {0, 0, 0, 0};
+  for (int i = r0 + tid; i < r1; i += kGemvClThreads) {
+    const unsigned loc = smem_u32(cl_part + i);
+    double pv[kGemvClMax];
+#pragma unroll
+    for (int e = 0; e < kGemvClMax; e++) pv[e] = e < C ? ld_dsmem(cluster_addr(loc, e)) : 0.0;
+    double sum = 0.0;
+#pragma unroll
+    for (int e = 0; e < kGemvClMax; e++)
+      if (e < C) sum += pv[e];
+    double lin = 0.0;
+    if (a) lin = ca * a[i];
+    if (b) lin = a ? lin + cb * b[i] : cb * b[i];
+    const double o = (a || b) ? lin + cs * sum : cs * sum;
+    out[i] = o;
+    if (which == 1) {
+      const double yi = yv[i], bi = bv[i];
+      q[0] += o * o;
+      q[1] += yi * yi;
+      q[2] += (yi - o) * (yi - o);
+      q[3] += bi * yi;
+    } else if (which == 2) {
+      const double yi = yv[i], bi = bv[i], gi = gv[i];
+      q[0] += gi * o;
+      q[1] += yi * o;
+      q[2] += o * o;
+      q[3] += bi * o;
+    }
+  }
+  if (which != 0) {
+    // only the warps that hold rows of this CTA contribute
+    const int rows = r1 - r0;
+    int nw = (min(rows, kGemvClThreads) + 31) / 32;
+    if (nw < 1) nw = 1;
+    const double tot = block_sum_k<4>(q, red, nw);
+    if (tid < 4) st_dsmem(cluster_addr(smem_u32(&scal[c][tid]), 0), tot);
+  }
+  // every CTA is done with the others' shared memory: none may leave before
+  cluster_arrive();
+  cluster_wait();
+  if (which != 0 && c == 0 && tid < 4) {
+    double tot = 0.0;
+    for (int e = 0; e < C; e++) tot += scal[e][tid];
+    const int k = tid;
+    double* dst = which == 1 ? (k == 0 ? &stw->g2 : k == 1 ? &stw->y2 : k == 2 ? &stw->yg2 : &stw->by)
+                             : (k == 0 ? &stw->gd : k == 1 ? &stw->yd : k == 2 ? &stw->dd : &stw->bd);
+    *dst = tot;
+  }
+}
+
 // out_k = ch*h_k + cq*q_k + cd*dot(P[:, k], v), one warp per column.
 __global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, long long r, const double* __restrict__ v,
                          double* __restrict__ out, const double* __restrict__ h, double ch,
@@ -449,7 +586,18 @@ __global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, lon
   for (long long k = gw; k < r; k += tw) {
     const double* col = P + k * ldp;
     double acc = 0.0;
-    for (int i = lane; i < m; i += 32) acc = fma(col[i], v[i], acc);
+    // 16 rows per lane in flight; the padding terms add 0 * 0
+    for (int i0 = 0; i0 < m; i0 += 32 * 16) {
+      double pv[16], vv[16];
+#pragma unroll
+      for (int e = 0; e < 16; e++) {
+        const int i = i0 + lane + 32 * e;
+        pv[e] = i < m ? col[i] : 0.0;
+        vv[e] = i < m ? v[i] : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; e++) acc = fma(pv[e], vv[e], acc);
+    }
     acc = warp_sum(acc);
     if (lane == 0) {
       double o = cd * acc;
@@ -524,14 +672,79 @@ void launch_combine(double* out, const double* a, double ca, const double* b, do
   launch_k(k_combine, dim3(grid), dim3(kVecThreads), (size_t)(0), s, out, a, ca, b, cb, part, cs, m, which, y, bb, g, st, scratch);
 }
 
+// The cluster GEMV serves panels of at most kGemvClMaxEntries entries (the
+// panel capacity decides, so one context always takes the same kernel).
+static bool gemv_cluster_ok(int m, long long rcap) {
+  return m <= kGemvClMaxRows && (long long)m * rcap <= kGemvClMaxEntries;
+}
+
+// Cluster size for k_gemv_cl: 16 CTAs where the device allows a cluster that
+// large, else 8; 0 if neither can be resident.  Decided once per process.
+static int gemv_cluster_size() {
+  static int C = -1;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    C = 0;
+    if (cudaFuncSetAttribute(k_gemv_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * kGemvClMaxRows)) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    if (cudaFuncSetAttribute(k_gemv_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      cudaGetLastError();
+    for (int cand : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cand);
+      cfg.blockDim = dim3(kGemvClThreads);
+      cfg.dynamicSmemBytes = sizeof(double) * kGemvClMaxRows;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cand;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_gemv_cl, &cfg) == cudaSuccess && nclusters > 0) {
+        C = cand;
+        return;
+      }
+      cudaGetLastError();
+    }
+  });
+  return C;
+}
+
 void launch_gemv_n(const double* P, long long ldp, int m, const double* coef, const DevState* st, long long r_host,
                    long long rcap, double* out, const double* a, double ca, const double* b, double cb, double cs,
                    int which, const double* yv, const double* bv, const double* gv, DevState* stw, double* scratch,
                    double* cpart, unsigned* tile_ctr, cudaStream_t s) {
+  count_launch();
+  if (gemv_cluster_ok(m, rcap)) {
+    const int C = gemv_cluster_size();
+    if (C > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(kGemvClThreads);
+      cfg.dynamicSmemBytes = sizeof(double) * (size_t)m;
+      cfg.stream = s;
+      cudaLaunchAttribute at[2];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[1].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 2;
+      if (cudaLaunchKernelEx(&cfg, k_gemv_cl, P, ldp, m, coef, st, r_host, rcap, out, a, ca, b, cb, cs, which, yv, bv,
+                             gv, stw) == cudaSuccess)
+        return;
+      cudaGetLastError();
+    }
+  }
   // a fixed launch shape; the kernel derives its column chunks from r alone
   const long long split = kGemvMaxSplit;
-  (void)r_host;
-  count_launch();
   dim3 grid((m + 31) / 32, (unsigned)split);
   launch_k(k_gemv_n, dim3(grid), dim3(256), (size_t)(0), s, P, ldp, m, coef, st, r_host, rcap, out, a, ca, b, cb, cs, which, yv, bv, gv, stw,
                                 scratch, cpart, tile_ctr);
