@@ -359,7 +359,7 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
   PhaseTimer timer(c, kPhaseGrad);
   launch_prox_count(mode, x, c->u, c->t, c->y, c->d, c->n, (int)c->m, pp, apply_update, c->st, c->counts,
                     c->vpartials, c->grid_vec, s);
-  launch_prox_scatter(mode, x, c->u, c->n, pp, c->counts + c->grid_vec, c->J, c->wJ, c->grid_vec, s);
+  launch_prox_scatter(mode, x, c->u, c->n, pp, c->counts, c->vpartials, c->st, c->J, c->wJ, c->grid_vec, s);
   launch_gather(c->A, c->dtype, c->lda, (int)c->m, c->J, c->st, -1, c->rcap, c->P, c->ldp, c->P32, c->ldp32, c->sms,
                 s, c->col_mean, c->col_scale);
   launch_grad(c, mode, b, -1);
@@ -981,7 +981,7 @@ ssnal_en_status ssnal_en_op_prox_active(ssnal_en_ctx* c, const double* x, const 
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   launch_prox_count(kProxThreshold, x, const_cast<double*>(u), nullptr, nullptr, nullptr, c->n, (int)c->m, pp, 0,
                     c->st, c->counts, c->vpartials, c->grid_vec, s);
-  launch_prox_scatter(kProxThreshold, x, u, c->n, pp, c->counts + c->grid_vec, J, wJ, c->grid_vec, s);
+  launch_prox_scatter(kProxThreshold, x, u, c->n, pp, c->counts, c->vpartials, c->st, J, wJ, c->grid_vec, s);
   CK(cudaGetLastError());
   ssnal_en_status e = read_state(c);
   if (e != SSNAL_EN_OK) return e;

@@ -83,7 +83,8 @@ void launch_prox_count(int mode, const double* x, double* u, const double* t, do
                        long long n, int m, ProxParams pp, int apply_update, DevState* st,
                        long long* counts, double* partials, int grid, cudaStream_t s);
 void launch_prox_scatter(int mode, const double* x, const double* u, long long n, ProxParams pp,
-                         const long long* offsets, int32_t* J, double* wJ, int grid, cudaStream_t s);
+                         const long long* counts, const double* partials, DevState* st, int32_t* J, double* wJ,
+                         int grid, cudaStream_t s);
 void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sms, cudaStream_t s);
 void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t* J, const DevState* st,
                    long long r_host, long long rcap, double* P, long long ldp, float* P32, long long ldp32,

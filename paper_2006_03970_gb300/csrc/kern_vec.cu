@@ -15,17 +15,15 @@ namespace ssnal {
 std::atomic<long long> g_launches{0};
 
 constexpr int kVecThreads = 256;
-// Blocks per thread in the last block's scan of the per-block counts (the O(n)
-// passes run at most kScanPer * kVecThreads blocks).
-constexpr int kScanPer = 4;
+constexpr int kVecMaxBlocks = 1024;  // every block of pass 2 reads all per-block counts
 
-// Blocks for the O(n) passes: at most two per SM and at least 256 entries per
-// block, so that the FP64 work (a few dozen FP64 operations per entry, at the
-// GPU's low FP64 rate) is spread evenly over the SMs.
+// Blocks for the O(n) passes: at most two per SM (and kVecMaxBlocks) and at least
+// 256 entries per block, so that the FP64 work (a few FP64 operations per entry,
+// at the GPU's low FP64 rate) is spread evenly over the SMs.
 int vec_grid(long long n, int sms) {
   long long g = (n + 255) / 256;
   long long cap = 2LL * sms;
-  if (cap > (long long)kScanPer * kVecThreads) cap = (long long)kScanPer * kVecThreads;
+  if (cap > kVecMaxBlocks) cap = kVecMaxBlocks;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
@@ -67,11 +65,9 @@ __device__ __forceinline__ void block_range(long long n, long long& start, long 
 
 // Pass 1 of the prox / active-set step.  Optionally applies the accepted
 // line-search step first (u += s t, y += s d).  Per block: number of active
-// entries and partial norms (one six-value block reduction); the last block
-// loads every block's results at once, scans the counts into offsets and
-// reduces the norms into the state, all in a fixed order.
-// counts: [0, grid) per-block counts, [grid, 2*grid] exclusive offsets.
-// partials: grid x 6 doubles.
+// entries (integer reduction) and five partial norms (one FP64 reduction),
+// written to counts[b] and partials[6 b ..].  No tail: the next kernel (pass 2)
+// reads them once this grid has completed.
 template <int MODE>
 __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __restrict__ x, double* __restrict__ u,
                                                             const double* __restrict__ t, double* __restrict__ y,
@@ -80,7 +76,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
                                                             long long* counts, double* partials) {
   pdl_entry();
   __shared__ double red[5 * kVecThreads];
-  __shared__ long long shl[32];
+  __shared__ unsigned cred[kVecThreads / 32];
   long long start, stop;
   block_range(n, start, stop);
   const double s = apply_update ? st->s : 0.0;
@@ -121,82 +117,78 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
       pen += e * e;
     }
   }
-  // block totals: the count in integers, the five norms in one FP64 reduction
-  {
-    __shared__ unsigned cred[kVecThreads / 32];
-    const unsigned wc = __reduce_add_sync(0xffffffffu, cnt);
-    if ((threadIdx.x & 31) == 0) cred[threadIdx.x >> 5] = wc;
-    const double q[5] = {w2, w1, xw2, vw2, pen};
-    const double tot = block_sum_k<5>(q, red, kVecThreads / 32);
-    if (MODE == kProxThreshold && threadIdx.x < 5) partials[blockIdx.x * 6 + threadIdx.x] = tot;
-    if (threadIdx.x == 0) {
-      long long c = 0;
-      for (int w = 0; w < kVecThreads / 32; w++) c += cred[w];
-      counts[blockIdx.x] = c;
-    }
-  }
-  if (!last_block(&st->counters[kCtrProx])) return;
-  // ---- last block: thread t takes blocks [t*per, t*per + per); all its loads are
-  // issued before any is used
-  const int G = gridDim.x;
-  long long* offsets = counts + G;
-  const int per = (G + kVecThreads - 1) / kVecThreads;  // <= kScanPer (the grid is capped)
-  const int b0 = min(G, (int)threadIdx.x * per), b1 = min(G, b0 + per);
-  long long cc[kScanPer];
-  double pv[kScanPer][5];
-#pragma unroll
-  for (int e = 0; e < kScanPer; e++) {
-    const int b = b0 + e;
-    const bool ok = b < b1;
-    cc[e] = ok ? __ldcg(&counts[b]) : 0;
-#pragma unroll
-    for (int k = 0; k < 5; k++) pv[e][k] = (ok && MODE == kProxThreshold) ? ld_cg(&partials[b * 6 + k]) : 0.0;
-  }
-  long long csum = 0;
-#pragma unroll
-  for (int e = 0; e < kScanPer; e++) csum += cc[e];
-  const long long incl = block_incl_scan(csum, shl);
-  long long base = incl - csum;
-#pragma unroll
-  for (int e = 0; e < kScanPer; e++)
-    if (b0 + e < b1) {
-      offsets[b0 + e] = base;
-      base += cc[e];
-    }
-  if (threadIdx.x == kVecThreads - 1) {
-    offsets[G] = incl;
-    st->r = incl;
-  }
+  const unsigned wc = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) cred[threadIdx.x >> 5] = wc;
   if (MODE == kProxThreshold) {
-    double q[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-    for (int e = 0; e < kScanPer; e++)
-      if (e < per)
-#pragma unroll
-        for (int k = 0; k < 5; k++) q[k] += pv[e][k];
-    const double tot = block_sum_k<5>(q, red, kVecThreads / 32);
-    if (threadIdx.x == 0) st->w2 = tot;
-    if (threadIdx.x == 1) st->w1 = tot;
-    if (threadIdx.x == 2) st->xw2 = tot;
-    if (threadIdx.x == 3) st->vw2 = tot;
-    if (threadIdx.x == 4) st->dualpen = tot;
+    const double q[5] = {w2, w1, xw2, vw2, pen};
+    const double tot = block_sum_k<5>(q, red, kVecThreads / 32);  // its barriers also publish cred
+    if (threadIdx.x < 5) partials[blockIdx.x * 6 + threadIdx.x] = tot;
+  } else {
+    __syncthreads();
   }
-  reset_counter(&st->counters[kCtrProx]);
+  if (threadIdx.x == 0) {
+    long long c = 0;
+    for (int w = 0; w < kVecThreads / 32; w++) c += cred[w];
+    counts[blockIdx.x] = c;
+  }
 }
 
-// Pass 2: ordered compaction.  Block b writes its active indices, ascending,
-// starting at offsets[b]; w_J holds the prox values (eq. prox_elastic).
+// Sum of a long long over the block (blockDim == kVecThreads); every thread
+// gets the total.
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  long long tot = 0;
+#pragma unroll
+  for (int w = 0; w < kVecThreads / 32; w++) tot += sh[w];
+  return tot;
+}
+
+// Pass 2: ordered compaction.  Block b first forms its offset, the sum of the
+// counts of blocks 0..b-1 written by pass 1 (block 0 also writes r and reduces
+// the norms into the state, in a fixed order); then it writes its active
+// indices, ascending, from that offset; w_J holds the prox values (eq.
+// prox_elastic).
 template <int MODE>
 __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __restrict__ x,
                                                               const double* __restrict__ u, long long n,
-                                                              ProxParams pp, const long long* __restrict__ offsets,
+                                                              ProxParams pp, const long long* __restrict__ counts,
+                                                              const double* __restrict__ partials, DevState* st,
                                                               int32_t* __restrict__ J, double* __restrict__ wJ) {
   pdl_entry();
   __shared__ long long shl[32];
   __shared__ long long tile_total;
+  __shared__ double red[5 * kVecThreads];
+  const int G = gridDim.x, b = blockIdx.x;
+  long long before = 0, all_cnt = 0;
+  for (int c = threadIdx.x; c < G; c += kVecThreads) {
+    const long long v = __ldcg(&counts[c]);
+    all_cnt += v;
+    if (c < b) before += v;
+  }
+  before = block_sum_ll(before, shl);
+  all_cnt = block_sum_ll(all_cnt, shl);
+  if (b == 0) {
+    if (threadIdx.x == 0) st->r = all_cnt;
+    if (MODE == kProxThreshold) {
+      double q[5] = {0, 0, 0, 0, 0};
+      for (int c = threadIdx.x; c < G; c += kVecThreads)
+#pragma unroll
+        for (int k = 0; k < 5; k++) q[k] += ld_cg(&partials[c * 6 + k]);
+      const double tot = block_sum_k<5>(q, red, kVecThreads / 32);
+      if (threadIdx.x == 0) st->w2 = tot;
+      if (threadIdx.x == 1) st->w1 = tot;
+      if (threadIdx.x == 2) st->xw2 = tot;
+      if (threadIdx.x == 3) st->vw2 = tot;
+      if (threadIdx.x == 4) st->dualpen = tot;
+    }
+  }
   long long start, stop;
   block_range(n, start, stop);
-  long long pos = offsets[blockIdx.x];
+  long long pos = before;
   for (long long base = start; base < stop; base += blockDim.x) {
     long long j = base + threadIdx.x;
     double w = 0.0;
@@ -621,12 +613,15 @@ void launch_prox_count(int mode, const double* x, double* u, const double* t, do
 }
 
 void launch_prox_scatter(int mode, const double* x, const double* u, long long n, ProxParams pp,
-                         const long long* offsets, int32_t* J, double* wJ, int grid, cudaStream_t s) {
+                         const long long* counts, const double* partials, DevState* st, int32_t* J, double* wJ,
+                         int grid, cudaStream_t s) {
   count_launch();
   if (mode == kProxSupport)
-    launch_k(k_prox_scatter<kProxSupport>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp, offsets, J, wJ);
+    launch_k(k_prox_scatter<kProxSupport>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp, counts,
+             partials, st, J, wJ);
   else
-    launch_k(k_prox_scatter<kProxThreshold>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp, offsets, J, wJ);
+    launch_k(k_prox_scatter<kProxThreshold>, dim3(grid), dim3(kVecThreads), (size_t)(0), s, x, u, n, pp, counts,
+             partials, st, J, wJ);
 }
 
 void launch_set_x(double* x, const double* u, long long n, ProxParams pp, int sms, cudaStream_t s) {

@@ -28,8 +28,8 @@ constexpr int kStaticMaxBlocks = 1024;     // blocks covered by the scratch arra
 static_assert(kStaticChunk * kStaticMaxBlocks == SSNAL_EN_STATIC_MAX_N, "limit in the header");
 
 struct StaticScratch {
-  DevState st;                                // r, the norms and the last-block counter
-  long long counts[2 * kStaticMaxBlocks + 2];  // per-block counts, then exclusive offsets
+  DevState st;                                // r and the norms
+  long long counts[2 * kStaticMaxBlocks + 2];  // per-block counts
   double partials[6 * kStaticMaxBlocks];      // per-block partial norms
 };
 
@@ -74,7 +74,7 @@ extern "C" ssnal_en_status ssnal_en_prox_active_static(const double* x, const do
   ssnal_en_status e = scratch_on_current_device(&sc);
   if (e != SSNAL_EN_OK) return e;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // r and the last-block counter must start at zero; the rest is written before it is read.
+  // the state starts at zero; counts and partials are written before they are read.
   if (cudaMemsetAsync(&sc->st, 0, sizeof(DevState), s) != cudaSuccess) return SSNAL_EN_ECUDA;
   const int grid = (int)((n + kStaticChunk - 1) / kStaticChunk);
   ProxParams pp;
@@ -86,7 +86,7 @@ extern "C" ssnal_en_status ssnal_en_prox_active_static(const double* x, const do
   pp.inv_onep = 1.0 / pp.onep;
   launch_prox_count(kProxThreshold, x, const_cast<double*>(u), nullptr, nullptr, nullptr, n, 0, pp, 0, &sc->st,
                     sc->counts, sc->partials, grid, s);
-  launch_prox_scatter(kProxThreshold, x, u, n, pp, sc->counts + grid, J, wJ, grid, s);
+  launch_prox_scatter(kProxThreshold, x, u, n, pp, sc->counts, sc->partials, &sc->st, J, wJ, grid, s);
   if (cudaGetLastError() != cudaSuccess) return SSNAL_EN_ECUDA;
   long long rv = 0;
   if (cudaMemcpyAsync(&rv, &sc->st.r, sizeof(rv), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SSNAL_EN_ECUDA;
