@@ -239,6 +239,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   }
   return false;
 }
+// 2-D tensor copy (TMA) of one box at (x, y) into shared memory, completing on
+// the mbarrier `bar` of this CTA.
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const void* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 // ---- thread-block clusters: rank, size, distributed shared memory, barrier
 __device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank) {
   unsigned r;

@@ -127,6 +127,8 @@ bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, doubl
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
                              double alpha, cudaStream_t s);
 // acc = (first ? alpha c : acc + alpha c) with (L L^T) c = rhs
+// Tensor map over an FP32 factor for the 2-CTA triangular solves (kern_stream.cu).
+bool make_factor_tensor_map(void* map_out, const float* L, long long ld, int N);
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s);
 

@@ -5,6 +5,7 @@
 //   * forward/backward substitution with the factor, accumulating the
 //     correction into an FP64 vector (the solve of an iterative refinement).
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -1278,6 +1279,170 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 }
 
 // ---------------------------------------------------------------------------
+// The same solves for N <= 32 kTrsvPairMaxT on a cluster of kTrsvQ CTAs with
+// the row blocks split into contiguous parts of T0 = ceil(T / kTrsvQ) blocks, so
+// that all but kTrsvQ - 1 links of each pass stay inside a CTA; every tile of L
+// passes from L2 to one SM per pass, so the parts also spread that traffic (about
+// 64 GB/s per SM), which bounds a link inside a CTA.  Warp w of CTA c owns
+// block J = c T0 + w, lane l row (forward) or column (backward) 32J + l.  Each warp streams the T-1 tiles of L it needs (forward: L[J, I],
+// I < J; backward: L[I, J], I > J, in the order they are consumed) through its
+// own ring of kTrsvRing shared-memory tiles, one 2-D TMA copy per tile (128-byte
+// swizzle: the 16-byte chunk index is XORed with the tile column mod 8, so both
+// the row reads of the forward pass and the column reads of the backward pass
+// are free of bank conflicts).  z_J and c_J reach the owner's warps through
+// shared memory and a local mbarrier arrival, the other CTAs through st.async
+// completing on their per-block mbarriers.  Every wait is bounded
+// (DevState::timeout).
+constexpr int kTrsvPairMaxT = 20;
+constexpr int kTrsvQ = 4;     // CTAs per cluster
+constexpr int kTrsvRing = 6;  // tiles in flight per warp
+constexpr int kTrsvMaxT0 = (kTrsvPairMaxT + kTrsvQ - 1) / kTrsvQ;
+
+__global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0)
+    k_trsv_pair(const __grid_constant__ CUtensorMap tmL, int N, const double* __restrict__ rhs,
+                double* __restrict__ acc, int first, double alpha, const float* __restrict__ Wd, DevState* st) {
+  pdl_entry();
+  cgx::cluster_group cluster = cgx::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ __align__(1024) float tpr[];
+  const int T = (N + 31) / 32, T0 = (T + kTrsvQ - 1) / kTrsvQ;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  // 1 KB alignment for the swizzled tiles
+  float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tpr) + 1023) & ~(uintptr_t)1023);
+  float* ring = base + warp * kTrsvRing * 1024;    // this warp's tile ring
+  float* zbuf = base + nwarp * kTrsvRing * 1024;   // T x 32: z_I
+  float* cbuf = zbuf + T * 32;                     // T x 32: c_I
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(cbuf + T * 32);  // 2T: forward, backward
+  unsigned long long* rbars = bars + 2 * T + warp * kTrsvRing;                      // this warp's ring slots
+  float* rscr = reinterpret_cast<float*>(bars + 2 * T + nwarp * kTrsvRing);            // nwarp x 32 scratch
+  // block J belongs to CTA J / T0; its values reach the owner's own barrier by
+  // one local arrival after plain stores, the other CTAs' by 128 bytes of st.async
+  for (int k = tid; k < 2 * T; k += blockDim.x) {
+    mbar_init(smem_u32(bars + k), 1);
+    if ((k % T) / T0 != rank) mbar_expect_tx(smem_u32(bars + k), 128);
+  }
+  if (lane < kTrsvRing) mbar_init(smem_u32(rbars + lane), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  cluster.sync();
+  const int J = rank * T0 + warp;  // this warp's row block
+  bool ok = true;
+  if (J < T) {
+    const int row = 32 * J + lane;
+    const bool live = row < N;
+    float r = live ? (float)rhs[row] : 0.0f;
+    const float* Wb = Wd + (long long)J * 1024;
+    // tile t of this warp: forward L[J, t] for t < J, then backward L[I, J], I = T-1 .. J+1
+    auto issue = [&](int t) {
+      if (lane == 0) {
+        const int slot = t % kTrsvRing;
+        const unsigned bar = smem_u32(rbars + slot);
+        mbar_expect_tx(bar, 4096);
+        if (t < J)
+          tma_load_2d(smem_u32(ring + slot * 1024), &tmL, 32 * J, 32 * t, bar);
+        else
+          tma_load_2d(smem_u32(ring + slot * 1024), &tmL, 32 * (T - 1 - (t - J)), 32 * J, bar);
+      }
+    };
+    const int ntile = T - 1;
+    for (int t = 0; t < kTrsvRing && t < ntile; t++) issue(t);
+    // W_JJ row l (forward) in registers
+    float w[32];
+#pragma unroll
+    for (int g = 0; g < 8; g++) {
+      const float4 v = reinterpret_cast<const float4*>(Wb + lane * 32)[g];
+      w[4 * g] = v.x; w[4 * g + 1] = v.y; w[4 * g + 2] = v.z; w[4 * g + 3] = v.w;
+    }
+    auto publish = [&](float* buf, unsigned long long* bar) {
+      const unsigned dst = smem_u32(buf + J * 32 + lane), b = smem_u32(bar);
+      buf[J * 32 + lane] = r;  // this CTA first: its consumers are the next link
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b);  // release: the warp's stores before the arrival
+#pragma unroll
+      for (int c = 1; c < kTrsvQ; c++) {
+        const int d = (rank + c) % kTrsvQ;  // the next CTA first: the chain continues there
+        st_async_f32(cluster_addr(dst, d), r, cluster_addr(b, d));
+      }
+    };
+    // r through shared memory (one 128-bit broadcast load per four entries)
+    float* rb = rscr + warp * 32;
+    auto wr_product = [&]() {  // sum_q w[q] r_q, even q then odd q
+      rb[lane] = r;
+      __syncwarp();
+      const float4* r4 = reinterpret_cast<const float4*>(rb);
+      float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+      for (int g = 0; g < 8; g++) {
+        const float4 v = r4[g];
+        z0 = fmaf(w[4 * g], v.x, z0);
+        z1 = fmaf(w[4 * g + 1], v.y, z1);
+        z0 = fmaf(w[4 * g + 2], v.z, z0);
+        z1 = fmaf(w[4 * g + 3], v.w, z1);
+      }
+      __syncwarp();  // every lane has read rb before it is written again
+      return z0 + z1;
+    };
+    auto form_z = [&]() {  // z_J = W_JJ r_J: lane l takes row l of W
+      r = wr_product();
+      publish(zbuf, bars + J);
+#pragma unroll
+      for (int q = 0; q < 32; q++) w[q] = Wb[q * 32 + lane];  // column l of W for the backward pass
+    };
+    if (J == 0) form_z();
+    const int sw = lane >> 2, se = lane & 3;  // forward: chunk and element of row `lane` in a tile column
+    for (int t = 0; t < ntile; t++) {
+      const int slot = t % kTrsvRing;
+      // always waited (bounded), so that no copy is in flight when the CTA leaves
+      if (!mbar_wait(smem_u32(rbars + slot), (unsigned)((t / kTrsvRing) & 1))) ok = false;
+      const float* tile = ring + slot * 1024;
+      float s0 = 0.0f, s1 = 0.0f;
+      if (t < J) {
+        if (ok && !mbar_wait(smem_u32(bars + t), 0u)) ok = false;
+        const float4* z4 = reinterpret_cast<const float4*>(zbuf + t * 32);
+#pragma unroll
+        for (int g = 0; g < 8; g++) {
+          const float4 z = z4[g];
+          // element (row lane, column q) of the tile: column q is the q-th 128-byte row
+          s0 = fmaf(tile[(4 * g) * 32 + ((sw ^ ((4 * g) & 7)) << 2) + se], z.x, s0);
+          s1 = fmaf(tile[(4 * g + 1) * 32 + ((sw ^ ((4 * g + 1) & 7)) << 2) + se], z.y, s1);
+          s0 = fmaf(tile[(4 * g + 2) * 32 + ((sw ^ ((4 * g + 2) & 7)) << 2) + se], z.z, s0);
+          s1 = fmaf(tile[(4 * g + 3) * 32 + ((sw ^ ((4 * g + 3) & 7)) << 2) + se], z.w, s1);
+        }
+        r -= s0 + s1;
+        if (t == J - 1) form_z();
+      } else {
+        const int I = T - 1 - (t - J);
+        if (ok && !mbar_wait(smem_u32(bars + T + I), 0u)) ok = false;
+        const float4* c4 = reinterpret_cast<const float4*>(cbuf + I * 32);
+#pragma unroll
+        for (int g = 0; g < 8; g++) {
+          // column `lane` of the tile is its lane-th 128-byte row; rows 4g .. 4g+3 are chunk g
+          const float4 v = *reinterpret_cast<const float4*>(tile + lane * 32 + ((g ^ (lane & 7)) << 2));
+          const float4 cv = c4[g];
+          s0 = fmaf(v.x, cv.x, s0);
+          s1 = fmaf(v.y, cv.y, s1);
+          s0 = fmaf(v.z, cv.z, s0);
+          s1 = fmaf(v.w, cv.w, s1);
+        }
+        r -= s0 + s1;
+      }
+      __syncwarp();  // every lane has read the slot (the reads fed r) before it is refilled
+      if (t + kTrsvRing < ntile) issue(t + kTrsvRing);
+    }
+    r = wr_product();  // c_J = W_JJ^T r_J: lane l takes column l of W
+    if (live) acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
+    publish(cbuf, bars + T + J);
+  }
+  // every value sent to this CTA has landed before it exits (the ring copies of a
+  // warp were all waited for: each issued tile is consumed)
+  for (int k = tid; k < 2 * T; k += blockDim.x)
+    if (ok && !mbar_wait(smem_u32(bars + k), 0u)) ok = false;
+  if (!ok) st->timeout = 1;
+  __syncthreads();
+  cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
 // Newton systems above kClusterN: right-looking Cholesky over super-blocks of at
 // most kClusterN rows.  Each diagonal super-block is factored by k_chol_cluster
 // (which also leaves its inverse 32x32 diagonal blocks), the rows below it are
@@ -1726,6 +1891,25 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
     count_launch();
     launch_k(k_trsv_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, L, ldl, N, rhs, acc, first, alpha);
     return;
+  }
+  CUtensorMap tmL;
+  if (Wdiag && N <= 32 * kTrsvPairMaxT && make_factor_tensor_map(&tmL, L, ldl, N)) {
+    const int T = (N + 31) / 32, T0 = (T + kTrsvQ - 1) / kTrsvQ;
+    const size_t smem = 1024 + (size_t)T0 * kTrsvRing * 4096 + (size_t)2 * T * 32 * sizeof(float) +
+                        (size_t)(2 * T + T0 * kTrsvRing) * 8 + (size_t)T0 * 32 * sizeof(float);
+    static bool done_pr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !done_pr[dev]) {
+      const int T0m = kTrsvMaxT0;
+      cudaFuncSetAttribute(k_trsv_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(1024 + (size_t)T0m * kTrsvRing * 4096 + (size_t)2 * kTrsvPairMaxT * 32 * sizeof(float) +
+                                 (size_t)(2 * kTrsvPairMaxT + T0m * kTrsvRing) * 8 + (size_t)T0m * 32 * sizeof(float)));
+      if (dev >= 0 && dev < 64) done_pr[dev] = true;
+    }
+    count_launch();
+    launch_k(k_trsv_pair, dim3(kTrsvQ), dim3(32 * T0), smem, s, tmL, N, rhs, acc, first, alpha, Wdiag, st);
+    if (cudaGetLastError() == cudaSuccess) return;
   }
   if (Wdiag && N <= 32 * kTrsvCLMaxT) {
     const int T = (N + 31) / 32;

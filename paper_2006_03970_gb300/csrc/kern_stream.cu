@@ -721,13 +721,6 @@ struct LaneCfg {
   long long groups;  // column groups of 32
 };
 
-__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
 
 template <int MODE, int ELT>
 __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_constant__ CUtensorMap tmap, int m, long long n,
@@ -1054,6 +1047,34 @@ bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda,
                          : bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                       const_cast<void*>(A), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Tensor map over a Cholesky factor L (FP32, column-major, ld floats per
+// column, ld * 4 a multiple of 16 bytes): N x N, 32 x 32 boxes with the 128-byte
+// swizzle (16-byte chunk index XOR row index mod 8 within each 1 KB), zero fill
+// past N.
+bool make_factor_tensor_map(void* map_out, const float* L, long long ld, int N) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  if ((ld * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(L) & 15) != 0 || N <= 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)N};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                      const_cast<float*>(L), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
