@@ -42,7 +42,9 @@ struct ssnal_en_ctx {
   int stream_kind = 0;  // kStreamFloatFloat or kStreamDfma (FP64 storage)
   // device workspaces
   DevState* st = nullptr;
-  DevState* st_host = nullptr;  // pinned mirror
+  DevState* st_host = nullptr;  // pinned mirror (device-mapped)
+  unsigned* st_flag = nullptr;  // pinned: sequence number written after the mirror
+  unsigned st_seq = 0;
   double *u = nullptr, *t = nullptr, *xpath = nullptr;
   double *y = nullptr, *d = nullptr, *g = nullptr, *bdev = nullptr, *res = nullptr, *tmpm = nullptr;
   double* bstage = nullptr;  // b of ssnal_en_path_host
@@ -165,6 +167,7 @@ void free_all(ssnal_en_ctx* c) {
   c->ev_pending.clear();
   dev_free(c->st);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->st_flag) cudaFreeHost(c->st_flag);
   dev_free(c->u);
   dev_free(c->t);
   dev_free(c->xpath);
@@ -285,10 +288,39 @@ struct PhaseTimer {
   }
 };
 
+// The state after the work queued so far.  A kernel behind that work writes the
+// state into the host mirror and then a sequence number, which this thread
+// polls: no copy-engine transfer and no blocking wake-up on the common path.
+// The poll checks the stream for errors now and then and, after about 50 us,
+// falls back to a blocking synchronisation.  With profiling on, the stream is
+// synchronised so that the recorded events have completed.
 ssnal_en_status read_state(ssnal_en_ctx* c) {
-  CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (!c->ev_pending.empty()) prof_harvest(c);
+  if (c->prof || !c->st_flag) {
+    CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!c->ev_pending.empty()) prof_harvest(c);
+    return SSNAL_EN_OK;
+  }
+  const unsigned want = ++c->st_seq;
+  launch_state_out(c->st, c->st_host, c->st_flag, want, c->stream);
+  CK(cudaGetLastError());
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned it = 1;; it++) {
+    if (__atomic_load_n(c->st_flag, __ATOMIC_ACQUIRE) == want) break;
+    if ((it & 1023) == 0) {
+      const cudaError_t e = cudaStreamQuery(c->stream);
+      if (e == cudaSuccess) {  // the stream has drained: the flag must be there
+        if (__atomic_load_n(c->st_flag, __ATOMIC_ACQUIRE) != want) return SSNAL_EN_ECUDA;
+        break;
+      }
+      if (e != cudaErrorNotReady) return SSNAL_EN_ECUDA;
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(50)) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (__atomic_load_n(c->st_flag, __ATOMIC_ACQUIRE) != want) return SSNAL_EN_ECUDA;
+        break;
+      }
+    }
+  }
   return SSNAL_EN_OK;
 }
 
@@ -680,6 +712,8 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->tc_part, syrk_tc_part_floats(c->sms));
 #undef AL
   if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) s = SSNAL_EN_ENOMEM;
+  if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_flag, 64) != cudaSuccess) s = SSNAL_EN_ENOMEM;
+  if (s == SSNAL_EN_OK) *c->st_flag = 0;
   if (s == SSNAL_EN_OK) s = grow_panel(c, m < n ? m : n);
   if (s == SSNAL_EN_OK && cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream) != cudaSuccess) s = SSNAL_EN_ECUDA;
   if (s == SSNAL_EN_OK &&

@@ -79,6 +79,9 @@ struct ProxParams {
 
 // ---- launch wrappers (kern_vec.cu)
 int vec_grid(long long n, int sms);
+// Copies *st to the pinned, device-mapped host mirror and then writes seq to flag
+// (host memory), after a system-scope fence.
+void launch_state_out(const DevState* st, DevState* host, unsigned* flag, unsigned seq, cudaStream_t s);
 void launch_prox_count(int mode, const double* x, double* u, const double* t, double* y, const double* d,
                        long long n, int m, ProxParams pp, int apply_update, DevState* st,
                        long long* counts, double* partials, int grid, cudaStream_t s);

@@ -600,7 +600,28 @@ __global__ void k_gemv_t(const double* __restrict__ P, long long ldp, int m, lon
   }
 }
 
+// Copies the solver state to its pinned host mirror (device-mapped) and then,
+// after a system-scope fence, writes `seq` to the host flag, which the host polls.
+// It waits (programmatic dependent launch) for every kernel before it.
+__global__ void k_state_out(const unsigned long long* __restrict__ st, unsigned long long* host, int words,
+                            unsigned* flag, unsigned seq) {
+  pdl_entry();
+  for (int i = threadIdx.x; i < words; i += blockDim.x) host[i] = st[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    *reinterpret_cast<volatile unsigned*>(flag) = seq;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
+void launch_state_out(const DevState* st, DevState* host, unsigned* flag, unsigned seq, cudaStream_t s) {
+  static_assert(sizeof(DevState) % 8 == 0, "DevState is copied in 8-byte words");
+  count_launch();
+  launch_k(k_state_out, dim3(1), dim3(64), (size_t)0, s, reinterpret_cast<const unsigned long long*>(st),
+           reinterpret_cast<unsigned long long*>(host), (int)(sizeof(DevState) / 8), flag, seq);
+}
+
 void launch_prox_count(int mode, const double* x, double* u, const double* t, double* y, const double* d,
                        long long n, int m, ProxParams pp, int apply_update, DevState* st, long long* counts,
                        double* partials, int grid, cudaStream_t s) {
