@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-STREAM_TRAFFIC_BYTES = 401698304 + 4062464  # ncu, one k_stream_lane<kModeT> launch, m=500 n=1e5
+STREAM_TRAFFIC_BYTES = 401668352 + 3752704  # ncu, one k_stream_lane<kModeT> launch, m=500 n=1e5
 METRIC = "EN fits/s to KKT<=1e-6"
 UNIT = "fits/s"
 WORKLOAD = ("FP64 warm-started Elastic Net path: m=500, n=100000, 100-feature AR(1) blocks rho=0.7, "

@@ -175,7 +175,9 @@ ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* ctx, const double* b_host, doub
  * the context's stream around every launch of the A^T d stream (the one pass
  * over A of each Newton step, eq. line_search fused in) and their elapsed
  * times are summed at the next synchronisation.
- *  enable  1: record from now on, 0: stop recording.
+ *  enable  1: record from now on, 2: also record the phases of
+ *          ssnal_en_profile_phases (more events on the host's path between
+ *          kernels), 0: stop recording.
  *  reset   1: zero the sums before reporting.
  *  stream_ms        summed device time of those launches (host, may be NULL)
  *  stream_launches  number of those launches (host, may be NULL)
@@ -187,7 +189,8 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t rese
                                  int64_t* stream_launches, double* stream_bytes, int64_t* kernel_launches);
 
 /* Per-phase device time since the last ssnal_en_profile(reset = 1), recorded
- * while profiling is enabled.  Four phases, in this order:
+ * while profiling is enabled at level 2 (level 1 records phase 2 only).  Four
+ * phases, in this order:
  *  0 prox + active set + gather + gradient (eqs. prox_elastic, Q_def, grad_phy)
  *  1 Newton direction: SYRK, Cholesky, solves and refinement (eqs. AJ_system, smw_formula)
  *  2 the pass over A with the fused line search (eq. line_search)

@@ -412,10 +412,12 @@ def ssnal_en_profile_phases(ctx):
     return {PHASES[k]: (ms[k], n[k]) for k in range(4)}
 
 
-def ssnal_en_profile(ctx, enable: bool, reset: bool = False):
-    """Returns dict(stream_ms, stream_launches, stream_bytes, kernel_launches)."""
+def ssnal_en_profile(ctx, enable, reset: bool = False, phases: bool = False):
+    """Returns dict(stream_ms, stream_launches, stream_bytes, kernel_launches).
+    ``phases`` also records the phases of ssnal_en_profile_phases (level 2)."""
     ms, nl, by, kl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
-    _check(load_library().ssnal_en_profile(ctx, int(bool(enable)), int(bool(reset)), ctypes.byref(ms),
+    level = (2 if phases else 1) if enable else 0
+    _check(load_library().ssnal_en_profile(ctx, level, int(bool(reset)), ctypes.byref(ms),
                                            ctypes.byref(nl), ctypes.byref(by), ctypes.byref(kl)),
            "ssnal_en_profile")
     return {"stream_ms": ms.value, "stream_launches": nl.value, "stream_bytes": by.value,

@@ -268,7 +268,11 @@ struct PhaseTimer {
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   int phase;
   PhaseTimer(ssnal_en_ctx* c_, int ph) : c(c_), phase(ph) {
-    if (!c->prof) return;
+    // level 1 times the passes over A only (few events on the host's path)
+    if (!c->prof || (ph != kPhaseStream && c->prof < 2)) {
+      c = nullptr;
+      return;
+    }
     if (c->ev_pool.empty()) {
       if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
         c = nullptr;
@@ -292,10 +296,10 @@ struct PhaseTimer {
 // state into the host mirror and then a sequence number, which this thread
 // polls: no copy-engine transfer and no blocking wake-up on the common path.
 // The poll checks the stream for errors now and then and, after about 50 us,
-// falls back to a blocking synchronisation.  With profiling on, the stream is
-// synchronised so that the recorded events have completed.
+// falls back to a blocking synchronisation.  Recorded profiling events are
+// waited for before they are read.
 ssnal_en_status read_state(ssnal_en_ctx* c) {
-  if (c->prof || !c->st_flag) {
+  if (!c->st_flag) {
     CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (!c->ev_pending.empty()) prof_harvest(c);
@@ -320,6 +324,10 @@ ssnal_en_status read_state(ssnal_en_ctx* c) {
         break;
       }
     }
+  }
+  if (!c->ev_pending.empty()) {
+    CK(cudaEventSynchronize(c->ev_pending.back().second));
+    prof_harvest(c);
   }
   return SSNAL_EN_OK;
 }
@@ -964,7 +972,7 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* c, int32_t enable, int32_t reset,
       c->phase_n[k] = 0;
     }
   }
-  c->prof = enable ? 1 : 0;
+  c->prof = enable < 0 ? 0 : enable > 2 ? 2 : enable;
   if (stream_ms) *stream_ms = c->prof_ms;
   if (stream_launches) *stream_launches = c->prof_launches;
   if (stream_bytes) *stream_bytes = c->prof_bytes;
