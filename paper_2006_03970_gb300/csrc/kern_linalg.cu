@@ -8,6 +8,8 @@
 #include <cuda.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ssnal {
@@ -566,23 +568,37 @@ constexpr int kCholThreads = 384;
 constexpr int kCholTrail = 6;  // trailing warps
 constexpr int kClusterN = 640;
 constexpr int kClusterT = kClusterN / 32;                 // 20 tiles per side
-constexpr int kClusterDoubleT = 16;                       // double-buffered panel up to this many tile rows
+constexpr int kCluster16CTAs = 16;                        // the wide variant: one 16-CTA cluster (where allowed)
+constexpr int kCluster16N = 864;                          // its limit: 27 tiles per side
+constexpr int kClusterTMax = kCluster16N / 32;
+constexpr size_t kClusterSmemLimit = 232448 - 2048;       // dynamic shared memory per CTA (static part aside)
 constexpr int kTileF = 32 * 33;                           // floats per padded tile
 constexpr unsigned kTileBytes = kTileF * sizeof(float);   // 4224, a multiple of 16
 constexpr unsigned kPanelBytes = 1024 * sizeof(float);    // a transposed panel tile
 
-__host__ __device__ constexpr int cluster_slots(int T) { return (T * (T + 1) / 2 + kClusterCTAs - 1) / kClusterCTAs; }
-__host__ __device__ constexpr int cluster_nbuf(int T) { return T <= kClusterDoubleT ? 2 : 1; }
-__host__ __device__ constexpr size_t cluster_smem(int T) {
-  return ((size_t)(cluster_slots(T) + 2) * kTileF + (size_t)cluster_nbuf(T) * T * 1024) * sizeof(float) + 32;
+__host__ __device__ constexpr int cluster_slots(int T, int C = kClusterCTAs) { return (T * (T + 1) / 2 + C - 1) / C; }
+// bytes of shared memory with nb panel buffers
+__host__ __device__ constexpr size_t cluster_bytes(int T, int C, int nb) {
+  return ((size_t)(cluster_slots(T, C) + 2) * kTileF + (size_t)nb * T * 1024) * sizeof(float) + 32;
 }
-constexpr size_t cluster_smem_max() {
+// the panel is double-buffered wherever two buffers fit (T <= 16 with 8 CTAs, T <= 19 with 16)
+__host__ __device__ constexpr int cluster_nbuf(int T, int C = kClusterCTAs) {
+  return cluster_bytes(T, C, 2) <= kClusterSmemLimit ? 2 : 1;
+}
+__host__ __device__ constexpr size_t cluster_smem(int T, int C = kClusterCTAs) {
+  return cluster_bytes(T, C, cluster_nbuf(T, C));
+}
+constexpr size_t cluster_smem_max(int C = kClusterCTAs, int Tmax = kClusterT) {
   size_t m = 0;
-  for (int T = 5; T <= kClusterT; T++) m = cluster_smem(T) > m ? cluster_smem(T) : m;
+  for (int T = 5; T <= Tmax; T++) m = cluster_smem(T, C) > m ? cluster_smem(T, C) : m;
   return m;
 }
 static_assert(cluster_slots(kClusterT) <= 32, "one lane per owned slot");
-static_assert(cluster_smem_max() <= 232448 - 1024, "shared memory per CTA");
+static_assert(cluster_slots(kClusterTMax, kCluster16CTAs) <= 32, "one lane per owned slot");
+static_assert(cluster_smem_max() <= kClusterSmemLimit, "shared memory per CTA");
+static_assert(cluster_smem_max(kCluster16CTAs, kClusterTMax) <= kClusterSmemLimit, "shared memory per CTA");
+static_assert(cluster_nbuf(16) == 2 && cluster_nbuf(17) == 1, "8 CTAs: two panel buffers up to 16 tile rows");
+static_assert(cluster_nbuf(19, kCluster16CTAs) == 2, "16 CTAs: two panel buffers up to 19 tile rows");
 
 // bulk copy of `bytes` from this CTA's shared memory to (possibly) another
 // CTA's, completing `bytes` on that CTA's mbarrier
@@ -735,40 +751,42 @@ __device__ __forceinline__ void panel_solve_warp(float* A, const float* U, int l
 // consumer on the critical chain) is issued on its own, then lanes 0..7 issue
 // the others.  The data must have been fenced for the async proxy and
 // synchronised within the warp.
+template <int C>
 __device__ __forceinline__ void push_tile(unsigned src, unsigned dst, unsigned bytes, unsigned bar, unsigned mask,
                                           int first, int lane) {
   if (lane == 0 && (mask >> first & 1u)) bulk_s2c(cluster_addr(dst, first), src, bytes, cluster_addr(bar, first));
   __syncwarp();
-  if (lane < kClusterCTAs && lane != first && (mask >> lane & 1u))
+  if (lane < C && lane != first && (mask >> lane & 1u))
     bulk_s2c(cluster_addr(dst, lane), src, bytes, cluster_addr(bar, lane));
 }
 
 // Named barrier of the four diagonal warps (0-3) of a CTA.
 __device__ __forceinline__ void diag_quad_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThreads)
+template <int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
     k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag) {
   pdl_entry();
   __shared__ __align__(16) float fcol[128];                  // column exchange of the diagonal factor
-  __shared__ __align__(8) unsigned long long tbar_s[2 * kClusterT];  // panel tile arrivals per (buffer, tile row)
+  __shared__ __align__(8) unsigned long long tbar_s[2 * kClusterTMax];  // panel tile arrivals per (buffer, tile row)
   __shared__ __align__(8) unsigned long long dbar_s;               // diagonal factor arrivals
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) float csm[];
   const int T = (N + 31) / 32;
-  const int nbuf = cluster_nbuf(T);
+  const int nbuf = cluster_nbuf(T, C);
   float* own = csm;                                        // owned tiles
-  float* panel = own + cluster_slots(T) * kTileF;          // nbuf x T transposed panel tiles
+  float* panel = own + cluster_slots(T, C) * kTileF;          // nbuf x T transposed panel tiles
   float* dbuf = panel + nbuf * T * 1024;                   // L^T of the next diagonal tile, 1/diag at [1024..]
   float* ustage = dbuf + kTileF;                           // the owner of a diagonal tile builds that buffer here
   const unsigned dbar = smem_u32(&dbar_s);
   __shared__ int slot_ij[32];                    // (i << 8) | j of the tile in each owned slot
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned all = (1u << kClusterCTAs) - 1u;
-  const int nslots = (T * (T + 1) / 2 - rank + kClusterCTAs - 1) / kClusterCTAs;
+  const unsigned all = (1u << C) - 1u;
+  const int nslots = (T * (T + 1) / 2 - rank + C - 1) / C;
   for (int sl = tid; sl < nslots; sl += blockDim.x) {
     int ti, tj;
-    tri_tile(rank + sl * kClusterCTAs, ti, tj);
+    tri_tile(rank + sl * C, ti, tj);
     slot_ij[sl] = (ti << 8) | tj;
   }
   __syncthreads();
@@ -778,9 +796,9 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
   const int my_j = lane < nslots ? slot_ij[lane] & 255 : -1;
   auto panel_tile = [&](int k, int i) { return panel + ((k % nbuf) * T + i) * 1024; };
   // tile i of panel k arrives on tbar(k, i); its phase parity is tpar(k)
-  auto tbar = [&](int k, int i) { return smem_u32(&tbar_s[(k % nbuf) * kClusterT + i]); };
+  auto tbar = [&](int k, int i) { return smem_u32(&tbar_s[(k % nbuf) * kClusterTMax + i]); };
   auto tpar = [&](int k) { return (unsigned)((k / nbuf) & 1); };
-  auto owner = [&](int i, int j) { return tri_index(i, j) % kClusterCTAs; };
+  auto owner = [&](int i, int j) { return tri_index(i, j) % C; };
   // the first consumer of panel tile (i, k) on the critical chain: the owner of
   // (k+1, k+1) for the first tile, else the owner of (i, k+1), which solves it next
   auto first_of = [&](int i, int k) { return i == k + 1 ? owner(k + 1, k + 1) : owner(i, k + 1); };
@@ -811,12 +829,12 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
   // panel-column ownership of column j: the CTAs owning a tile (i, j), i > j
   auto receivers_of = [&](int j) {
     unsigned m = 0;
-    for (int i = j + 1; i < T; i++) m |= 1u << (tri_index(i, j) % kClusterCTAs);
+    for (int i = j + 1; i < T; i++) m |= 1u << (tri_index(i, j) % C);
     return m;
   };
   if (tid == 0) {
     for (int b = 0; b < nbuf; b++)
-      for (int i = 0; i < T; i++) mbar_init(smem_u32(&tbar_s[b * kClusterT + i]), 1);
+      for (int i = 0; i < T; i++) mbar_init(smem_u32(&tbar_s[b * kClusterTMax + i]), 1);
     mbar_init(dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // arm for the first diagonal push and the first panel(s): panel k + nbuf is
@@ -837,7 +855,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
     bad |= !factor_tile_warp(own, ustage, fcol, lane);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, receivers_of(0), owner(1, 0), lane);
+    push_tile<C>(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, receivers_of(0), owner(1, 0), lane);
   }
   if (receivers_of(0) >> rank & 1u) {
     if (ok && !mbar_wait(dbar, dphase & 1u)) ok = false;
@@ -850,13 +868,13 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
       panel_solve_warp(Ai, dbuf, lane);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      push_tile(smem_u32(Ai), smem_u32(panel_tile(0, i)), kPanelBytes, tbar(0, i), all, first_of(i, 0), lane);
+      push_tile<C>(smem_u32(Ai), smem_u32(panel_tile(0, i)), kPanelBytes, tbar(0, i), all, first_of(i, 0), lane);
     }
   }
 
   for (int k = 0; k + 1 < T; k++) {
     const int next = tri_index(k + 1, k + 1);
-    const bool diag_here = next % kClusterCTAs == rank;
+    const bool diag_here = next % C == rank;
     const unsigned recv_next = receivers_of(k + 1);
     const bool solve_here = (recv_next >> rank & 1u) != 0;
     // arm for the push of the next diagonal tile (the previous one was consumed)
@@ -869,7 +887,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
     if (warp < 4) {
       diag_quad_sync();  // the four are done with step k-1
       if (diag_here) {
-        float* D = own + (next / kClusterCTAs) * kTileF;
+        float* D = own + (next / C) * kTileF;
         if (ok && !mbar_wait(tbar(k, k + 1), tpar(k))) ok = false;
         if (ok) diag_update_rows(D, panel_tile(k, k + 1), warp, lane);
         diag_quad_sync();
@@ -878,7 +896,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
           if (recv_next) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            push_tile(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, recv_next,
+            push_tile<C>(smem_u32(ustage), smem_u32(dbuf), kTileBytes, dbar, recv_next,
                       k + 2 < T ? owner(k + 2, k + 1) : rank, lane);
           }
         }
@@ -923,7 +941,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
           pushed = true;
           for (unsigned m = mine; m; m &= m - 1) {
             const int sl = __ffs(m) - 1, i = __shfl_sync(0xffffffffu, my_i, sl);
-            push_tile(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, tbar(k + 1, i), all,
+            push_tile<C>(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, tbar(k + 1, i), all,
                       first_of(i, k + 1), lane);
           }
         }
@@ -966,7 +984,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
     if (!pushed)  // each warp pushes the tiles it solved (after its own proxy fence)
       for (unsigned m = mine; m; m &= m - 1) {
         const int sl = __ffs(m) - 1, i = __shfl_sync(0xffffffffu, my_i, sl);
-        push_tile(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, tbar(k + 1, i), all,
+        push_tile<C>(smem_u32(own + sl * kTileF), smem_u32(panel_tile(k + 1, i)), kPanelBytes, tbar(k + 1, i), all,
                   first_of(i, k + 1), lane);
       }
   }
@@ -1007,6 +1025,8 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kCholThre
     }
   }
 }
+template __global__ void k_chol_cluster<kClusterCTAs>(float*, long long, int, DevState*, float*);
+template __global__ void k_chol_cluster<kCluster16CTAs>(float*, long long, int, DevState*, float*);
 
 // ---------------------------------------------------------------------------
 // Triangular solves with the factor of the cluster Cholesky (kSmallN < N <=
@@ -1293,7 +1313,7 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 // shared memory and a local mbarrier arrival, the other CTAs through st.async
 // completing on their per-block mbarriers.  Every wait is bounded
 // (DevState::timeout).
-constexpr int kTrsvPairMaxT = 20;
+constexpr int kTrsvPairMaxT = 27;
 constexpr int kTrsvQ = 4;     // CTAs per cluster
 constexpr int kTrsvRing = 6;  // tiles in flight per warp
 constexpr int kTrsvMaxT0 = (kTrsvPairMaxT + kTrsvQ - 1) / kTrsvQ;
@@ -1778,18 +1798,53 @@ bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, doubl
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !done[dev]) {
-    cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
+    cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
     cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((size_t)(32 * kClusterN + 1024 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float)));
     if (dev >= 0 && dev < 64) done[dev] = true;
   }
   count_launch(4);
-  launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
+  launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
   launch_k(k_inv_trace_setup, dim3(64), dim3(256), (size_t)(0), s, S, ldS, N, Np);
   const size_t tsm = (size_t)(32 * Np + 1024 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
   launch_k(k_trsm_blocks, dim3(Np / 32), dim3(256), (size_t)(tsm), s, S, ldS, 0, Np, Np, Np, Wdiag);
   launch_k(k_frob2, dim3(Np / 32), dim3(256), (size_t)(0), s, S + Np, ldS, Np, partial, out, st);
   return cudaGetLastError() == cudaSuccess;
+}
+
+// Whether a 16-CTA cluster of k_chol_cluster can be resident on this device
+// (a non-portable cluster size); decided once per process.
+static bool chol16_ok() {
+  static int ok = -1;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    ok = 0;
+    const size_t smem = cluster_smem_max(kCluster16CTAs, kClusterTMax);
+    if (cudaFuncSetAttribute(k_chol_cluster<kCluster16CTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_chol_cluster<kCluster16CTAs>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCluster16CTAs);
+    cfg.blockDim = dim3(kCholThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kCluster16CTAs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_chol_cluster<kCluster16CTAs>, &cfg) == cudaSuccess && nclusters > 0)
+      ok = 1;
+    else
+      cudaGetLastError();
+  });
+  return ok == 1;
 }
 
 bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s) {
@@ -1799,16 +1854,25 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, nullptr, nullptr, 1.0);
     return false;
   }
+  // above 16 tile rows the 8-CTA kernel holds one panel buffer (a full cluster barrier per step);
+  // the 16-CTA kernel keeps two up to 19 tile rows and covers N <= kCluster16N
+  const bool wide = Wdiag && N > 512 && N <= kCluster16N && chol16_ok();
+  if (wide) {
+    count_launch();
+    launch_k(k_chol_cluster<kCluster16CTAs>, dim3(kCluster16CTAs), dim3(kCholThreads),
+             (size_t)(cluster_smem((N + 31) / 32, kCluster16CTAs)), s, G, ldg, N, st, Wdiag);
+    if (cudaGetLastError() == cudaSuccess) return true;
+  }
   if (N <= kClusterN) {
     static bool done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !done[dev]) {
-      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
+      cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag);
+    launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag);
     if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
   }
   if (Wdiag && N <= kMaxM) {
@@ -1818,7 +1882,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     cudaGetDevice(&dev);
     const size_t trsm_smem_max = (size_t)(32 * kClusterN + 1024 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float);
     if (dev < 0 || dev >= 64 || !done_sb[dev]) {
-      cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
+      cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
       cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem_max);
       if (dev >= 0 && dev < 64) done_sb[dev] = true;
     }
@@ -1829,7 +1893,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       const int nk = N - k0 < B ? N - k0 : B;
       float* Gkk = G + k0 + (long long)k0 * ldg;
       count_launch();
-      launch_k(k_chol_cluster, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((nk + 31) / 32)), s, Gkk, ldg, nk, st,
+      launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((nk + 31) / 32)), s, Gkk, ldg, nk, st,
                                                                              Wdiag + (long long)(k0 / 32) * 1024);
       const int r0 = k0 + nk, R = N - r0;
       if (R > 0) {
