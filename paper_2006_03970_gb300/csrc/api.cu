@@ -61,6 +61,7 @@ struct ssnal_en_ctx {
   double* P = nullptr;
   float* P32 = nullptr;
   int64_t ldp = 0, ldp32 = 0, rcap = 0;
+  double last_nb1 = 0.0;  // 1 + ||b|| of the last solve's b
   float* G = nullptr;
   int64_t ldg = 0;
   float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
@@ -488,8 +489,10 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
   return SSNAL_EN_OK;
 }
 
+// nb1_known > 0: 1 + ||b|| of this b, already known (points of one path); else it is
+// computed here (one host round trip).
 ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double lam2, double* x, double* y_io,
-                           ssnal_en_result* out) {
+                           ssnal_en_result* out, double nb1_known = 0.0) {
   auto t0 = std::chrono::steady_clock::now();
   const ssnal_en_options& o = c->opt;
   cudaStream_t s = c->stream;
@@ -498,14 +501,17 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
   memset(&R, 0, sizeof(R));
   R.lambda1 = lam1;
   R.lambda2 = lam2;
-  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
-  // ||b|| via the combine kernel's scalar products (y := b temporarily)
-  CK(cudaMemcpyAsync(c->bdev, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-  launch_combine(c->tmpm, c->bdev, 1.0, nullptr, 0.0, nullptr, 0.0, m, 1, c->bdev, c->bdev, nullptr, c->st,
-                 c->comb_scratch, s);
-  ssnal_en_status e = read_state(c);
-  if (e != SSNAL_EN_OK) return e;
-  const double nb1 = 1.0 + sqrt(c->st_host->g2);
+  launch_solve_begin(c->st, c->bdev, b, m, s);  // state := 0, bdev := b
+  ssnal_en_status e = SSNAL_EN_OK;
+  double nb1 = nb1_known;
+  if (!(nb1 > 0.0)) {
+    // ||b|| via the combine kernel's scalar products (y := b temporarily)
+    launch_combine(c->tmpm, c->bdev, 1.0, nullptr, 0.0, nullptr, 0.0, m, 1, c->bdev, c->bdev, nullptr, c->st,
+                   c->comb_scratch, s);
+    if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+    nb1 = 1.0 + sqrt(c->st_host->g2);
+  }
+  c->last_nb1 = nb1;
   // ---- initial dual iterate and u = A^T y (reading: y0 = A x0 - b)
   ProxParams pp = make_pp(o.sigma0, lam1, lam2);
   if (o.use_y0 && y_io) {
@@ -815,11 +821,13 @@ ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, co
   ssnal_en_status worst = SSNAL_EN_OK;
   const ssnal_en_options saved = c->opt;
   c->opt.use_y0 = 0;
+  double nb1 = 0.0;  // 1 + ||b||, the same at every point of the path
   for (int k = 0; k < K; k++) {
     const double lam1 = c_grid[k] * gmax;
     const double lam2 = (1.0 - alpha) / alpha * c_grid[k] * gmax;
     ssnal_en_result r;
-    e = solve_impl(c, b, lam1, lam2, c->xpath, nullptr, &r);
+    e = solve_impl(c, b, lam1, lam2, c->xpath, nullptr, &r, nb1);
+    nb1 = c->last_nb1;
     if (e != SSNAL_EN_OK && e != SSNAL_EN_ENOCONV) {
       c->opt = saved;
       return e;
@@ -827,9 +835,8 @@ ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, co
     if (e == SSNAL_EN_ENOCONV) worst = SSNAL_EN_ENOCONV;
     if (out) out[k] = r;
     if (X) {
-      cudaError_t ce = cudaMemcpyAsync(X + (size_t)k * c->n, c->xpath, sizeof(double) * c->n,
-                                       cudaMemcpyDeviceToDevice, s);
-      if (ce != cudaSuccess) {
+      launch_copy_f64(X + (size_t)k * c->n, c->xpath, c->n, c->sms, s);
+      if (cudaGetLastError() != cudaSuccess) {
         c->opt = saved;
         return SSNAL_EN_ECUDA;
       }

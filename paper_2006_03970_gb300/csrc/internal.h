@@ -79,6 +79,10 @@ struct ProxParams {
 
 // ---- launch wrappers (kern_vec.cu)
 int vec_grid(long long n, int sms);
+// Zeroes *st and copies b (m values) to bdev, in one launch.
+void launch_solve_begin(DevState* st, double* bdev, const double* b, int m, cudaStream_t s);
+// dst[0..n) = src[0..n) on the stream.
+void launch_copy_f64(double* dst, const double* src, long long n, int sms, cudaStream_t s);
 // Copies *st to the pinned, device-mapped host mirror and then writes seq to flag
 // (host memory), after a system-scope fence.
 void launch_state_out(const DevState* st, DevState* host, unsigned* flag, unsigned seq, cudaStream_t s);

@@ -249,7 +249,7 @@ struct LoadI8 {
 };
 
 // Gather of A_J: P[:, k] = A[:, J[k]] (FP64) and P32[:, k] = float(P[:, k]).
-// One warp per column, grid-stride.  If r exceeds the panel capacity nothing is
+// One warp per column, grid-stride, 16 loads per lane in flight.  If r exceeds the panel capacity nothing is
 // written and the overflow flag is raised for the host.
 template <class Load>
 __global__ void __launch_bounds__(256) k_gather(Load ld, long long lda, int m, const int32_t* __restrict__ J, const DevState* st,
@@ -268,11 +268,23 @@ __global__ void __launch_bounds__(256) k_gather(Load ld, long long lda, int m, c
     const long long col = J[k], src = col * lda;
     double* dst = P + k * ldp;
     float* dst32 = P32 + k * ldp32;
-#pragma unroll 4
-    for (int i = lane; i < m; i += 32) {
-      const double v = ld(col, src + i);
-      dst[i] = v;
-      dst32[i] = (float)v;
+    // 16 loads per lane in flight before any store: one column of up to 512 rows
+    // costs one memory round trip
+    for (int i0 = 0; i0 < m; i0 += 32 * 16) {
+      double v[16];
+#pragma unroll
+      for (int e = 0; e < 16; e++) {
+        const int i = i0 + lane + 32 * e;
+        v[e] = i < m ? ld(col, src + i) : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; e++) {
+        const int i = i0 + lane + 32 * e;
+        if (i < m) {
+          dst[i] = v[e];
+          dst32[i] = (float)v[e];
+        }
+      }
     }
   }
 }
@@ -614,7 +626,38 @@ __global__ void k_state_out(const unsigned long long* __restrict__ st, unsigned 
   }
 }
 
+// Start of a solve: zeroes the solver state and copies b into the context's
+// copy (one launch instead of a memset and a copy-engine transfer).
+__global__ void k_solve_begin(unsigned long long* __restrict__ st, int st_words, double* __restrict__ bdev,
+                              const double* __restrict__ b, int m) {
+  pdl_entry();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int i = tid; i < st_words; i += nt) st[i] = 0ull;
+  for (int i = tid; i < m; i += nt) bdev[i] = b[i];
+}
+
+// dst[0..n) = src[0..n) (FP64, grid-stride).
+__global__ void k_copy_f64(double* __restrict__ dst, const double* __restrict__ src, long long n) {
+  pdl_entry();
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < n; i += nt) dst[i] = src[i];
+}
+
 // ---------------------------------------------------------------- launchers
+void launch_solve_begin(DevState* st, double* bdev, const double* b, int m, cudaStream_t s) {
+  count_launch();
+  launch_k(k_solve_begin, dim3(4), dim3(256), (size_t)0, s, reinterpret_cast<unsigned long long*>(st),
+           (int)(sizeof(DevState) / 8), bdev, b, m);
+}
+
+void launch_copy_f64(double* dst, const double* src, long long n, int sms, cudaStream_t s) {
+  long long g = (n + 255) / 256;
+  if (g > 4LL * sms) g = 4LL * sms;
+  if (g < 1) g = 1;
+  count_launch();
+  launch_k(k_copy_f64, dim3((int)g), dim3(256), (size_t)0, s, dst, src, n);
+}
+
 void launch_state_out(const DevState* st, DevState* host, unsigned* flag, unsigned seq, cudaStream_t s) {
   static_assert(sizeof(DevState) % 8 == 0, "DevState is copied in 8-byte words");
   count_launch();
