@@ -28,7 +28,7 @@ enum CounterSlot {
   kCtrBarrier = 6,  // two words: arrival count and generation of the cooperative grid barrier
   kCtrGemv = 8
 };
-constexpr int kSmallNewton = 128;  // Newton systems up to this size are factored by one CTA
+constexpr int kSmallNewton = 32;  // Newton systems up to this size (one tile) are factored by one CTA
 
 // Values computed on the device and read by the host once per Newton step.
 // The host never writes these except through cudaMemsetAsync of the whole struct.

@@ -1848,7 +1848,10 @@ static bool chol16_ok() {
 }
 
 bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s) {
-  if (N <= kSmallN) {
+  // one tile: one CTA; up to kSmallN also without inverse diagonal blocks.  From two
+  // tiles on, the cluster factor and the 4-CTA solves are faster (N = 64: 20 us
+  // against 61 us for the single-CTA factor and solves; N = 128: 37 against 131)
+  if (N <= kSmallNewton || (N <= kSmallN && !Wdiag)) {
     small_smem_attr();
     count_launch();
     launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, nullptr, nullptr, 1.0);
@@ -1950,7 +1953,7 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s) {
   if (N <= 0) return;
-  if (N <= kSmallN) {
+  if (N <= kSmallNewton || (N <= kSmallN && !Wdiag)) {
     small_smem_attr();
     count_launch();
     launch_k(k_trsv_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, L, ldl, N, rhs, acc, first, alpha);
