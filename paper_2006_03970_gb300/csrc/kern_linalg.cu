@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_llt(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Small Newton systems (N <= kSmallN): one CTA factors the matrix in shared
+// Small Newton systems (N <= kSmallN; used for one tile, N <= 32, and whenever no
+// inverse diagonal blocks are wanted): one CTA factors the matrix in shared
 // memory (right-looking, column by column) and optionally solves one right-hand
 // side in the same launch.
 constexpr int kSmallN = 128;
@@ -538,27 +539,29 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Cluster tile Cholesky (kSmallN < N <= kClusterN).  The lower triangle is cut
-// into 32x32 tiles; tile (i, j), i >= j, with linear index i(i+1)/2 + j lives in
-// the shared memory of CTA (index mod kClusterCTAs) of one thread-block cluster.
-// Right-looking blocked Cholesky with a lookahead of one column: in step k every
-// CTA updates its trailing tiles A_ij -= L_ik L_jk^T (one warp per tile) with
-// the panel column k it received, while warp 0 of the owner of (k+1, k+1)
-// updates that tile first, factors it and pushes L^T of it to the owners of the
-// panel tiles (i, k+1); those solve L_i,k+1 L_k+1,k+1^T = A_i,k+1 as soon as
-// their own updates are done and push the solved tiles (stored transposed) into
-// the panel buffer of every CTA.  Pushes are bulk shared-to-shared copies that
-// complete on the receiver's mbarriers.  With T <= 16 tile rows the panel
-// buffer is double-buffered and the cluster barrier that frees a buffer is
-// split (arrive after the reads, wait before the next overwrite), so it never
-// waits in practice; with more tile rows a full cluster barrier precedes each
-// push.  At the end each CTA inverts its diagonal tiles for the triangular
-// solves.  Rows and columns beyond N are padded with the identity, so the
-// factor of the padded matrix is L plus an identity block.
+// Cluster tile Cholesky (32 < N <= kClusterN on 8 CTAs, up to kCluster16N on 16).
+// The lower triangle is cut into 32x32 tiles; tile (i, j), i >= j, with linear
+// index i(i+1)/2 + j lives in the shared memory of CTA (index mod C) of one
+// thread-block cluster of C CTAs.  Right-looking blocked Cholesky with a
+// lookahead of one column.  In step k the four diagonal warps of the owner of
+// (k+1, k+1) update that tile with panel tile (k+1, k) as soon as it has
+// arrived, warp 0 factors it and pushes L^T of it to the owners of the panel
+// tiles (i, k+1); each of those tiles belongs to one trailing warp for good,
+// which updates it with panel k, solves L_i,k+1 L_k+1,k+1^T = A_i,k+1 once the
+// diagonal factor has arrived and pushes the solved tile (stored transposed) into
+// the panel buffer of every CTA, the consumer on the critical chain first; then it
+// applies panel k to its other tiles.  The diagonal warps apply panel k to the
+// other owned diagonal tiles.  Pushes are bulk shared-to-shared copies that
+// complete on the receivers' per-tile mbarriers.  Where two panel buffers fit in
+// shared memory the cluster barrier that frees a buffer is split (each warp
+// waits for the previous phase only where it pushes); otherwise a full cluster
+// barrier precedes each push.  At the end each CTA inverts its diagonal tiles for
+// the triangular solves.  Rows and columns beyond N are padded with the
+// identity, so the factor of the padded matrix is L plus an identity block.
 // Layout in shared memory: owned tiles (row stride 33; off-diagonal tiles are
 // stored transposed with row stride 32 once solved), the panel buffer(s) of
 // transposed tiles (32 x 32), L^T of the current diagonal tile with its
-// reciprocal diagonal, a staging copy of it, and the mbarriers.
+// reciprocal diagonal, and a staging copy of it; the mbarriers are static.
 namespace cgx = cooperative_groups;
 constexpr int kClusterCTAs = 8;
 // Threads per CTA of k_chol_cluster: warps 0-3 keep the diagonal tiles (warp 0
@@ -1029,9 +1032,10 @@ template __global__ void k_chol_cluster<kClusterCTAs>(float*, long long, int, De
 template __global__ void k_chol_cluster<kCluster16CTAs>(float*, long long, int, DevState*, float*);
 
 // ---------------------------------------------------------------------------
-// Triangular solves with the factor of the cluster Cholesky (kSmallN < N <=
-// kClusterN) and its inverse diagonal blocks W_II = L_II^{-1}: right-looking
-// block substitution in one CTA.  Thread t owns row t of the right-hand side.
+// Triangular solves with the factor of the cluster Cholesky (N <= kClusterN)
+// and its inverse diagonal blocks W_II = L_II^{-1}: right-looking block
+// substitution in one CTA (the fallback of k_trsv_pair and k_trsv_cluster when a
+// cluster launch is refused).  Thread t owns row t of the right-hand side.
 // Step I of the forward pass: warp I forms z_I = W_II r_I; every row below
 // block I then subtracts L[t, I] z_I.  The backward pass runs the same way
 // with L^T.  The block column (forward) or block row (backward) that the next

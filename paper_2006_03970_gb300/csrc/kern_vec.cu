@@ -2,7 +2,9 @@
 //   * prox + active set + ordered compaction of J (eqs. prox_elastic, Q_def),
 //   * gather of A_J into a packed panel,
 //   * the panel GEMVs A_J w (eq. grad_phy) and A_J^T v (eq. smw_formula),
-//   * m-vector combines with the scalar products the line search needs.
+//   * m-vector combines with the scalar products the line search needs,
+//   * the start of a solve (state zeroed, b copied), vector copies, and the copy
+//     of the solver state into the host mirror that the host polls.
 // Every reduction runs in a fixed order, so results are bitwise repeatable.
 #include <cuda_bf16.h>
 
