@@ -1032,6 +1032,65 @@ template __global__ void k_chol_cluster<kClusterCTAs>(float*, long long, int, De
 template __global__ void k_chol_cluster<kCluster16CTAs>(float*, long long, int, DevState*, float*);
 
 // ---------------------------------------------------------------------------
+// One-tile Newton systems (N <= 32) by one warp.  The lower triangle of G is
+// staged into a 32x32 shared tile padded with the identity beyond N.  With
+// `factor` the tile is factored by factor_tile_warp, L is written back to the
+// lower triangle of G and a non-positive pivot sets st->chol_fail; otherwise G
+// already holds L.  If rhs != nullptr, (L L^T) c = rhs is then solved by two
+// 32-step chains with lane l holding entry l: each row of L (forward) or column
+// (backward) is scaled once by 1/L_ll, so step q broadcasts lane q's final
+// value and the lanes still open subtract one product.  acc = alpha c, or
+// acc + alpha c when !first (FP64 output).
+__global__ void __launch_bounds__(32) k_tile1_solve(float* __restrict__ G, long long ld, int N, int factor,
+                                                    DevState* st, const double* __restrict__ rhs,
+                                                    double* __restrict__ acc, int first, double alpha) {
+  pdl_entry();
+  __shared__ float D[32 * 33];
+  __shared__ __align__(16) float U[1024 + 32];
+  __shared__ __align__(16) float cb[128];
+  const int lane = threadIdx.x;
+#pragma unroll 8
+  for (int j = 0; j < 32; j++) {
+    float v = (lane == j) ? 1.0f : 0.0f;
+    if (lane < N && j < N && lane >= j) v = G[lane + (long long)j * ld];
+    D[lane * 33 + j] = v;
+  }
+  __syncwarp();
+  if (factor) {
+    const bool ok = factor_tile_warp(D, U, cb, lane);
+    __syncwarp();
+    for (int j = 0; j < N; j++)
+      if (lane >= j && lane < N) G[lane + (long long)j * ld] = D[lane * 33 + j];
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) st->chol_fail = 1;
+  }
+  if (!rhs) return;
+  const float rl = __frcp_rn(D[lane * 33 + lane]);
+  float a[32], b[32];
+#pragma unroll
+  for (int q = 0; q < 32; q++) {
+    a[q] = D[lane * 33 + q] * rl;  // L_lq / L_ll, read for q < l
+    b[q] = D[q * 33 + lane] * rl;  // L_ql / L_ll, read for q > l
+  }
+  float r = lane < N ? (float)rhs[lane] * rl : 0.0f;
+#pragma unroll
+  for (int q = 0; q < 32; q++) {
+    if (q < N) {
+      const float zq = __shfl_sync(0xffffffffu, r, q);
+      if (lane > q) r = fmaf(-a[q], zq, r);
+    }
+  }
+  r *= rl;  // z_l / L_ll
+#pragma unroll
+  for (int q = 31; q >= 0; q--) {
+    if (q < N) {
+      const float cq = __shfl_sync(0xffffffffu, r, q);
+      if (lane < q) r = fmaf(-b[q], cq, r);
+    }
+  }
+  if (lane < N) acc[lane] = first ? alpha * (double)r : acc[lane] + alpha * (double)r;
+}
+
+// ---------------------------------------------------------------------------
 // Triangular solves with the factor of the cluster Cholesky (N <= kClusterN)
 // and its inverse diagonal blocks W_II = L_II^{-1}: right-looking block
 // substitution in one CTA (the fallback of k_trsv_pair and k_trsv_cluster when a
@@ -1855,7 +1914,13 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
   // one tile: one CTA; up to kSmallN also without inverse diagonal blocks.  From two
   // tiles on, the cluster factor and the 4-CTA solves are faster (N = 64: 20 us
   // against 61 us for the single-CTA factor and solves; N = 128: 37 against 131)
-  if (N <= kSmallNewton || (N <= kSmallN && !Wdiag)) {
+  if (N <= kSmallNewton) {
+    count_launch();
+    launch_k(k_tile1_solve, dim3(1), dim3(32), 0, s, G, ldg, N, 1, st, (const double*)nullptr, (double*)nullptr, 1,
+             1.0);
+    return false;
+  }
+  if (N <= kSmallN && !Wdiag) {
     small_smem_attr();
     count_launch();
     launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, nullptr, nullptr, 1.0);
@@ -1949,15 +2014,20 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
 
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
                              double alpha, cudaStream_t s) {
-  small_smem_attr();
+  if (N <= 0) return;
   count_launch();
-  launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, rhs, acc, alpha);
+  launch_k(k_tile1_solve, dim3(1), dim3(32), 0, s, G, ldg, N, 1, st, rhs, acc, 1, alpha);
 }
 
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s) {
   if (N <= 0) return;
-  if (N <= kSmallNewton || (N <= kSmallN && !Wdiag)) {
+  if (N <= kSmallNewton) {
+    count_launch();
+    launch_k(k_tile1_solve, dim3(1), dim3(32), 0, s, const_cast<float*>(L), ldl, N, 0, st, rhs, acc, first, alpha);
+    return;
+  }
+  if (N <= kSmallN && !Wdiag) {
     small_smem_attr();
     count_launch();
     launch_k(k_trsv_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, L, ldl, N, rhs, acc, first, alpha);

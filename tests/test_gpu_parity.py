@@ -181,7 +181,7 @@ def test_grad_gather(m, n, r):
 
 # ---------------------------------------------------------------- a5 + a6: Newton system
 @pytest.mark.parametrize("syrk_tc", [1, 0])
-@pytest.mark.parametrize("m,r", [(30, 0), (30, 1), (30, 29), (30, 30), (30, 31), (100, 250), (257, 65),
+@pytest.mark.parametrize("m,r", [(30, 0), (30, 1), (30, 29), (30, 30), (30, 31), (5, 7), (40, 32), (32, 40), (100, 250), (257, 65),
                                  (500, 120), (128, 129), (129, 300), (300, 200), (200, 400), (700, 600),
                                  (720, 680), (900, 800), (760, 800), (1000, 999)])
 def test_newton_direction(m, r, syrk_tc):
