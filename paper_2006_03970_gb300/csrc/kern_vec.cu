@@ -19,12 +19,14 @@ std::atomic<long long> g_launches{0};
 constexpr int kVecThreads = 256;
 constexpr int kVecMaxBlocks = 1024;  // every block of pass 2 reads all per-block counts
 
-// Blocks for the O(n) passes: at most two per SM (and kVecMaxBlocks) and at least
+// Blocks for the O(n) passes: at most four per SM (and kVecMaxBlocks) and at least
 // 256 entries per block, so that the FP64 work (a few FP64 operations per entry,
-// at the GPU's low FP64 rate) is spread evenly over the SMs.
+// at the GPU's low FP64 rate) is spread evenly over the SMs.  At n = 1e5 four
+// blocks per SM (one pass of loads per thread) take the count and scatter pair
+// from 18.8 to 15.3 us against two per SM.
 int vec_grid(long long n, int sms) {
   long long g = (n + 255) / 256;
-  long long cap = 2LL * sms;
+  long long cap = 4LL * sms;
   if (cap > kVecMaxBlocks) cap = kVecMaxBlocks;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
@@ -514,16 +516,33 @@ __global__ void __launch_bounds__(kGemvClThreads) k_gemv_cl(const double* __rest
     if (i >= m) break;
     const double* p = P + i;
     double acc = 0.0;
-    for (long long k = k0; k < k1; k += kGemvClUnroll) {
+    long long k = k0;
+    for (; k + kGemvClUnroll <= k1; k += kGemvClUnroll) {
       double pv[kGemvClUnroll], cv[kGemvClUnroll];
 #pragma unroll
       for (int e = 0; e < kGemvClUnroll; e++) {
-        const bool ok = k + e < k1;
+        pv[e] = p[(k + e) * ldp];
+        cv[e] = coef[k + e];
+      }
+#pragma unroll
+      for (int e = 0; e < kGemvClUnroll; e++) acc = fma(pv[e], cv[e], acc);
+    }
+    // the last partial group: all its loads in flight, but only the products that
+    // exist (the FP64 pipe, not the loads, bounds this phase)
+    const int rem = (int)(k1 - k);
+    if (rem > 0) {
+      double pv[kGemvClUnroll], cv[kGemvClUnroll];
+#pragma unroll
+      for (int e = 0; e < kGemvClUnroll; e++) {
+        const bool ok = e < rem;
         pv[e] = ok ? p[(k + e) * ldp] : 0.0;
         cv[e] = ok ? coef[k + e] : 0.0;
       }
 #pragma unroll
-      for (int e = 0; e < kGemvClUnroll; e++) acc = fma(pv[e], cv[e], acc);
+      for (int e = 0; e < kGemvClUnroll; e++) {
+        if (e >= rem) break;
+        acc = fma(pv[e], cv[e], acc);
+      }
     }
     cl_part[i] = acc;
   }
