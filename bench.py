@@ -194,9 +194,11 @@ def run_gpu(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     fits = 0
+    newton = 0  # one A^T d stream launch per Newton step
     for _ in range(args.steps):
         st, res, done = pkg.ssnal_en_path(ctx.ctx, b, ALPHA, grid, X)
         fits += _count_fits(res, done)
+        newton += sum(r.newton_iters for r in res[:done])
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -248,10 +250,11 @@ def run_gpu(args):
                 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel on this
                 # workload (profiles/k_stream_lane_modeT_m500_n1e5.md)
                 "traffic": STREAM_TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
-                "peak_kind": peak_kind, "launches": launches,
+                "peak_kind": peak_kind, "launches": newton, "timed_launches": launches,
+                "timed_every": 8,
                 "avg_launch_us": (s_ms / launches * 1e3) if launches else None,
                 "bytes_per_launch": (prof1["stream_bytes"] / launches) if launches else None,
-                "share_of_step": (s_ms / ms) if ms > 0 else None}
+                "share_of_step": (s_ms / launches * newton / ms) if (ms > 0 and launches) else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",

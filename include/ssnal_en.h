@@ -172,16 +172,19 @@ ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* ctx, const double* b_host, doub
                                    ssnal_en_result* out, int32_t* n_done);
 
 /* Kernel accounting of this context.  When enabled, CUDA events are recorded on
- * the context's stream around every launch of the A^T d stream (the one pass
- * over A of each Newton step, eq. line_search fused in) and their elapsed
- * times are summed at the next synchronisation.
- *  enable  1: record from now on, 2: also record the phases of
+ * the context's stream around launches of the A^T d stream (the one pass over A
+ * of each Newton step, eq. line_search fused in) and their elapsed times are
+ * summed as they complete.
+ *  enable  1: record around every eighth launch from now on (the first, the
+ *          ninth, ...: a recorded launch loses its overlap with the kernels
+ *          beside it, so level 1 keeps that cost to one launch in eight),
+ *          2: record around every launch and also the phases of
  *          ssnal_en_profile_phases (more events on the host's path between
  *          kernels), 0: stop recording.
  *  reset   1: zero the sums before reporting.
- *  stream_ms        summed device time of those launches (host, may be NULL)
- *  stream_launches  number of those launches (host, may be NULL)
- *  stream_bytes     algorithmic bytes of those launches: A once (m*n*elem) plus
+ *  stream_ms        summed device time of the recorded launches (host, may be NULL)
+ *  stream_launches  number of the recorded launches (host, may be NULL)
+ *  stream_bytes     algorithmic bytes of the recorded launches: A once (m*n*elem) plus
  *                   the vectors d (read), x, u (read) and t (written)
  *  kernel_launches  kernels launched by this library in this process so far
  * Synchronises the stream.  Errors: EINVAL (null ctx), ECUDA. */
@@ -189,7 +192,8 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t rese
                                  int64_t* stream_launches, double* stream_bytes, int64_t* kernel_launches);
 
 /* Per-phase device time since the last ssnal_en_profile(reset = 1), recorded
- * while profiling is enabled at level 2 (level 1 records phase 2 only).  Four
+ * while profiling is enabled at level 2 (level 1 records one launch in eight of
+ * phase 2 only).  Four
  * phases, in this order:
  *  0 prox + active set + gather + gradient (eqs. prox_elastic, Q_def, grad_phy)
  *  1 Newton direction: SYRK, Cholesky, solves and refinement (eqs. AJ_system, smw_formula)

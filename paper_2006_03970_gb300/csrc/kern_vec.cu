@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
   long long start, stop;
   block_range(n, start, stop);
   const double s = apply_update ? st->s : 0.0;
-  if (apply_update && blockIdx.x == 0) {
+  // y += s d in the last block, whose range of entries is the shortest
+  if (apply_update && blockIdx.x == gridDim.x - 1) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) y[i] = __dadd_rn(y[i], __dmul_rn(s, d[i]));
   }
   unsigned cnt = 0;
@@ -167,6 +168,28 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
   __shared__ long long tile_total;
   __shared__ double red[5 * kVecThreads];
   const int G = gridDim.x, b = blockIdx.x;
+  long long start, stop;
+  block_range(n, start, stop);
+  // the entries of the first tile are loaded and classified before the counts of
+  // the blocks ahead are read, so that the two latencies overlap
+  auto classify = [&](long long j, double& w, bool& act) {
+    w = 0.0;
+    act = false;
+    if (j < stop) {
+      const double xj = x[j];
+      if (MODE == kProxSupport) {
+        w = xj;
+        act = xj != 0.0;
+      } else {
+        const double v = v_of(xj, u[j], pp.sigma);
+        act = is_active(v, pp);
+        w = prox_value(v, pp);
+      }
+    }
+  };
+  double w0;
+  bool act0;
+  classify(start + threadIdx.x, w0, act0);
   long long before = 0, all_cnt = 0;
   for (int c = threadIdx.x; c < G; c += kVecThreads) {
     const long long v = __ldcg(&counts[c]);
@@ -190,24 +213,12 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
       if (threadIdx.x == 4) st->dualpen = tot;
     }
   }
-  long long start, stop;
-  block_range(n, start, stop);
   long long pos = before;
   for (long long base = start; base < stop; base += blockDim.x) {
-    long long j = base + threadIdx.x;
-    double w = 0.0;
-    bool act = false;
-    if (j < stop) {
-      const double xj = x[j];
-      if (MODE == kProxSupport) {
-        w = xj;
-        act = xj != 0.0;
-      } else {
-        const double v = v_of(xj, u[j], pp.sigma);
-        act = is_active(v, pp);
-        w = prox_value(v, pp);
-      }
-    }
+    const long long j = base + threadIdx.x;
+    double w = w0;
+    bool act = act0;
+    if (base != start) classify(j, w, act);
     long long incl = block_incl_scan(act ? 1 : 0, shl);
     if (act) {
       long long p = pos + incl - 1;
@@ -505,10 +516,25 @@ __global__ void __launch_bounds__(kGemvClThreads) k_gemv_cl(const double* __rest
   extern __shared__ double cl_part[];  // m partial row sums of this CTA's columns
   __shared__ double red[4 * kGemvClThreads];
   __shared__ double scal[kGemvClMax][4];
-  const long long r = r_host >= 0 ? r_host : st->r;
-  if (r > rcap) return;  // the same r in every CTA: none reaches a barrier
   const int C = (int)cluster_size(), c = (int)cluster_rank();
   const int tid = threadIdx.x;
+  // this CTA's rows of the combine; the operands of each thread's first row are
+  // loaded now, so that their latency is spent during the products
+  const int mr = (m + C - 1) / C;
+  const int r0 = min(m, c * mr), r1 = min(m, r0 + mr);
+  double fa = 0.0, fb = 0.0, fy = 0.0, fbv = 0.0, fg = 0.0;
+  if (r0 + tid < r1) {
+    const int i = r0 + tid;
+    if (a) fa = a[i];
+    if (b) fb = b[i];
+    if (which != 0) {
+      fy = yv[i];
+      fbv = bv[i];
+    }
+    if (which == 2) fg = gv[i];
+  }
+  const long long r = r_host >= 0 ? r_host : st->r;
+  if (r > rcap) return;  // the same r in every CTA: none reaches a barrier
   const long long per = (r + C - 1) / C;
   const long long k0 = min(r, (long long)c * per), k1 = min(r, k0 + per);
   for (int i0 = 0; i0 < m; i0 += kGemvClThreads) {
@@ -548,8 +574,6 @@ __global__ void __launch_bounds__(kGemvClThreads) k_gemv_cl(const double* __rest
   }
   cluster_arrive();
   cluster_wait();
-  const int mr = (m + C - 1) / C;
-  const int r0 = min(m, c * mr), r1 = min(m, r0 + mr);
   double q[4] = {0, 0, 0, 0};
   for (int i = r0 + tid; i < r1; i += kGemvClThreads) {
     const unsigned loc = smem_u32(cl_part + i);
@@ -560,19 +584,23 @@ __global__ void __launch_bounds__(kGemvClThreads) k_gemv_cl(const double* __rest
 #pragma unroll
     for (int e = 0; e < kGemvClMax; e++)
       if (e < C) sum += pv[e];
+    const bool first = i == r0 + tid;
+    double ai = 0.0, bi_ = 0.0;
+    if (a) ai = first ? fa : a[i];
+    if (b) bi_ = first ? fb : b[i];
     double lin = 0.0;
-    if (a) lin = ca * a[i];
-    if (b) lin = a ? lin + cb * b[i] : cb * b[i];
+    if (a) lin = ca * ai;
+    if (b) lin = a ? lin + cb * bi_ : cb * bi_;
     const double o = (a || b) ? lin + cs * sum : cs * sum;
     out[i] = o;
     if (which == 1) {
-      const double yi = yv[i], bi = bv[i];
+      const double yi = first ? fy : yv[i], bi = first ? fbv : bv[i];
       q[0] += o * o;
       q[1] += yi * yi;
       q[2] += (yi - o) * (yi - o);
       q[3] += bi * yi;
     } else if (which == 2) {
-      const double yi = yv[i], bi = bv[i], gi = gv[i];
+      const double yi = first ? fy : yv[i], bi = first ? fbv : bv[i], gi = first ? fg : gv[i];
       q[0] += gi * o;
       q[1] += yi * o;
       q[2] += o * o;
