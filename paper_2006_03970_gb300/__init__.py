@@ -413,8 +413,9 @@ def ssnal_en_profile_phases(ctx):
 
 
 def ssnal_en_profile(ctx, enable, reset: bool = False, phases: bool = False):
-    """Returns dict(stream_ms, stream_launches, stream_bytes, kernel_launches).
-    ``phases`` also records the phases of ssnal_en_profile_phases (level 2)."""
+    """Returns dict(stream_ms, stream_launches, stream_bytes, kernel_launches) of the
+    A^T d stream launches that carried events: one in eight at level 1; every
+    launch, and the phases of ssnal_en_profile_phases, with ``phases`` (level 2)."""
     ms, nl, by, kl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
     level = (2 if phases else 1) if enable else 0
     _check(load_library().ssnal_en_profile(ctx, level, int(bool(reset)), ctypes.byref(ms),
