@@ -127,7 +127,8 @@ def test_at_y_ignores_padding_rows():
 
 
 # ---------------------------------------------------------------- a2: prox + J
-@pytest.mark.parametrize("n", [1, 255, 256, 257, 5000, 100_003])
+# 400_000: more entries per block than threads (several tiles of the compaction per block)
+@pytest.mark.parametrize("n", [1, 255, 256, 257, 5000, 100_003, 400_000])
 def test_prox_active_set(n):
     rng = np.random.default_rng(n)
     m = 8
