@@ -130,7 +130,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
 // N <= 640; returns false otherwise or on a launch error.
 bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, double* partial, double* out,
                cudaStream_t s);
-// N <= kSmallNewton: factor and solve one right-hand side in one launch (acc = c)
+// N <= kSmallNewton: factor and solve one right-hand side in one launch by one warp (acc = alpha c)
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
                              double alpha, cudaStream_t s);
 // acc = (first ? alpha c : acc + alpha c) with (L L^T) c = rhs

@@ -236,10 +236,10 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv_llt(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Small Newton systems (N <= kSmallN; used for one tile, N <= 32, and whenever no
-// inverse diagonal blocks are wanted): one CTA factors the matrix in shared
-// memory (right-looking, column by column) and optionally solves one right-hand
-// side in the same launch.
+// Small systems without inverse diagonal blocks (32 < N <= kSmallN: a factor
+// whose caller wants no W_II, and the solves after a factor that left none): one
+// CTA factors the matrix (column by column) or stages L in shared memory and
+// solves.  One tile (N <= 32) goes to k_tile1_solve instead.
 constexpr int kSmallN = 128;
 constexpr int kSmallThreads = 1024;
 
@@ -293,18 +293,12 @@ constexpr size_t kSmallSmem = (size_t)(kSmallN * (kSmallN + 1) + kSmallN) * size
 // elements (lane + 32a, warp + 32b), a, b < 4.  Column k: the owner of (k, k)
 // takes the square root, the owners of column k scale it into a shared column
 // buffer, and every thread applies the rank-one update to its own elements
-// (two block barriers per column).  L is written back to G; if rhs != nullptr
-// the CTA also solves (L L^T) c = rhs and stores acc = alpha c (FP64).
+// (two block barriers per column).  L is written back to G.
 __global__ void __launch_bounds__(kSmallThreads) k_chol_small(float* __restrict__ G, long long ld, int N,
-                                                              DevState* st, const double* __restrict__ rhs,
-                                                              double* __restrict__ acc, double alpha) {
+                                                              DevState* st) {
   pdl_entry();
-  extern __shared__ float sm_small[];
-  float* Ls = sm_small;
-  float* z = sm_small + kSmallN * (kSmallN + 1);
   __shared__ float col[kSmallN];
   __shared__ float rdiag;
-  const int ldl = kSmallN + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float a[4][4];
 #pragma unroll
@@ -366,18 +360,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_chol_small(float* __restrict_
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int i = lane + 32 * p, j = warp + 32 * q;
-      if (i < N && j < N && i >= j) {
-        G[i + (long long)j * ld] = a[p][q];
-        Ls[i + j * ldl] = a[p][q];
-      } else if (i < kSmallN && j < kSmallN) {
-        Ls[i + j * ldl] = 0.0f;
-      }
+      if (i < N && j < N && i >= j) G[i + (long long)j * ld] = a[p][q];
     }
-  if (!rhs) return;
-  for (int i = tid; i < N; i += blockDim.x) z[i] = (float)rhs[i];
-  __syncthreads();
-  smem_forward_backward(Ls, ldl, N, z);
-  for (int i = tid; i < N; i += blockDim.x) acc[i] = alpha * (double)z[i];
 }
 
 // (L L^T) c = rhs with L (N <= kSmallN) staged into shared memory; acc = c or acc + c.
@@ -1807,7 +1791,6 @@ static void small_smem_attr() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && done[dev]) return;
-  cudaFuncSetAttribute(k_chol_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
   cudaFuncSetAttribute(k_trsv_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallSmem);
   if (dev >= 0 && dev < 64) done[dev] = true;
 }
@@ -1921,9 +1904,8 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     return false;
   }
   if (N <= kSmallN && !Wdiag) {
-    small_smem_attr();
     count_launch();
-    launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, G, ldg, N, st, nullptr, nullptr, 1.0);
+    launch_k(k_chol_small, dim3(1), dim3(kSmallThreads), (size_t)0, s, G, ldg, N, st);
     return false;
   }
   // above 16 tile rows the 8-CTA kernel holds one panel buffer (a full cluster barrier per step);
