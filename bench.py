@@ -45,6 +45,21 @@ def _dist():
     return rank, world, local
 
 
+def reduce_over_ranks(elapsed, units, device):
+    """(max of `elapsed`, sum of `units`) over the ranks of the default process group;
+    the inputs unchanged without one.  The job's time is its slowest rank's; every rank
+    contributes the fits it completed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return elapsed, units
+    t = torch.tensor([float(elapsed), float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return tmax[0].item(), t[1].item()
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -205,15 +220,7 @@ def run_gpu(args):
     prof1 = pkg.ssnal_en_profile(ctx.ctx, False, False)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(fits)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms, fits_all = tmax[0].item(), t[1].item()
-    else:
-        fits_all = fits
+    ms, fits_all = reduce_over_ranks(ms, fits, "cuda")
     value = fits_all / (ms / 1e3)
 
     # end to end through the public C ABI with host buffers (b in, all solutions out)
@@ -230,13 +237,7 @@ def run_gpu(args):
         efits += _count_fits(res, done)
     edt = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([edt, float(efits)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        edt, efits = tmax[0].item(), t[1].item()
+    edt, efits = reduce_over_ranks(edt, efits, "cuda")
     e2e_value = efits / edt
 
     peak, peak_kind = _peaks()
