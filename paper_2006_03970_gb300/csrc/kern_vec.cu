@@ -22,8 +22,8 @@ constexpr int kVecMaxBlocks = 1024;  // every block of pass 2 reads all per-bloc
 // Blocks for the O(n) passes: at most four per SM (and kVecMaxBlocks) and at least
 // 256 entries per block, so that the FP64 work (a few FP64 operations per entry,
 // at the GPU's low FP64 rate) is spread evenly over the SMs.  At n = 1e5 four
-// blocks per SM (one pass of loads per thread) take the count and scatter pair
-// from 18.8 to 15.3 us against two per SM.
+// blocks per SM (one entry per thread) made the whole solve path about 1 % faster
+// than two per SM (three per SM was not better).
 int vec_grid(long long n, int sms) {
   long long g = (n + 255) / 256;
   long long cap = 4LL * sms;
