@@ -117,3 +117,62 @@ def test_mutant_smw_transposed_operand(monkeypatch):
 def test_mutant_active_set_threshold(monkeypatch):
     monkeypatch.setattr(R, "active_set", lambda v, s, l1: np.flatnonzero(np.abs(v) > l1))
     assert not _solution_matches_cd()
+
+
+def _null_model_at_lambda_max():
+    # lam_max (Sec. 4.1) is the smallest penalty whose solution is the null model: at
+    # c = 1 the solution must be x = 0 (and then y = -b)
+    p = synth.make_problem(30, 120, k=4, seed=8)
+    l1, l2 = R.lambdas(p.At, p.b, 0.6, 1.0)
+    r = R.solve(p.At, p.b, l1, l2)
+    return r.converged and np.all(r.x == 0.0)
+
+
+def _psi_is_lagrangian_at_z_bar():
+    # Prop. 2: psi(y) = L_sigma(y, z_bar(y) | x)
+    p = synth.make_problem(20, 60, k=4, seed=9)
+    l1, l2 = R.lambdas(p.At, p.b, 0.7, 0.4)
+    rng = np.random.default_rng(3)
+    x, y, s = rng.normal(size=60) * (rng.random(60) < 0.3), rng.normal(size=20), 0.6
+    z = R.z_bar(y, x, p.At, s, l1, l2)
+    return np.isclose(R.psi(y, x, p.At, p.b, s, l1, l2), R.aug_lagrangian(y, z, x, p.At, p.b, s, l1, l2), rtol=1e-12)
+
+
+def _mxm_branch_ok():
+    # r >= m takes the m x m system; V = I + kappa A_J A_J^T is pinned by finite
+    # differences of grad psi (test_oracle_psi.py)
+    rng = np.random.default_rng(4)
+    AJt = rng.normal(size=(26, 20))
+    g = rng.normal(size=20)
+    d = R.newton_direction(AJt, g, 0.37)
+    return np.allclose((np.eye(20) + 0.37 * AJt.T @ AJt) @ d, -g, atol=1e-10)
+
+
+def test_unmutated_extra_pins_pass():
+    assert _null_model_at_lambda_max() and _psi_is_lagrangian_at_z_bar() and _mxm_branch_ok()
+
+
+def test_mutant_lambdas_alpha_swapped(monkeypatch):
+    def bad(At, b, alpha, c):
+        g = np.abs(np.asarray(At) @ np.asarray(b)).max()
+        return (1.0 - alpha) / alpha * c * g, c * g
+    monkeypatch.setattr(R, "lambdas", bad)
+    assert not _null_model_at_lambda_max()
+
+
+def test_mutant_z_bar_without_sigma(monkeypatch):
+    monkeypatch.setattr(R, "z_bar", lambda y, x, At, s, l1, l2: R.prox_p_star_over_sigma(x - s * (At @ y), 1.0, l1, l2))
+    assert not _psi_is_lagrangian_at_z_bar()
+
+
+def test_mutant_mxm_branch_without_kappa(monkeypatch):
+    orig = R.newton_direction
+
+    def bad(AJt, g, kappa):
+        r, m = AJt.shape
+        if r < m:
+            return orig(AJt, g, kappa)
+        M = np.eye(m) + AJt.T @ AJt
+        return -sla.cho_solve(sla.cho_factor(M, lower=True), g)
+    monkeypatch.setattr(R, "newton_direction", bad)
+    assert not _mxm_branch_ok()
