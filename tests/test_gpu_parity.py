@@ -384,3 +384,26 @@ def test_invalid_lambda_rejected():
             ctx.solve(p.b, l1, l2)
         assert e.value.status == pkg.EINVAL
     ctx.close()
+
+
+# ---------------------------------------------------------------- tracing (ssnal_en_profile)
+def test_profile_times_one_stream_launch_in_eight_and_all_at_level_two():
+    p = synth.make_problem(80, 3000, k=8, seed=12, block=20, rho=0.7)
+    grid = synth.path_grid(10, 0.05)
+    ctx = pkg.Context(p.At)
+    ctx.path(p.b, 0.6, grid)  # warm-up
+    torch.cuda.synchronize()
+    for level2, every in ((False, 8), (True, 1)):
+        pkg.ssnal_en_profile(ctx.ctx, True, True, phases=level2)
+        X, res, done = ctx.path(p.b, 0.6, grid)
+        prof = pkg.ssnal_en_profile(ctx.ctx, False, False)
+        newton = sum(r.newton_iters for r in res[:done])  # one A^T d launch per Newton step
+        assert done == len(grid) and newton > 8
+        assert prof["stream_launches"] == (newton + every - 1) // every
+        assert prof["stream_ms"] > 0.0
+        per = prof["stream_bytes"] / prof["stream_launches"]
+        assert per == pytest.approx(8.0 * 80 * 3000 + 3 * 8.0 * 3000 + 8.0 * 80)  # A once, x u t, d
+        if level2:
+            ph = pkg.ssnal_en_profile_phases(ctx.ctx)
+            assert all(n > 0 for _, n in ph.values())
+    ctx.close()
