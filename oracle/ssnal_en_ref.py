@@ -17,6 +17,9 @@ Readings of points the paper leaves open (each used identically by the CUDA path
     trials; if none passes, the last trial step is taken.
   * The active set uses the strict test |v_j| > sigma lam1 (eq. for Q).
   * SMW form iff 0 < r < m; m x m form iff r >= m; r = 0 gives d = -grad psi.
+  * Conjugate gradients replace the direct Newton solve when m and r both exceed 1e4
+    (Sec. 3.2), started at d = 0 and stopped at ||V d + g|| <= 1e-10 ||g|| (the paper
+    gives no CG tolerance).
   * The x update: x <- x - sigma (A^T y + z) with z from Prop. 2 (2); by the Moreau
     decomposition (Sec. 2.2) this is prox_{sigma p}(x - sigma A^T y), which is
     evaluated in that form so that inactive coordinates are exactly zero.
@@ -128,6 +131,38 @@ def newton_direction(AJt, g, kappa):
     return -sla.cho_solve(sla.cho_factor(M, lower=True), g)
 
 
+def newton_direction_cg(AJt, g, kappa, rtol=1e-10, maxiter=None, history=None):
+    """Approximate solve of (I_m + kappa A_J A_J^T) d = -g (eq. AJ_system) by conjugate
+    gradients, which Algorithm 1 step (1) allows and Sec. 3.2 proposes once m and r both
+    exceed 1e4.  Matrix-free: V p = p + kappa A_J (A_J^T p).  Textbook CG started at d = 0;
+    it stops when ||V d + g|| <= rtol ||g|| or after maxiter iterations (default 10 m: in
+    exact arithmetic at most m are needed, rounding can add some).  If
+    ``history`` is a list, the iterate of every iteration is appended to it.  Returns
+    (d, iterations)."""
+    AJt = np.asarray(AJt, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m = g.size
+    d = np.zeros(m)
+    res = -g.copy()  # -g - V d at d = 0
+    p = res.copy()
+    rr = res @ res
+    stop = rtol * np.sqrt(g @ g)
+    limit = 10 * m if maxiter is None else maxiter
+    it = 0
+    while np.sqrt(rr) > stop and it < limit:
+        Vp = p + kappa * (AJt.T @ (AJt @ p))
+        alpha = rr / (p @ Vp)
+        d = d + alpha * p
+        res = res - alpha * Vp
+        rr_next = res @ res
+        p = res + (rr_next / rr) * p
+        rr = rr_next
+        it += 1
+        if history is not None:
+            history.append(d.copy())
+    return d, it
+
+
 @dataclasses.dataclass
 class Options:
     sigma0: float = 5e-3       # Sec. 4.1
@@ -139,6 +174,8 @@ class Options:
     max_al: int = 100
     max_newton: int = 50
     max_ls: int = 40
+    cg_above: int = 10_000     # CG Newton solve when m and r both exceed this (Sec. 3.2)
+    cg_rtol: float = 1e-10
 
 
 @dataclasses.dataclass
@@ -193,7 +230,10 @@ def solve(At, b, lam1, lam2, x0=None, y0=None, opts: Options | None = None) -> R
             if np.linalg.norm(g) / nb1 <= opts.tol:
                 break
             kappa = sigma / (1.0 + sigma * lam2)
-            d = newton_direction(At[J], g, kappa)        # eqs. AJ_system / smw_formula
+            if m > opts.cg_above and len(J) > opts.cg_above:
+                d, _ = newton_direction_cg(At[J], g, kappa, opts.cg_rtol)   # Sec. 3.2
+            else:
+                d = newton_direction(At[J], g, kappa)    # eqs. AJ_system / smw_formula
             r_hist.append(len(J))
             newton += 1
             psi0 = psi(y, x, At, b, sigma, lam1, lam2)

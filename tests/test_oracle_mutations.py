@@ -176,3 +176,43 @@ def test_mutant_mxm_branch_without_kappa(monkeypatch):
         return -sla.cho_solve(sla.cho_factor(M, lower=True), g)
     monkeypatch.setattr(R, "newton_direction", bad)
     assert not _mxm_branch_ok()
+
+
+def _cg_within_krylov_bound():
+    # V = I + kappa A_J A_J^T has rank(A_J) + 1 distinct eigenvalues: CG needs at most that many steps
+    rng = np.random.default_rng(5)
+    AJt, g = rng.normal(size=(3, 200)), rng.normal(size=200)
+    d, it = R.newton_direction_cg(AJt, g, 0.05, rtol=1e-12)
+    V = np.eye(200) + 0.05 * AJt.T @ AJt
+    return it <= 5 and np.linalg.norm(V @ d + g) <= 1e-11 * np.linalg.norm(g)
+
+
+def _cg_mutant(alpha_fn=None, beta_zero=False):
+    def cg(AJt, g, kappa, rtol=1e-10, maxiter=None, history=None):
+        m = g.size
+        d, res = np.zeros(m), -g.copy()
+        p, rr = res.copy(), res @ res
+        it = 0
+        while np.sqrt(rr) > rtol * np.linalg.norm(g) and it < (10 * m if maxiter is None else maxiter):
+            Vp = p + kappa * (AJt.T @ (AJt @ p))
+            alpha = alpha_fn(rr, p, Vp) if alpha_fn else rr / (p @ Vp)
+            d, res = d + alpha * p, res - alpha * Vp
+            rr_next = res @ res
+            p = res + (0.0 if beta_zero else rr_next / rr) * p
+            rr, it = rr_next, it + 1
+        return d, it
+    return cg
+
+
+def test_unmutated_cg_pin_passes():
+    assert _cg_within_krylov_bound()
+
+
+def test_mutant_cg_step_without_V(monkeypatch):
+    monkeypatch.setattr(R, "newton_direction_cg", _cg_mutant(alpha_fn=lambda rr, p, Vp: rr / (p @ p)))
+    assert not _cg_within_krylov_bound()
+
+
+def test_mutant_cg_without_conjugation(monkeypatch):
+    monkeypatch.setattr(R, "newton_direction_cg", _cg_mutant(beta_zero=True))
+    assert not _cg_within_krylov_bound()
