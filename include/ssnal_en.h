@@ -346,14 +346,15 @@ ssnal_en_status ssnal_en_op_newton(ssnal_en_ctx* ctx, int64_t r, double kappa, c
  *  x, u    device, length n (FP64)
  *  J, wJ   device outputs, capacity n: J ascending (int32), wJ the prox values (FP64)
  *  r       host output: |J|
- *  stream  cudaStream_t to run on (NULL = legacy default stream); the call
- *          synchronises it before returning.
+ *  stream  cudaStream_t to run on (NULL = legacy default stream).
+ * The call is synchronous: it copies r to the host and synchronises `stream`
+ * before returning, so it must not be called while `stream` is being captured
+ * into a CUDA graph.  x, u, J and wJ must live on the current device.
  * Its scratch memory is one fixed array in the library's device code (about
  * 66 KB, kept by every GPU that loads the library until the process exits):
  *  - n above SSNAL_EN_STATIC_MAX_N is rejected with ENOTSUP before any device work;
  *  - the first call on a device looks up the array's device address once
- *    (cudaGetSymbolAddress with that device current); make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress with that device current) and caches it;
  *  - all calls on a device share the array and it keeps the last call's
  *    contents; each call clears what must start at zero, and calls whose GPU
  *    work overlaps (several streams or host threads) race, so the caller must

@@ -7,7 +7,8 @@ The method (Sec. 3, Algorithm 1) is an augmented Lagrangian (AL) method on the
 dual (D): min_{y,z} h*(y) + p*(z) s.t. A^T y + z = 0, whose inner sub-problem is
 solved by a semi-smooth Newton (SsN) method on psi(y) (Prop. 2).
 
-Readings of points the paper leaves open (each used identically by the CUDA path):
+Readings of points the paper leaves open (the CUDA path takes the same readings; the
+conjugate-gradient branch below applies only where the device supports CG solves):
   * grad h*(y) = y + b  (Sec. 3 writes "y - b" once, "y + b" twice; h*(y) = 1/2||y||^2 + b^T y).
   * x^0 = 0 or the warm start, y^0 = A x^0 - b, sigma^0 = 5e-3 grown x5 per AL
     iteration and capped at sigma_max (Sec. 4.1; Algorithm 1 step (2)).

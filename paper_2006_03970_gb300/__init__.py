@@ -427,10 +427,22 @@ def ssnal_en_profile(ctx, enable, reset: bool = False, phases: bool = False):
 
 def ssnal_en_prox_active_static(x, u, sigma, lambda1, lambda2, J, wJ, stream=None) -> int:
     """Allocation-free prox / active-set step (no context; see the header for the
-    limits and the shared-scratch rules).  x, u: FP64 device tensors of length n;
-    J (int32), wJ (FP64): device outputs of capacity n.  Returns |J|."""
+    limits and the shared-scratch rules).  x, u: FP64 device tensors of length n on the
+    current device; J (int32), wJ (FP64): device outputs of capacity n.  Synchronous:
+    do not call it while the stream is being captured.  Returns |J|."""
+    import torch
+    n = int(x.numel())
+    for name, t, dt in (("x", x, torch.float64), ("u", u, torch.float64), ("J", J, torch.int32),
+                        ("wJ", wJ, torch.float64)):
+        if t.dtype != dt or not t.is_contiguous() or t.device.type != "cuda":
+            raise ValueError(f"ssnal_en_prox_active_static: {name} must be a contiguous CUDA {dt} tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"ssnal_en_prox_active_static: {name} is on {t.device}, the current device is "
+                             f"cuda:{torch.cuda.current_device()} (the scratch address is per device)")
+    if u.numel() != n or J.numel() < n or wJ.numel() < n:
+        raise ValueError("ssnal_en_prox_active_static: u needs n entries, J and wJ at least n")
     r = ctypes.c_int64(0)
-    _check(load_library().ssnal_en_prox_active_static(_ptr(x), _ptr(u), int(x.numel()), float(sigma),
+    _check(load_library().ssnal_en_prox_active_static(_ptr(x), _ptr(u), n, float(sigma),
                                                       float(lambda1), float(lambda2), _ptr(J), _ptr(wJ),
                                                       ctypes.byref(r), _stream_handle(stream)),
            "ssnal_en_prox_active_static")

@@ -68,3 +68,22 @@ def test_solve_with_cg_forced_on_matches_coordinate_descent():
     assert r.converged
     assert np.abs(r.x - xc).max() <= 1e-6 * np.abs(xc).max()
     assert np.array_equal(np.flatnonzero(r.x), np.flatnonzero(xc))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fit_with_cg_near_the_switch_matches_the_direct_solve(seed):
+    # a lowered threshold sends some Newton steps of one fit to CG and others to the
+    # direct solve (r crosses the threshold); both fits meet the KKT tolerance and
+    # reach the same objective and support
+    p = synth.make_problem(60, 300, k=8, seed=40 + seed, block=10, rho=0.6)
+    l1, l2 = R.lambdas(p.At, p.b, 0.6, 0.2)
+    direct = R.solve(p.At, p.b, l1, l2, opts=R.Options(tol=1e-8))
+    mixed = R.solve(p.At, p.b, l1, l2, opts=R.Options(tol=1e-8, cg_above=50, cg_rtol=1e-12))
+    assert max(direct.r_history) > 50 >= min(direct.r_history)  # m = 60: the threshold is crossed
+    for res in (direct, mixed):
+        assert res.converged and res.kkt1 <= 1e-8 and res.kkt3 <= 1e-8
+    Pd = C.primal_objective(p.At, p.b, direct.x, l1, l2)
+    Pm = C.primal_objective(p.At, p.b, mixed.x, l1, l2)
+    assert abs(Pd - Pm) <= 1e-10 * max(1.0, abs(Pd))
+    assert np.abs(direct.x - mixed.x).max() <= 1e-6 * np.abs(direct.x).max()
+    assert np.array_equal(np.flatnonzero(direct.x), np.flatnonzero(mixed.x))

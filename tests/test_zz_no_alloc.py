@@ -69,3 +69,31 @@ def test_static_prox_active_rejects_sizes_beyond_its_scratch(lib):
                                          pkg.STATIC_MAX_N + 1, 1.0, 1.0, 1.0, ctypes.c_void_p(J.data_ptr()),
                                          ctypes.c_void_p(x.data_ptr()), ctypes.byref(r), None)
     assert st == pkg.ENOTSUP and r.value == -1
+
+
+@pytest.mark.parametrize("n", [1, 257, 100_003, 2_097_152])
+def test_static_prox_active_matches_the_oracle(lib, n):
+    # against the definitions themselves (eq. Q_def, eq. prox_elastic): J bit-exact and
+    # ascending, w_J with the same rounding sequence as the elementwise definition
+    from oracle import ssnal_en_ref as R
+    x, u = _case(n, 100 + n)
+    sigma, l1, l2 = 0.37, 2.1, 0.8
+    J = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    wJ = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    r = pkg.ssnal_en_prox_active_static(torch.as_tensor(x, device="cuda"), torch.as_tensor(u, device="cuda"),
+                                        sigma, l1, l2, J, wJ)
+    v = x - sigma * u
+    Jo = R.active_set(v, sigma, l1)
+    assert r == len(Jo)
+    np.testing.assert_array_equal(J[:r].cpu().numpy(), Jo)
+    np.testing.assert_array_equal(wJ[:r].cpu().numpy(), R.prox_sigma_p(v, sigma, l1, l2)[Jo])
+
+
+def test_static_prox_active_checks_its_tensors(lib):
+    x = torch.zeros(16, dtype=torch.float64, device="cuda")
+    J = torch.zeros(8, dtype=torch.int32, device="cuda")
+    wJ = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):  # J shorter than n
+        pkg.ssnal_en_prox_active_static(x, x, 1.0, 1.0, 1.0, J, wJ)
+    with pytest.raises(ValueError):  # wrong dtype
+        pkg.ssnal_en_prox_active_static(x.float(), x, 1.0, 1.0, 1.0, J, wJ)
