@@ -42,8 +42,12 @@ typedef enum {
   SSNAL_EN_F64 = 0,      /* double */
   SSNAL_EN_F32 = 1,      /* float */
   SSNAL_EN_BF16 = 2,     /* bfloat16 bit patterns (uint16) */
-  SSNAL_EN_I8_GENO = 3   /* int8 codes; entry = (code - col_mean[j]) * col_scale[j], evaluated in FP64
+  SSNAL_EN_I8_GENO = 3,  /* int8 codes; entry = (code - col_mean[j]) * col_scale[j], evaluated in FP64
                             from the FP32 mean and scale (standardization applied on the fly) */
+  SSNAL_EN_I2_GENO = 4   /* 2-bit genotype codes 0..3, four per byte: row i of column j is bits
+                            2 (i mod 4) and 2 (i mod 4) + 1 of byte (j lda + i) / 4; lda counts codes
+                            and must be a multiple of 64 (a column stride of whole 16-byte units);
+                            entries as for I8_GENO */
 } ssnal_en_dtype;
 
 typedef enum {
@@ -90,13 +94,27 @@ typedef struct {
                            With BF16 / FP32 / I8_GENO storage and precision 0, 2 or 3 every pass over A
                            is float-float (products of the stored values are exact). */
   int32_t refine_steps; /* 1: iterative-refinement steps of the Newton solve (FP64 residual through
-                           the packed A_J, FP32 factor) */
+                           the packed A_J, FP32 factor).  The first correction also measures the
+                           FP32 solve's relative error: above 1e-2 (the refinement would not
+                           contract) the Newton step is redone with the FP64 system, see newton_fp64 */
   int32_t use_y0;       /* 0: y0 = A x0 - b; 1: take y0 from the y argument of ssnal_en_solve */
   int32_t ls_fused;     /* 16: trial steps evaluated inside the A^T d pass (1..16); later trials
                            are evaluated by a pass over the stored n-vectors only */
   int32_t syrk_tc;      /* 1: Newton-matrix SYRK on the tensor cores (tcgen05, BF16 operands, FP32
                            accumulation; FP64 panels as a three-way BF16 split); 0: FP32 FMA */
   int64_t max_active;   /* 0: path stops after the first point with at least this many nonzeros (0 = never) */
+  int32_t newton_fp64;  /* Newton system of eqs. AJ_system / smw_formula:
+                           0: formed and factored in FP32 with FP64 refinement; when that factor meets
+                              a non-positive pivot or its refinement does not contract, the step is not
+                              taken and its direction is recomputed with the Newton matrix formed,
+                              factored (Cholesky) and solved in FP64, and the rest of that fit stays
+                              on the FP64 system;
+                           1: always the FP64 system */
+  int32_t cg_maxit;     /* 0: CG iterations per Newton solve at most 10 m (see cg_above) */
+  int64_t cg_above;     /* 10000: the Newton system is solved by conjugate gradients (matrix-free,
+                           V p = p + kappa A_J (A_J^T p)) when m and r both exceed this (Algorithm 1
+                           step (1), Sec. 3.2); 0 < cg_above < 10000 moves the switch */
+  double cg_rtol;       /* 1e-10: CG stops at ||V d + g|| <= cg_rtol ||g|| (the paper gives no tolerance) */
 } ssnal_en_options;
 
 /* Per-fit report. */
@@ -113,6 +131,8 @@ typedef struct {
   double seconds;        /* wall time of the fit on the host clock */
   double sigma;          /* sigma of the last AL iteration */
   double lambda1, lambda2;
+  int32_t newton_fp64;   /* Newton directions computed with the FP64 system (see ssnal_en_options) */
+  int32_t cg_iters;      /* conjugate-gradient iterations (all Newton solves) */
 } ssnal_en_result;
 
 /* Fills *opts with the defaults listed above. */
@@ -177,7 +197,8 @@ ssnal_en_status ssnal_en_path_host(ssnal_en_ctx* ctx, const double* b_host, doub
  * summed as they complete.
  *  enable  1: record around every eighth launch from now on (the first, the
  *          ninth, ...: a recorded launch loses its overlap with the kernels
- *          beside it, so level 1 keeps that cost to one launch in eight),
+ *          beside it, so level 1 keeps that cost to one launch in eight), and
+ *          around every u = A^T y pass (phase 4 of ssnal_en_profile_phases),
  *          2: record around every launch and also the phases of
  *          ssnal_en_profile_phases (more events on the host's path between
  *          kernels), 0: stop recording.
@@ -193,15 +214,19 @@ ssnal_en_status ssnal_en_profile(ssnal_en_ctx* ctx, int32_t enable, int32_t rese
 
 /* Per-phase device time since the last ssnal_en_profile(reset = 1), recorded
  * while profiling is enabled at level 2 (level 1 records one launch in eight of
- * phase 2 only).  Four
- * phases, in this order:
+ * phase 2 and every launch of phase 4 only).  Five phases, in this order:
  *  0 prox + active set + gather + gradient (eqs. prox_elastic, Q_def, grad_phy)
- *  1 Newton direction: SYRK, Cholesky, solves and refinement (eqs. AJ_system, smw_formula)
+ *  1 Newton direction: SYRK, Cholesky, solves and refinement, or the CG iterations
+ *    (eqs. AJ_system, smw_formula)
  *  2 the pass over A with the fused line search (eq. line_search)
  *  3 the multiplier update x <- prox(x - sigma A^T y) (eq. update_x)
- * phase_ms, phase_count: host arrays of 4 (either may be NULL).  Time on the
- * stream outside these phases (host round trips) is not attributed.
+ *  4 the passes u = A^T y at the start of a fit and before SsN stopping tests of the
+ *    mixed precision mode (float-float over the stored values; Prop. 2)
+ * phase_ms, phase_count: host arrays of SSNAL_EN_PROFILE_PHASES (either may be
+ * NULL).  Time on the stream outside these phases (host round trips) is not
+ * attributed.
  * Synchronises the stream.  Errors: EINVAL (null ctx), ECUDA. */
+#define SSNAL_EN_PROFILE_PHASES 5
 ssnal_en_status ssnal_en_profile_phases(ssnal_en_ctx* ctx, double* phase_ms, int64_t* phase_count);
 
 /* ---------------------------------------------------------------------------

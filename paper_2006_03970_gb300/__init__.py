@@ -17,7 +17,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "F64", "F32", "BF16", "I8_GENO", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
+    "F64", "F32", "BF16", "I8_GENO", "I2_GENO", "pack_codes_2bit", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
     "ssnal_en_solve_batch", "Instance", "Server", "ssnal_en_server_create", "ssnal_en_server_submit",
@@ -31,7 +31,7 @@ __all__ = [
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libssnal_en.so")
 
-F64, F32, BF16, I8_GENO = 0, 1, 2, 3
+F64, F32, BF16, I8_GENO, I2_GENO = 0, 1, 2, 3, 4
 OK, EINVAL, ENOMEM, ENOCONV, ECUDA, ETIMEOUT, ENOTSUP = range(7)
 _ELEM = {F64: 8, F32: 4, BF16: 2, I8_GENO: 1}
 STATIC_MAX_N = 2097152  # SSNAL_EN_STATIC_MAX_N
@@ -54,7 +54,9 @@ class Options(ctypes.Structure):
                 ("mu", ctypes.c_double), ("beta", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_al", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("max_ls", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("refine_steps", ctypes.c_int32), ("use_y0", ctypes.c_int32),
-                ("ls_fused", ctypes.c_int32), ("syrk_tc", ctypes.c_int32), ("max_active", ctypes.c_int64)]
+                ("ls_fused", ctypes.c_int32), ("syrk_tc", ctypes.c_int32), ("max_active", ctypes.c_int64),
+                ("newton_fp64", ctypes.c_int32), ("cg_maxit", ctypes.c_int32), ("cg_above", ctypes.c_int64),
+                ("cg_rtol", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):
@@ -72,7 +74,7 @@ class Result(ctypes.Structure):
                 ("ls_trials", ctypes.c_int32), ("active", ctypes.c_int64), ("kkt1", ctypes.c_double),
                 ("kkt3", ctypes.c_double), ("primal_obj", ctypes.c_double), ("dual_gap", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("sigma", ctypes.c_double), ("lambda1", ctypes.c_double),
-                ("lambda2", ctypes.c_double)]
+                ("lambda2", ctypes.c_double), ("newton_fp64", ctypes.c_int32), ("cg_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -178,11 +180,30 @@ def ssnal_en_default_options(**overrides) -> Options:
 default_options = ssnal_en_default_options
 
 
+def pack_codes_2bit(codes: np.ndarray) -> np.ndarray:
+    """Packs genotype codes 0..3 of a feature-major (n, m) array four per byte in the
+    SSNAL_EN_I2_GENO layout: returns (n, lda / 4) uint8 with lda = m rounded up to 64,
+    row i of column j in bits 2 (i mod 4), 2 (i mod 4) + 1 of byte i / 4 of that column
+    (rows past m hold code 0)."""
+    c = np.asarray(codes)
+    n, m = c.shape
+    if c.size and (c.min() < 0 or c.max() > 3):
+        raise ValueError("2-bit codes must lie in 0..3")
+    lda = (m + 63) // 64 * 64
+    full = np.zeros((n, lda), dtype=np.uint8)
+    full[:, :m] = c
+    q = full.reshape(n, lda // 4, 4)
+    return (q[:, :, 0] | (q[:, :, 1] << 2) | (q[:, :, 2] << 4) | (q[:, :, 3] << 6)).astype(np.uint8)
+
+
 def device_matrix(At: np.ndarray, dtype: int = F64, device="cuda"):
     """Copies a feature-major (n, m) array (== column-major A) to the device with a
-    16-byte-aligned leading dimension; returns (tensor of shape (n, lda), m)."""
+    16-byte-aligned leading dimension; returns (tensor of shape (n, lda), m).  For
+    I2_GENO, At holds the codes 0..3 and the tensor the packed bytes (n, lda / 4)."""
     import torch
     n, m = At.shape
+    if dtype == I2_GENO:
+        return torch.from_numpy(pack_codes_2bit(At)).to(device), m
     es = _ELEM[dtype]
     q = 16 // es
     lda = (m + q - 1) // q * q
@@ -207,8 +228,10 @@ def device_matrix(At: np.ndarray, dtype: int = F64, device="cuda"):
 
 def ssnal_en_create(A, m: int, dtype: int = F64, options: Options | None = None, stream=None,
                     col_mean=None, col_scale=None):
-    """A: device tensor (n, lda) holding column-major A.  Returns an opaque context handle."""
-    mat = Matrix(m=m, n=A.shape[0], lda=A.shape[1], dtype=dtype, reserved=0, data=A.data_ptr(),
+    """A: device tensor (n, lda) holding column-major A ((n, lda / 4) packed bytes for
+    I2_GENO).  Returns an opaque context handle."""
+    lda = A.shape[1] * 4 if dtype == I2_GENO else A.shape[1]
+    mat = Matrix(m=m, n=A.shape[0], lda=lda, dtype=dtype, reserved=0, data=A.data_ptr(),
                  col_mean=col_mean.data_ptr() if col_mean is not None else None,
                  col_scale=col_scale.data_ptr() if col_scale is not None else None)
     ctx = ctypes.c_void_p()
@@ -254,7 +277,8 @@ def ssnal_en_server_create(mats, workers=8, options: Options | None = None, max_
     """mats: list of (device tensor (n, lda), m, dtype, col_mean, col_scale).  Returns a handle."""
     arr = (Matrix * len(mats))()
     for k, (A, m, dtype, cm, cs) in enumerate(mats):
-        arr[k] = Matrix(m=m, n=A.shape[0], lda=A.shape[1], dtype=dtype, reserved=0, data=A.data_ptr(),
+        lda = A.shape[1] * 4 if dtype == I2_GENO else A.shape[1]
+        arr[k] = Matrix(m=m, n=A.shape[0], lda=lda, dtype=dtype, reserved=0, data=A.data_ptr(),
                         col_mean=cm.data_ptr() if cm is not None else None,
                         col_scale=cs.data_ptr() if cs is not None else None)
     h = ctypes.c_void_p()
@@ -401,15 +425,16 @@ def ssnal_en_op_newton(ctx, r, kappa, g, d):
                   "ssnal_en_op_newton", allow=(OK, ENOCONV))
 
 
-PHASES = ("prox_gather_grad", "newton_direction", "stream_line_search", "al_update")
+PHASES = ("prox_gather_grad", "newton_direction", "stream_line_search", "al_update", "u_refresh")
+PROFILE_PHASES = 5  # SSNAL_EN_PROFILE_PHASES
 
 
 def ssnal_en_profile_phases(ctx):
     """Device ms and counts per phase (see PHASES) since the last profile reset."""
-    ms = (ctypes.c_double * 4)()
-    n = (ctypes.c_int64 * 4)()
+    ms = (ctypes.c_double * PROFILE_PHASES)()
+    n = (ctypes.c_int64 * PROFILE_PHASES)()
     _check(load_library().ssnal_en_profile_phases(ctx, ms, n), "ssnal_en_profile_phases")
-    return {PHASES[k]: (ms[k], n[k]) for k in range(4)}
+    return {PHASES[k]: (ms[k], n[k]) for k in range(PROFILE_PHASES)}
 
 
 def ssnal_en_profile(ctx, enable, reset: bool = False, phases: bool = False):

@@ -20,7 +20,8 @@
 using namespace ssnal;
 
 // Phases timed by ssnal_en_profile_phases.
-enum { kPhaseGrad = 0, kPhaseNewton = 1, kPhaseStream = 2, kPhaseUpdate = 3, kPhases = 4 };
+enum { kPhaseGrad = 0, kPhaseNewton = 1, kPhaseStream = 2, kPhaseUpdate = 3, kPhaseRefresh = 4, kPhases = 5 };
+static_assert(kPhases == SSNAL_EN_PROFILE_PHASES, "phase count in the header");
 
 struct ssnal_en_ctx {
   int64_t m = 0, n = 0, lda = 0;
@@ -65,6 +66,11 @@ struct ssnal_en_ctx {
   float* G = nullptr;
   int64_t ldg = 0;
   float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
+  int last_wdiag = 0;      // the last FP32 factor wrote Wdiag
+  double* corr = nullptr;  // first refinement correction (capacity max(m, rcap))
+  double* cgp = nullptr;   // search direction of the CG Newton solve (m)
+  double* G64 = nullptr;   // FP64 Newton matrix / factor, allocated on first use (m x m)
+  int64_t ldg64 = 0;
   float* tuneS = nullptr;  // tuning: factor and identity for tr(G^{-1}) (2 Np x Np), allocated on first use
   double* tune_dev = nullptr;  // tuning: per-column-block partial sums and the result
   void* Xtc = nullptr;     // BF16 split panels of the tensor-core SYRK (capacity rcap)
@@ -86,15 +92,18 @@ namespace {
 
 int64_t round_up(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
-size_t elem_size(int dtype) {
+// Bytes per stored entry of A (a quarter for 2-bit codes), 0 for an unknown type.
+double elem_bytes(int dtype) {
   switch (dtype) {
     case SSNAL_EN_F64: return 8;
     case SSNAL_EN_F32: return 4;
     case SSNAL_EN_BF16: return 2;
     case SSNAL_EN_I8_GENO: return 1;
+    case SSNAL_EN_I2_GENO: return 0.25;
     default: return 0;
   }
 }
+bool is_geno(int dtype) { return dtype == SSNAL_EN_I8_GENO || dtype == SSNAL_EN_I2_GENO; }
 
 #define CK(call)                                  \
   do {                                            \
@@ -120,10 +129,14 @@ void dev_free(void* p) {
 }
 
 // Panel capacity: r columns of m rows (FP64 and FP32 copies) plus r-space vectors.
+// Capacity grows by doubling while the panel is small next to the m x m system; beyond
+// 4 m columns (A_J then holds many times the bytes of the Newton matrix) it grows to the
+// need plus an eighth, so that a panel of 1e5 columns does not reserve twice that.
 ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
   if (need <= c->rcap) return SSNAL_EN_OK;
   int64_t cap = c->rcap > 0 ? c->rcap : 256;
   while (cap < need) cap *= 2;
+  if (need > 4 * c->m) cap = (need + need / 8 + 63) / 64 * 64;
   if (cap > c->n) cap = c->n;
   if (cap < need) cap = need;
   cudaStreamSynchronize(c->stream);
@@ -133,6 +146,8 @@ ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
   dev_free(c->q);
   dev_free(c->resr);
   dev_free(c->Xtc);
+  dev_free(c->corr);
+  c->corr = nullptr;
   c->P = nullptr;
   c->P32 = nullptr;
   c->Xtc = nullptr;
@@ -144,6 +159,7 @@ ssnal_en_status grow_panel(ssnal_en_ctx* c, int64_t need) {
   if ((s = dev_alloc(&c->h, (size_t)cap)) != SSNAL_EN_OK) return s;
   if ((s = dev_alloc(&c->q, (size_t)cap)) != SSNAL_EN_OK) return s;
   if ((s = dev_alloc(&c->resr, (size_t)cap)) != SSNAL_EN_OK) return s;
+  if ((s = dev_alloc(&c->corr, (size_t)(cap > c->m ? cap : c->m))) != SSNAL_EN_OK) return s;
   {
     // both orientations fit in 3 x m x round_up(max(m, cap), 64) BF16 entries
     const int64_t big = c->m > cap ? c->m : cap;
@@ -196,6 +212,9 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->P32);
   dev_free(c->G);
   dev_free(c->Wdiag);
+  dev_free(c->corr);
+  dev_free(c->cgp);
+  dev_free(c->G64);
   dev_free(c->tuneS);
   dev_free(c->tune_dev);
   dev_free(c->Xtc);
@@ -297,8 +316,9 @@ struct PhaseTimer {
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   int phase;
   PhaseTimer(ssnal_en_ctx* c_, int ph, bool on = true) : c(c_), phase(ph) {
-    // level 1 times the passes over A only (few events on the host's path)
-    if (!on || !c->prof || (ph != kPhaseStream && c->prof < 2)) {
+    // level 1 times the passes over A only: one A^T d pass in kProfEvery and every
+    // u = A^T y pass (a few per fit)
+    if (!on || !c->prof || (ph != kPhaseStream && ph != kPhaseRefresh && c->prof < 2)) {
       c = nullptr;
       return;
     }
@@ -368,6 +388,7 @@ int lane_elt(const ssnal_en_ctx* c, int mode) {
   if (c->dtype == SSNAL_EN_BF16) return plain ? kLaneBf16 : kLaneBf16FF;
   if (c->dtype == SSNAL_EN_F32) return plain ? kLaneF32 : kLaneF32FF;
   if (c->dtype == SSNAL_EN_I8_GENO) return plain ? kLaneI8 : kLaneI8FF;
+  if (c->dtype == SSNAL_EN_I2_GENO) return plain ? kLaneI2 : kLaneI2FF;
   return kLaneSplit;
 }
 
@@ -402,7 +423,7 @@ ssnal_en_status stream_t(ssnal_en_ctx* c, const double* x, ProxParams pp) {
   }
   if (timed) {
     c->prof_launches++;
-    const double es = (double)elem_size(c->dtype);
+    const double es = elem_bytes(c->dtype);
     c->prof_bytes += (double)c->m * (double)c->n * es + 3.0 * 8.0 * (double)c->n + 8.0 * (double)c->m;
   }
   return SSNAL_EN_OK;
@@ -452,15 +473,27 @@ ssnal_en_status prox_gather_grad(ssnal_en_ctx* c, int mode, const double* x, con
   return SSNAL_EN_OK;
 }
 
+// Contraction test of the FP32 solve.  The first refinement correction relative to the
+// refined solution, rho, estimates the relative error of the FP32 solve and the factor by
+// which each refinement step shrinks it (the error of the FP32 factor of a matrix formed
+// with FP32 accumulation is of the order of cond(G) 2^-24, times a growth with the
+// accumulation length).  rho > kRefineTau: the refinement does not contract and the
+// Newton step is redone with the FP64 system.  rho > kRefineMore: the direction is still
+// usable (its error after one step is about rho^2) but later steps of the fit take one
+// more refinement step (at most kRefineExtraMax more).
+constexpr double kRefineTau = 0.5;
+constexpr double kRefineMore = 1e-2;
+constexpr int kRefineExtraMax = 2;
+
 // Newton direction d for (I + kappa A_J A_J^T) d = -g on the gathered panel:
 // FP32 SYRK and Cholesky factor of the Newton matrix, FP64 residuals through
 // the panel (iterative refinement), and the dot products the line search needs.
 ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d,
-                                 const double* yv, const double* bv, int dots) {
+                                 const double* yv, const double* bv, int dots, int extra_refine = 0) {
   cudaStream_t s = c->stream;
   PhaseTimer timer(c, kPhaseNewton);
   const int m = (int)c->m;
-  const int refine = c->opt.refine_steps > 0 ? c->opt.refine_steps : 0;
+  const int refine = (c->opt.refine_steps > 0 ? c->opt.refine_steps : 0) + extra_refine;
   const int which = dots ? 2 : 0;
   const float* wd = nullptr;  // inverse diagonal blocks of the factor, when available
   if (r == 0) {
@@ -477,8 +510,10 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
     launch_gemv_t(c->P, c->ldp, m, r, g, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
     if (N <= kSmallNewton) {
       launch_chol_solve_small(c->G, c->ldg, N, c->st, c->h, c->q, 1.0, s);
+      c->last_wdiag = 0;
     } else {
       wd = chol_factor(c->G, c->ldg, N, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
+      c->last_wdiag = wd != nullptr;
       launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, wd, c->st, s);
     }
     for (int it = 0; it < refine; it++) {
@@ -486,7 +521,12 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->tmpm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr,
                     nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
       launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
-      launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, wd, c->st, s);
+      if (it == 0) {  // the first correction is the FP32 solve's error: test the contraction
+        launch_trsv_llt(c->G, c->ldg, N, c->resr, c->corr, 1, 1.0, wd, c->st, s);
+        launch_refine_update(c->q, c->corr, N, kRefineTau, c->st, s);
+      } else {
+        launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, wd, c->st, s);
+      }
     }
     launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, which, yv, bv, g, c->st,
                   c->comb_scratch, c->cpart, c->tile_ctr, s);
@@ -500,8 +540,10 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_syrk_nt(c->P32, c->ldp32, m, r, kappa, c->G, c->ldg, s);
     if (m <= kSmallNewton) {
       launch_chol_solve_small(c->G, c->ldg, m, c->st, g, d, -1.0, s);
+      c->last_wdiag = 0;
     } else {
       wd = chol_factor(c->G, c->ldg, m, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
+      c->last_wdiag = wd != nullptr;
       launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, wd, c->st, s);
     }
     for (int it = 0; it < refine; it++) {
@@ -509,12 +551,143 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
       launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
                     nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
-      launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, wd, c->st, s);
+      if (it == 0) {
+        launch_trsv_llt(c->G, c->ldg, m, c->tmpm, c->corr, 1, 1.0, wd, c->st, s);
+        launch_refine_update(d, c->corr, m, kRefineTau, c->st, s);
+      } else {
+        launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, wd, c->st, s);
+      }
     }
     if (dots)
       launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);
   }
   CK(cudaGetLastError());
+  return SSNAL_EN_OK;
+}
+
+// One more refinement step of the last FP32 solve (same panel, factor and g): the FP64
+// residual through the panel, an FP32 correction and the contraction test.  The
+// solution is q (r-space, SMW form) or d (m x m form).
+ssnal_en_status refine_once(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d) {
+  cudaStream_t s = c->stream;
+  const int m = (int)c->m;
+  const float* wd = c->last_wdiag ? c->Wdiag : nullptr;
+  if (r == 0) return SSNAL_EN_OK;
+  if (r < m) {
+    const int N = (int)r;
+    launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->tmpm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr,
+                  nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
+    launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
+    launch_trsv_llt(c->G, c->ldg, N, c->resr, c->corr, 1, 1.0, wd, c->st, s);
+    launch_refine_update(c->q, c->corr, N, kRefineTau, c->st, s);
+    launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, 0, nullptr, nullptr,
+                  nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
+  } else {
+    launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
+    launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
+                  nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
+    launch_trsv_llt(c->G, c->ldg, m, c->tmpm, c->corr, 1, 1.0, wd, c->st, s);
+    launch_refine_update(d, c->corr, m, kRefineTau, c->st, s);
+  }
+  CK(cudaGetLastError());
+  return SSNAL_EN_OK;
+}
+
+// The FP64 Newton matrix (m x m doubles), allocated the first time a context needs it.
+ssnal_en_status ensure_g64(ssnal_en_ctx* c) {
+  if (c->G64) return SSNAL_EN_OK;
+  c->ldg64 = round_up(c->m, 2);
+  return dev_alloc(&c->G64, (size_t)c->ldg64 * (size_t)c->m);
+}
+
+// Newton direction with the FP64 system: the Newton matrix of eq. smw_formula (r < m) or
+// eq. AJ_system (r >= m) formed from the FP64 panel with FP64 FMAs, its FP64 Cholesky
+// factor and FP64 triangular solves (kern_f64.cu); then the same final GEMV and scalar
+// products as the FP32 path.  A non-positive FP64 pivot sets DevState::f64_fail.
+ssnal_en_status newton_direction_f64(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d,
+                                     const double* yv, const double* bv, int dots) {
+  cudaStream_t s = c->stream;
+  ssnal_en_status e = ensure_g64(c);
+  if (e != SSNAL_EN_OK) return e;
+  PhaseTimer timer(c, kPhaseNewton);
+  const int m = (int)c->m;
+  const int which = dots ? 2 : 0;
+  if (r == 0) {
+    launch_gemv_n(c->P, c->ldp, m, c->wJ, c->st, 0, c->rcap, d, nullptr, 0.0, g, -1.0, 0.0, which, yv, bv, g, c->st,
+                  c->comb_scratch, c->cpart, c->tile_ctr, s);
+  } else if (r < m) {
+    // G = kappa^{-1} I + A_J^T A_J, h = A_J^T g, q = G^{-1} h, d = A_J q - g
+    const int N = (int)r;
+    launch_syrk64(c->P, c->ldp, m, N, 0, 1.0 / kappa, 1.0, c->G64, c->ldg64, c->st, s);
+    launch_gemv_t(c->P, c->ldp, m, r, g, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
+    chol64(c->G64, c->ldg64, N, c->st, s);
+    launch_trsv64(c->G64, c->ldg64, N, c->h, c->q, 1, 1.0, c->st, s);
+    launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, which, yv, bv, g, c->st,
+                  c->comb_scratch, c->cpart, c->tile_ctr, s);
+  } else {
+    // M = I + kappa A_J A_J^T, d = -M^{-1} g
+    launch_syrk64(c->P, c->ldp, m, (int)r, 1, 1.0, kappa, c->G64, c->ldg64, c->st, s);
+    chol64(c->G64, c->ldg64, m, c->st, s);
+    launch_trsv64(c->G64, c->ldg64, m, g, d, 1, -1.0, c->st, s);
+    if (dots)
+      launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);
+  }
+  CK(cudaGetLastError());
+  return SSNAL_EN_OK;
+}
+
+// True when the Newton system of this step is solved by conjugate gradients: m and r both
+// above options.cg_above (Algorithm 1 step (1); Sec. 3.2 proposes CG when both exceed 1e4).
+bool use_cg(const ssnal_en_ctx* c, int64_t r) { return c->m > c->opt.cg_above && r > c->opt.cg_above; }
+
+constexpr int kCgBatch = 8;  // CG iterations launched between two reads of the state
+
+// Newton direction by conjugate gradients on (I + kappa A_J A_J^T) d = -g, matrix-free
+// (V p = p + kappa A_J (A_J^T p) by the panel GEMV pair), FP64 throughout.  The scalars
+// stay on the device; the host reads the state once per kCgBatch iterations and stops
+// at the stopping test or after cg_maxit (default 10 m) iterations.  *iters receives
+// the iteration count.
+ssnal_en_status newton_direction_cg(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d,
+                                    const double* yv, const double* bv, int dots, int* iters) {
+  cudaStream_t s = c->stream;
+  const int m = (int)c->m;
+  const int64_t maxit = c->opt.cg_maxit > 0 ? c->opt.cg_maxit : 10 * c->m;
+  {
+    PhaseTimer timer(c, kPhaseNewton);
+    launch_cg_init(g, d, c->res, c->cgp, m, c->opt.cg_rtol, c->st, s);
+  }
+  CK(cudaGetLastError());
+  int64_t launched = 0;
+  for (;;) {
+    const int64_t batch = maxit - launched < kCgBatch ? maxit - launched : kCgBatch;
+    {
+      PhaseTimer timer(c, kPhaseNewton);
+      for (int64_t k = 0; k < batch; k++) {
+        // tmpm = p + kappa A_J (A_J^T p)
+        launch_gemv_t(c->P, c->ldp, m, r, c->cgp, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
+        launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, c->cgp, 1.0, nullptr, 0.0, kappa, 0,
+                      nullptr, nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
+        launch_cg_step(d, c->res, c->cgp, c->tmpm, m, c->st, s);
+      }
+    }
+    CK(cudaGetLastError());
+    launched += batch;
+    ssnal_en_status e = read_state(c);
+    if (e != SSNAL_EN_OK) return e;
+    if (c->st_host->cg_done || launched >= maxit) break;
+  }
+  *iters = c->st_host->cg_iters;
+  if (dots) {
+    PhaseTimer timer(c, kPhaseNewton);
+    launch_combine(d, nullptr, 0.0, d, 1.0, nullptr, 0.0, m, 2, yv, bv, g, c->st, c->comb_scratch, s);
+  }
+  CK(cudaGetLastError());
+  return SSNAL_EN_OK;
+}
+
+// Clears DevState::chol_fail, newton_bad and f64_fail (contiguous).
+ssnal_en_status clear_newton_flags(ssnal_en_ctx* c) {
+  CK(cudaMemsetAsync(&c->st->chol_fail, 0, 3 * sizeof(int32_t), c->stream));
   return SSNAL_EN_OK;
 }
 
@@ -548,11 +721,19 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
   } else {
     if ((e = prox_gather_grad(c, kProxSupport, x, c->bdev, pp, 0)) != SSNAL_EN_OK) return e;
   }
-  run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
+  {
+    PhaseTimer timer(c, kPhaseRefresh);
+    run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
+  }
   CK(cudaGetLastError());
   double sigma = o.sigma0;
   int converged = 0, failed = 0;
   int al = 0;
+  // Newton systems in FP64: always on request; otherwise from the first step whose FP32
+  // factor failed or whose refinement did not contract to the end of this fit (sigma
+  // only grows within a fit, so the FP32 system would not recover).
+  bool use_f64 = o.newton_fp64 == 1;
+  int extra_refine = 0;  // refinement steps added after a slowly contracting FP32 solve
   double kkt1 = INFINITY, kkt3 = INFINITY;
   for (al = 1; al <= o.max_al; al++) {
     pp = make_pp(sigma, lam1, lam2);
@@ -565,17 +746,28 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
       const DevState& h = *c->st_host;
       if (apply) R.ls_trials += h.ls_k + 1;
       apply = 0;
-      if (h.chol_fail) {
-        // the FP32 factor of the Newton matrix lost positive definiteness
-        failed = 1;
-        break;
+      if (h.chol_fail | h.newton_bad | h.f64_fail) {
+        // The last direction came from an unreliable FP32 solve (non-positive pivot, or a
+        // refinement that does not contract) or a failed FP64 factor; the prox pass above
+        // did not apply it, so y and u are those of the step before.
+        if (h.f64_fail) {  // the Newton matrix is not positive definite even in FP64
+          failed = 1;
+          break;
+        }
+        if ((e = clear_newton_flags(c)) != SSNAL_EN_OK) return e;
+        use_f64 = true;  // recompute this direction, and the rest of the fit, in FP64
+      } else if (h.refine_ratio > kRefineMore && extra_refine < kRefineExtraMax && c->opt.refine_steps > 0) {
+        extra_refine++;  // the FP32 solve contracts slowly: one more refinement step from now on
       }
       const double gn = sqrt(h.g2) / nb1;
       if (!(gn > o.tol) || newton_here >= o.max_newton) {
         if (!fresh) {
           // mixed precision: recompute u = A^T y in float-float before the SsN
           // stopping test is trusted (the KKT residuals and the x update read u)
-          run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
+          {
+            PhaseTimer timer(c, kPhaseRefresh);
+            run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
+          }
           CK(cudaGetLastError());
           fresh = true;
           continue;
@@ -584,7 +776,16 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
       }
       fresh = !mixed_stream(c);
       const int64_t r = h.r;
-      if ((e = newton_direction(c, r, kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
+      if (use_cg(c, r)) {
+        int it = 0;
+        if ((e = newton_direction_cg(c, r, kappa, c->g, c->d, c->y, c->bdev, 1, &it)) != SSNAL_EN_OK) return e;
+        R.cg_iters += it;
+      } else if (use_f64) {
+        if ((e = newton_direction_f64(c, r, kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
+        R.newton_fp64++;
+      } else if ((e = newton_direction(c, r, kappa, c->g, c->d, c->y, c->bdev, 1, extra_refine)) != SSNAL_EN_OK) {
+        return e;
+      }
       if ((e = stream_t(c, x, pp)) != SSNAL_EN_OK) return e;
       launch_ls_fallback(x, c->u, c->t, c->n, pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st, c->partials,
                          c->grid_stream, s);
@@ -635,12 +836,35 @@ ssnal_en_status check_options(const ssnal_en_options* o) {
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->max_active < 0) return SSNAL_EN_EINVAL;
   if (o->precision < 0 || o->precision > 3) return SSNAL_EN_EINVAL;
   if (o->syrk_tc < 0 || o->syrk_tc > 1) return SSNAL_EN_EINVAL;
+  if (o->newton_fp64 < 0 || o->newton_fp64 > 1 || o->cg_maxit < 0 || o->cg_above < 0) return SSNAL_EN_EINVAL;
+  if (!(o->cg_rtol > 0.0) || !(o->cg_rtol < 1.0)) return SSNAL_EN_EINVAL;
   return SSNAL_EN_OK;
 }
 
 }  // namespace
 
 namespace ssnal {
+// Releases a panel larger than `keep_cols` columns (it is grown again on demand), so that
+// a context kept between requests does not hold the panel of its largest active set.
+void ctx_trim(ssnal_en_ctx* c, int64_t keep_cols) {
+  if (!c || c->rcap <= keep_cols) return;
+  cudaStreamSynchronize(c->stream);
+  dev_free(c->P);
+  dev_free(c->P32);
+  dev_free(c->h);
+  dev_free(c->q);
+  dev_free(c->resr);
+  dev_free(c->Xtc);
+  dev_free(c->corr);
+  c->P = nullptr;
+  c->P32 = nullptr;
+  c->Xtc = nullptr;
+  c->h = c->q = c->resr = c->corr = nullptr;
+  c->rcap = 0;
+  if (grow_panel(c, c->m < c->n ? c->m : c->n) != SSNAL_EN_OK) cudaGetLastError();
+}
+int64_t ctx_m(const ssnal_en_ctx* c) { return c->m; }
+
 // The stream a context enqueues on; the batch and serving drivers give each
 // worker thread its own stream for the duration of one solve.
 cudaStream_t ctx_set_stream(ssnal_en_ctx* c, cudaStream_t s) {
@@ -671,6 +895,10 @@ void ssnal_en_default_options(ssnal_en_options* o) {
   o->ls_fused = kFusedLS;
   o->syrk_tc = 1;
   o->max_active = 0;
+  o->newton_fp64 = 0;
+  o->cg_maxit = 0;
+  o->cg_above = 10000;
+  o->cg_rtol = 1e-10;
 }
 
 const char* ssnal_en_status_string(int32_t s) {
@@ -690,12 +918,14 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
                                 void* stream) {
   if (!out || !A) return SSNAL_EN_EINVAL;
   *out = nullptr;
-  const size_t es = elem_size(A->dtype);
+  const double es = elem_bytes(A->dtype);
   if (es == 0 || !A->data || A->m <= 0 || A->n <= 0 || A->lda < A->m) return SSNAL_EN_EINVAL;
-  if ((A->lda * (int64_t)es) % 16 != 0 || ((uintptr_t)A->data) % 16 != 0) return SSNAL_EN_EINVAL;
+  // the column stride must be whole 16-byte units (2-bit codes: lda a multiple of 64 codes)
+  if (A->dtype == SSNAL_EN_I2_GENO ? (A->lda % 64 != 0) : ((int64_t)(A->lda * es) % 16 != 0)) return SSNAL_EN_EINVAL;
+  if (((uintptr_t)A->data) % 16 != 0) return SSNAL_EN_EINVAL;
   if (A->n >= (int64_t)0x7fffffff) return SSNAL_EN_ENOTSUP;
   if (A->m > kMaxM) return SSNAL_EN_ENOTSUP;
-  if (A->dtype == SSNAL_EN_I8_GENO && (!A->col_mean || !A->col_scale)) return SSNAL_EN_EINVAL;
+  if (is_geno(A->dtype) && (!A->col_mean || !A->col_scale)) return SSNAL_EN_EINVAL;
   ssnal_en_options o;
   if (opts)
     o = *opts;
@@ -740,6 +970,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->bdev, m);
   AL(c->res, m);
   AL(c->tmpm, m);
+  AL(c->cgp, m);
   AL(c->bstage, m);
   AL(c->J, n);
   AL(c->wJ, n);
@@ -946,7 +1177,12 @@ ssnal_en_status ssnal_en_tune(ssnal_en_ctx* c, const double* b, double alpha, co
     } else {
       if ((e = newton_direction(c, r, INFINITY, c->bdev, c->d, c->bdev, c->bdev, 1)) != SSNAL_EN_OK) return e;
       if ((e = read_state(c)) != SSNAL_EN_OK) return e;
-      if (!c->st_host->chol_fail) rss = c->st_host->dd;
+      if (c->st_host->chol_fail | c->st_host->newton_bad) {  // redo the least-squares solve in FP64
+        if ((e = clear_newton_flags(c)) != SSNAL_EN_OK) return e;
+        if ((e = newton_direction_f64(c, r, INFINITY, c->bdev, c->d, c->bdev, c->bdev, 1)) != SSNAL_EN_OK) return e;
+        if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+      }
+      if (!(c->st_host->chol_fail | c->st_host->f64_fail)) rss = c->st_host->dd;
     }
     P.nu = nu;
     P.rss = rss;
@@ -1088,11 +1324,32 @@ ssnal_en_status ssnal_en_op_grad(ssnal_en_ctx* c, const int32_t* J, const double
 ssnal_en_status ssnal_en_op_newton(ssnal_en_ctx* c, int64_t r, double kappa, const double* g, double* d) {
   if (!c || !g || !d || r < 0 || r > c->rcap || !(kappa > 0) || !is_finite_d(kappa)) return SSNAL_EN_EINVAL;
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
-  ssnal_en_status e = newton_direction(c, r, kappa, g, d, nullptr, nullptr, 0);
-  if (e != SSNAL_EN_OK) return e;
-  e = read_state(c);
-  if (e != SSNAL_EN_OK) return e;
-  return c->st_host->chol_fail ? SSNAL_EN_ENOCONV : SSNAL_EN_OK;
+  ssnal_en_status e = SSNAL_EN_OK;
+  if (use_cg(c, r)) {
+    int it = 0;
+    if ((e = newton_direction_cg(c, r, kappa, g, d, nullptr, nullptr, 0, &it)) != SSNAL_EN_OK) return e;
+    return c->st_host->cg_done ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
+  }
+  if (c->opt.newton_fp64 == 0) {
+    if ((e = newton_direction(c, r, kappa, g, d, nullptr, nullptr, 0)) != SSNAL_EN_OK) return e;
+    if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+    // more refinement steps while the corrections keep shrinking (by at least half each) and
+    // are above 1e-12 of the solution; a solve that stops contracting goes to FP64
+    double last = c->st_host->refine_ratio;
+    for (int extra = 0; extra < 16 && !(c->st_host->chol_fail | c->st_host->newton_bad) &&
+                        c->opt.refine_steps > 0 && last > 1e-12; extra++) {
+      if ((e = refine_once(c, r, kappa, g, d)) != SSNAL_EN_OK) return e;
+      if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+      const double now = c->st_host->refine_ratio;
+      if (!(now < 0.5 * last)) break;  // stagnation at the accuracy of the FP64 residual
+      last = now;
+    }
+    if (!(c->st_host->chol_fail | c->st_host->newton_bad)) return SSNAL_EN_OK;
+    if ((e = clear_newton_flags(c)) != SSNAL_EN_OK) return e;  // the FP32 solve is unreliable: FP64
+  }
+  if ((e = newton_direction_f64(c, r, kappa, g, d, nullptr, nullptr, 0)) != SSNAL_EN_OK) return e;
+  if ((e = read_state(c)) != SSNAL_EN_OK) return e;
+  return c->st_host->f64_fail ? SSNAL_EN_ENOCONV : SSNAL_EN_OK;
 }
 
 }  // extern "C"

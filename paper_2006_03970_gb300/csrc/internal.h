@@ -54,9 +54,19 @@ struct DevState {
   double lsdiff[kMaxLS];  // sum_j soft(v_j - s_k sigma t_j)^2 - soft(v_j)^2 per trial k
   // flags
   int32_t overflow;   // panel capacity exceeded by r
-  int32_t chol_fail;  // non-positive pivot in the Cholesky factorisation
+  // chol_fail, newton_bad and f64_fail are contiguous: the host clears the three at once.
+  // While any of them is set the next prox pass does not apply the pending step.
+  int32_t chol_fail;  // non-positive pivot in the FP32 Cholesky factorisation
+  int32_t newton_bad; // the first refinement correction of the FP32 solve exceeded the contraction bound
+  int32_t f64_fail;   // non-positive pivot in the FP64 Cholesky factorisation
   int32_t timeout;    // a bounded device-side wait gave up
   double gmax;        // ||A^T b||_inf (path)
+  double refine_ratio;  // ||first refinement correction|| / ||refined solution|| of the last FP32 solve
+  // conjugate-gradient Newton solve (kern_cg.cu)
+  double cg_rr;       // ||res||^2 of the current iterate
+  double cg_stop2;    // (rtol ||g||)^2
+  int32_t cg_iters;   // iterations of the current solve
+  int32_t cg_done;    // stopping test met (or breakdown)
   unsigned int counters[kNumCounters];
 };
 
@@ -69,7 +79,7 @@ constexpr int kStreamSplit = 17;       // same arithmetic on a pre-split float-p
 constexpr int kStreamLane = 18;        // pre-split copy, lane per column, 2-D TMA tiles (tensor map)
 // element types of the lane stream (see kern_stream.cu)
 constexpr int kLaneSplit = 0, kLaneBf16FF = 1, kLaneBf16 = 2, kLaneF32FF = 3, kLaneF32 = 4, kLaneI8FF = 5,
-              kLaneI8 = 6;
+              kLaneI8 = 6, kLaneI2FF = 7, kLaneI2 = 8;
 enum ProxMode { kProxThreshold = 0, kProxSupport = 1 };
 
 struct ProxParams {
@@ -139,6 +149,29 @@ bool make_factor_tensor_map(void* map_out, const float* L, long long ld, int N);
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s);
 
+// ---- FP64 Newton system (kern_f64.cu): the Newton matrix formed, factored and solved in FP64,
+// used when the FP32 factor fails or its refinement does not contract, or always on request.
+// G64: N x N column-major (lower triangle used), ldg64 >= N.
+// trans = 0: G64 = diag I + scale A_J^T A_J (N = r); trans = 1: G64 = diag I + scale A_J A_J^T (N = m).
+void launch_syrk64(const double* P, long long ldp, int m, int r, int trans, double diag, double scale, double* G64,
+                   long long ldg64, const DevState* st, cudaStream_t s);
+// Blocked Cholesky G64 = L L^T in place (lower); a non-positive pivot sets st->f64_fail.
+void chol64(double* G64, long long ldg64, int N, DevState* st, cudaStream_t s);
+// acc = alpha x (first) or acc += alpha x, with L L^T x = rhs (one CTA; skipped after f64_fail).
+void launch_trsv64(const double* L, long long ldl, int N, const double* rhs, double* acc, int first, double alpha,
+                   const DevState* st, cudaStream_t s);
+// acc += c over len entries; writes ||c|| / ||acc + c|| to st->refine_ratio and sets
+// st->newton_bad when it exceeds tau (a refinement correction measures the relative
+// error of the solution it corrects; above 1/2 the refinement does not contract).
+void launch_refine_update(double* acc, const double* c, int len, double tau, DevState* st, cudaStream_t s);
+
+// ---- conjugate-gradient Newton solve (kern_cg.cu), m <= 4096
+// d = 0, res = p = -g, rr = ||g||^2, stop when ||res|| <= rtol ||g||
+void launch_cg_init(const double* g, double* d, double* res, double* p, int m, double rtol, DevState* st,
+                    cudaStream_t s);
+// one iteration from Vp = (I + kappa A_J A_J^T) p; no-op once DevState::cg_done is set
+void launch_cg_step(double* d, double* res, double* p, const double* Vp, int m, DevState* st, cudaStream_t s);
+
 // ---- tensor-core SYRK (kern_tc.cu)
 size_t syrk_tc_panel_elems(int R, int K, int nsplit);
 size_t syrk_tc_part_floats(int sms);
@@ -167,5 +200,8 @@ void launch_check_range(const double* A, long long lda, int m, long long n, int*
 // api.cu: switch the stream of a context (returns the previous one)
 cudaStream_t ctx_set_stream(ssnal_en_ctx* c, cudaStream_t s);
 double ctx_mn(const ssnal_en_ctx* c);  // m * n of the context's matrix
+int64_t ctx_m(const ssnal_en_ctx* c);  // m of the context's matrix
+// frees a panel wider than keep_cols columns (regrown on demand)
+void ctx_trim(ssnal_en_ctx* c, int64_t keep_cols);
 
 }  // namespace ssnal

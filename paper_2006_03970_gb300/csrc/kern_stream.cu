@@ -677,17 +677,32 @@ constexpr int kEltF32FF = 3;    // FP32, float-float accumulation
 constexpr int kEltF32 = 4;      // FP32, FP32 accumulation
 constexpr int kEltI8FF = 5;     // int8 genotype codes, float-float accumulation
 constexpr int kEltI8 = 6;       // int8 genotype codes, FP32 accumulation
+constexpr int kEltI2FF = 7;     // 2-bit genotype codes (four per byte), float-float accumulation
+constexpr int kEltI2 = 8;       // 2-bit genotype codes, FP32 accumulation
 // The genotype entries are (code - mean_j) * scale_j: the stream sums code * y
 // and applies mean and scale per column, sum_i a_ij y_i = scale_j (sum_i c_ij y_i
 // - mean_j sum_i y_i).
 __host__ __device__ constexpr int elt_rows(int elt) {
-  return elt == kEltSplit ? 16 : (elt == kEltBf16FF || elt == kEltBf16) ? 64 : (elt == kEltI8FF || elt == kEltI8) ? 128 : 32;
+  return elt == kEltSplit                            ? 16
+         : (elt == kEltBf16FF || elt == kEltBf16)     ? 64
+         : (elt == kEltI8FF || elt == kEltI8)         ? 128
+         : (elt == kEltI2FF || elt == kEltI2)         ? 512
+                                                      : 32;
 }
-__host__ __device__ constexpr bool elt_i8(int elt) { return elt == kEltI8FF || elt == kEltI8; }
-// elements of the inner box dimension (128 bytes)
-__host__ __device__ constexpr int elt_box_inner(int elt) { return elt_rows(elt) == 16 ? 32 : elt_rows(elt); }
+// genotype codes (int8 or 2-bit): the column epilogue applies mean and scale
+__host__ __device__ constexpr bool elt_geno(int elt) {
+  return elt == kEltI8FF || elt == kEltI8 || elt == kEltI2FF || elt == kEltI2;
+}
+// elements (of the tensor map's data type) of the inner box dimension (128 bytes)
+__host__ __device__ constexpr int elt_box_inner(int elt) {
+  return elt_rows(elt) == 16 ? 32 : (elt == kEltI2FF || elt == kEltI2) ? 128 : elt_rows(elt);
+}
+// rows the vector d is padded to in shared memory (whole boxes)
+__host__ __device__ constexpr int lane_mpad(int m, int elt) {
+  return elt_rows(elt) > 128 ? (m + elt_rows(elt) - 1) / elt_rows(elt) * elt_rows(elt) : (m + 127) & ~127;
+}
 __host__ __device__ constexpr bool elt_ff(int elt) {
-  return elt == kEltSplit || elt == kEltBf16FF || elt == kEltF32FF || elt == kEltI8FF;
+  return elt == kEltSplit || elt == kEltBf16FF || elt == kEltF32FF || elt == kEltI8FF || elt == kEltI2FF;
 }
 
 // (S, L) += a * d on an element pair, a exact in FP32 (no low part)
@@ -709,6 +724,10 @@ __device__ __forceinline__ unsigned long long i8x2_biased(unsigned w, int k) {
   const unsigned lo = __byte_perm(x, 0x4B000000u, 0x7540u + (unsigned)k);
   const unsigned hi = __byte_perm(x, 0x4B000000u, 0x7540u + (unsigned)k + 1u);
   return (unsigned long long)lo | ((unsigned long long)hi << 32);
+}
+// the code of byte k of w (a value 0..3 in each byte) as FP32 2^23 + code (exact)
+__device__ __forceinline__ unsigned code_biased(unsigned w, int k) {
+  return __byte_perm(w, 0x4B000000u, 0x7540u + (unsigned)k);
 }
 // two BF16 values of one 32-bit word (memory order) as a packed FP32 pair
 __device__ __forceinline__ unsigned long long bf16x2_to_f32x2(unsigned w) {
@@ -737,7 +756,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
   extern __shared__ __align__(1024) unsigned char smem_lane[];
   constexpr int R = elt_rows(ELT);   // rows per box
   constexpr int P = R / 16;          // row pairs per 16-byte chunk of a column
-  const int mpad = (m + 127) & ~127;
+  const int mpad = lane_mpad(m, ELT);
   unsigned char* ring = smem_lane;  // [kLWarps][stages][kLBoxBytes]
   float4* D4 = reinterpret_cast<float4*>(smem_lane + (size_t)kLWarps * cfg.stages * kLBoxBytes);
   float2* DL = reinterpret_cast<float2*>(D4 + mpad / 2);
@@ -803,7 +822,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
   __syncthreads();
 
   double ysum = 0.0;  // sum_i vec_i (genotype mean correction)
-  if constexpr (elt_i8(ELT)) {
+  if constexpr (elt_geno(ELT)) {
     double a = 0.0;
     for (int i = tid; i < m; i += blockDim.x) a += vec[i];
     ysum = block_sum(a, red);
@@ -831,7 +850,46 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
 #pragma unroll
       for (int p = 0; p < 8; p++) {
         const int pp = (p + lane) & 7;
-        if constexpr (ELT == kEltSplit) {
+        if constexpr (P == 32) {
+          // 2-bit codes: 64 rows per 16-byte chunk, byte b of a word holds rows 4b .. 4b + 3
+          // (bits 2q, 2q + 1 for row 4b + q).  Each word is spread into four words of one
+          // code per byte (masks), each code becomes 2^23 + code in FP32 by a byte permute
+          // (exact), and the bias goes with one packed subtract per row pair.
+          const uint4 a = *reinterpret_cast<const uint4*>(colbase + pp * 16);
+          const uint4 b = *reinterpret_cast<const uint4*>(colbase + 32 * 128 + pp * 16);
+          const unsigned aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+          const unsigned long long bias = 0x4B0000004B000000ull;  // (2^23, 2^23)
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            unsigned ea[4], eb[4];
+#pragma unroll
+            for (int f = 0; f < 4; f++) {
+              ea[f] = (aw[q] >> (2 * f)) & 0x03030303u;
+              eb[f] = (bw[q] >> (2 * f)) & 0x03030303u;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; e++) {  // row pair 8 q + e: rows 16 q + 2 e, + 1 = 4 (e/2) + 2 (e%2) + {0, 1}
+              const int byte = e >> 1, f0 = 2 * (e & 1);
+              const unsigned long long av =
+                  f2sub((unsigned long long)code_biased(ea[f0], byte) |
+                            ((unsigned long long)code_biased(ea[f0 + 1], byte) << 32),
+                        bias);
+              const unsigned long long bv =
+                  f2sub((unsigned long long)code_biased(eb[f0], byte) |
+                            ((unsigned long long)code_biased(eb[f0 + 1], byte) << 32),
+                        bias);
+              const ulonglong2 d = D4p[P * pp + 8 * q + e];
+              if constexpr (elt_ff(ELT)) {
+                const unsigned long long dl = DLp[P * pp + 8 * q + e];
+                ff2_madd_exact(S2, L2, av, d.x, d.y, dl);
+                ff2_madd_exact(S2b, L2b, bv, d.x, d.y, dl);
+              } else {
+                S2 = f2fma(av, d.x, S2);
+                S2b = f2fma(bv, d.x, S2b);
+              }
+            }
+          }
+        } else if constexpr (ELT == kEltSplit) {
           const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(colbase + pp * 16);
           const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(colbase + 32 * 128 + pp * 16);
           const ulonglong2 d = D4p[pp];
@@ -901,7 +959,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
       const long long j = ((long long)blockIdx.x + q * gridDim.x) * kLCols + cc;
       const bool mine = j < n;
       double t = ((double)Sm + (double)Lm) * unscale;
-      if constexpr (elt_i8(ELT)) {
+      if constexpr (elt_geno(ELT)) {
         if (mine) t = (double)cscale[j] * (t - (double)cmean[j] * ysum);
       }
       if (mine) out[j] = t;
@@ -980,14 +1038,14 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
 
 constexpr size_t kLDynMax = 232448 - 12288;  // per-block limit minus the kernel's static shared memory
 
-static size_t lane_smem(int m, int stages) {
-  const int mpad = (m + 127) & ~127;
+static size_t lane_smem(int m, int stages, int elt) {
+  const int mpad = lane_mpad(m, elt);
   return (size_t)kLWarps * stages * kLBoxBytes + (size_t)mpad * 12 + (size_t)kLWarps * stages * 8 + 1024;
 }
 
-static int lane_stages(int m) {
+static int lane_stages(int m, int elt) {
   const size_t budget = kLDynMax;  // dynamic shared memory left beside the static part
-  const int mpad = (m + 127) & ~127;
+  const int mpad = lane_mpad(m, elt);
   int st = (int)((budget - (size_t)mpad * 12 - 1024) / ((size_t)kLWarps * kLBoxBytes + kLWarps * 8));
   if (st > 8) st = 8;
   return st;
@@ -1019,9 +1077,11 @@ bool make_split_tensor_map(void* map_out, const void* split, int m, long long n)
   return r == CUDA_SUCCESS;
 }
 
-// Tensor map over A stored as BF16 or FP32 (column-major, lda elements per
-// column, lda * element size a multiple of 16 bytes): boxes of 128 bytes of a
-// column x 64 columns, zero fill past row m.
+// Tensor map over A stored as BF16, FP32, int8 codes or 2-bit codes (column-major,
+// lda elements per column, the column stride a multiple of 16 bytes): boxes of 128
+// bytes of a column x 64 columns, zero fill past row m (2-bit codes: bytes, four rows
+// each, zero fill past byte ceil(m / 4); the zero codes past row m meet zero entries
+// of the vector).
 bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda, int m, long long n) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -1035,11 +1095,13 @@ bool make_elt_tensor_map(void* map_out, const void* A, int dtype, long long lda,
     }
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  const bool bf16 = dtype == SSNAL_EN_BF16, i8 = dtype == SSNAL_EN_I8_GENO;
+  const bool bf16 = dtype == SSNAL_EN_BF16, i2 = dtype == SSNAL_EN_I2_GENO;
+  const bool i8 = dtype == SSNAL_EN_I8_GENO || i2;
   const size_t es = i8 ? 1 : bf16 ? 2 : 4;
-  if ((lda * es) % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
-  cuuint64_t strides[1] = {(cuuint64_t)(lda * es)};
+  const long long ld_bytes = i2 ? lda / 4 : lda * (long long)es;  // column stride in bytes
+  if ((i2 && lda % 4 != 0) || ld_bytes % 16 != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(i2 ? (m + 3) / 4 : m), (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)ld_bytes};
   cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)kLCols};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(reinterpret_cast<CUtensorMap*>(map_out),
@@ -1087,7 +1149,7 @@ static void launch_lane(const void* map, int m, long long n, const double* vec, 
   static bool configured[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  const int stages = lane_stages(m);
+  const int stages = lane_stages(m, ELT);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
     cudaFuncSetAttribute(k_stream_lane<MODE, ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLDynMax);
     if (dev >= 0 && dev < 64) configured[dev] = true;
@@ -1100,7 +1162,7 @@ static void launch_lane(const void* map, int m, long long n, const double* vec, 
   if (grid > sms) grid = sms;
   if (grid < 1) grid = 1;
   const CUtensorMap* tm = reinterpret_cast<const CUtensorMap*>(map);
-  launch_k(k_stream_lane<MODE, ELT>, dim3((int)grid), dim3(kLThreads), (size_t)(lane_smem(m, stages)), s, *tm, m, n, vec, out, x, u, lp, st,
+  launch_k(k_stream_lane<MODE, ELT>, dim3((int)grid), dim3(kLThreads), (size_t)(lane_smem(m, stages, ELT)), s, *tm, m, n, vec, out, x, u, lp, st,
                                                                               partials, cfg, cmean, cscale);
 }
 
@@ -1130,6 +1192,8 @@ void launch_stream_lane(int mode, int elt, const void* map, int m, long long n, 
     case kEltF32: SSNAL_LANE(kEltF32); break;
     case kEltI8FF: SSNAL_LANE(kEltI8FF); break;
     case kEltI8: SSNAL_LANE(kEltI8); break;
+    case kEltI2FF: SSNAL_LANE(kEltI2FF); break;
+    case kEltI2: SSNAL_LANE(kEltI2); break;
     default: SSNAL_LANE(kEltSplit); break;
   }
 #undef SSNAL_LANE

@@ -83,6 +83,11 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
   __shared__ unsigned cred[kVecThreads / 32];
   long long start, stop;
   block_range(n, start, stop);
+  // a Newton direction flagged as unreliable (failed FP32 factor or a refinement that
+  // does not contract) is not applied: y and u stay, and the host recomputes the
+  // direction in FP64.  The flags are read from memory written by earlier kernels, so
+  // every block takes the same decision.
+  if (apply_update && (st->chol_fail | st->newton_bad | st->f64_fail)) apply_update = 0;
   const double s = apply_update ? st->s : 0.0;
   // y += s d in the last block, whose range of entries is the shortest
   if (apply_update && blockIdx.x == gridDim.x - 1) {
@@ -260,6 +265,19 @@ struct LoadI8 {
   const float* scale;
   __device__ double operator()(long long col, long long off) const {
     return ((double)A[off] - (double)mean[col]) * (double)scale[col];
+  }
+};
+
+// 2-bit genotype codes, four per byte (element offset off counts codes: byte off / 4,
+// bits 2 (off mod 4) ..): entry (code - mean_j) * scale_j, evaluated in FP64.  The
+// column stride is a multiple of 64 codes, so off mod 4 is the row mod 4.
+struct LoadI2 {
+  const uint8_t* A;
+  const float* mean;
+  const float* scale;
+  __device__ double operator()(long long col, long long off) const {
+    const unsigned code = (A[off >> 2] >> (2 * (unsigned)(off & 3))) & 3u;
+    return ((double)code - (double)mean[col]) * (double)scale[col];
   }
 };
 
@@ -760,8 +778,11 @@ void launch_gather(const void* A, int dtype, long long lda, int m, const int32_t
   else if (dtype == 2)
     launch_k(k_gather<LoadBF16>, dim3(grid), dim3(256), (size_t)0, s, LoadBF16{(const __nv_bfloat16*)A}, lda, m, J, st,
              r_host, rcap, P, ldp, P32, ldp32, ovf);
-  else
+  else if (dtype == 3)
     launch_k(k_gather<LoadI8>, dim3(grid), dim3(256), (size_t)0, s, LoadI8{(const int8_t*)A, cmean, cscale}, lda, m, J,
+             st, r_host, rcap, P, ldp, P32, ldp32, ovf);
+  else
+    launch_k(k_gather<LoadI2>, dim3(grid), dim3(256), (size_t)0, s, LoadI2{(const uint8_t*)A, cmean, cscale}, lda, m, J,
              st, r_host, rcap, P, ldp, P32, ldp32, ovf);
 }
 

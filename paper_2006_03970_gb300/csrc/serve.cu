@@ -116,23 +116,40 @@ void worker_main(ssnal_en_server* S) {
         sl = Slot();
       }
     }
-    if (st == SSNAL_EN_OK) {
+    // a solve that runs out of device memory (a large active set grows the panel) is
+    // retried once after this worker releases the contexts of its other matrices
+    for (int attempt = 0; attempt < 2 && st == SSNAL_EN_OK; attempt++) {
       if (cudaMemcpyAsync(sl.b, q->b.data(), sizeof(double) * A.m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-          cudaMemsetAsync(sl.x, 0, sizeof(double) * A.n, s) != cudaSuccess)
+          cudaMemsetAsync(sl.x, 0, sizeof(double) * A.n, s) != cudaSuccess) {
         st = SSNAL_EN_ECUDA;
-    }
-    if (st == SSNAL_EN_OK) {
+        break;
+      }
       if (q->scaled) {
         int32_t ndone = 0;
         st = ssnal_en_path(sl.ctx, sl.b, q->alpha, &q->c, 1, sl.x, &q->res, &ndone);
       } else {
         st = ssnal_en_solve(sl.ctx, sl.b, q->lambda1, q->lambda2, sl.x, nullptr, &q->res);
       }
+      if (st != SSNAL_EN_ENOMEM || attempt > 0) break;
+      cudaGetLastError();
+      for (size_t k = 0; k < slots.size(); k++) {
+        if ((int)k == q->mat || !slots[k].ctx) continue;
+        ssnal_en_destroy(slots[k].ctx);
+        cudaFree(slots[k].b);
+        cudaFree(slots[k].x);
+        slots[k] = Slot();
+      }
+      ssnal::ctx_trim(sl.ctx, 0);
+      st = SSNAL_EN_OK;
+    }
+    if (st == SSNAL_EN_OK || st == SSNAL_EN_ENOCONV) {
       q->x.resize((size_t)A.n);
       if (cudaMemcpyAsync(q->x.data(), sl.x, sizeof(double) * A.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
           cudaStreamSynchronize(s) != cudaSuccess)
         st = SSNAL_EN_ECUDA;
     }
+    // a context kept for later requests does not keep the panel of a large active set
+    if (sl.ctx) ssnal::ctx_trim(sl.ctx, 4 * ssnal::ctx_m(sl.ctx));
     q->res.status = st;
     {
       std::lock_guard<std::mutex> lk(S->mu);

@@ -1,0 +1,77 @@
+"""Small, self-contained workloads for kernel profiling (ncu) of the hot path.
+
+Each case is sized so that a full metric capture of one kernel ends within a minute
+or two while its operands still exceed the 129 MB L2 of a GB300:
+
+  precision-small  the precision workload's generator (50-feature AR(1) blocks, rho 0.5,
+                   FP32 generated, standardized, stored BF16) at m = 1000, n = 100000
+                   (200 MB), one mixed-form fit per alpha in {0.5, 0.9}, c = 0.3
+  newton-730       one Newton direction of the SMW form (eq. smw_formula) at m = 1000,
+                   r = 730 (the active-set size of the precision workload at alpha 0.5) on
+                   BF16 storage: the BF16 tensor-core SYRK, the cluster Cholesky and the
+                   triangular solves with their refinement
+
+    python -m paper_2006_03970_gb300.profile_cases precision-small
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+
+def precision_small(n=100_000, m=1000, fits=1):
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    p = synth.config3(m=m, n=n)
+    bits = synth.to_bf16_bits(p.At)
+    ctx = pkg.Context(bits, dtype=pkg.BF16, options=pkg.ssnal_en_default_options(precision=1))
+    b = torch.as_tensor(p.b, dtype=torch.float64, device="cuda")
+    X = torch.zeros((1, n), dtype=torch.float64, device="cuda")
+    out = []
+    for _ in range(fits):
+        for alpha in (0.5, 0.9):
+            st, res, done = pkg.ssnal_en_path(ctx.ctx, b, alpha, [0.3], X)
+            out.append((alpha, res[0].status, res[0].newton_iters, res[0].active))
+    torch.cuda.synchronize()
+    ctx.close()
+    return out
+
+
+def newton_730(m=1000, r=730, repeats=3):
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    rng = np.random.default_rng(730)
+    At = rng.normal(size=(r + 64, m)).astype(np.float32)
+    bits = synth.to_bf16_bits(At)
+    ctx = pkg.Context(bits, dtype=pkg.BF16, options=pkg.ssnal_en_default_options(precision=1))
+    J = torch.arange(r, dtype=torch.int32, device="cuda")
+    g = torch.as_tensor(rng.normal(size=m), device="cuda")
+    gd = torch.empty(m, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_grad(ctx.ctx, J, torch.zeros(r, dtype=torch.float64, device="cuda"), r, -g,
+                         torch.zeros(m, dtype=torch.float64, device="cuda"), gd)
+    d = torch.empty(m, dtype=torch.float64, device="cuda")
+    for _ in range(repeats):
+        pkg.ssnal_en_op_newton(ctx.ctx, r, 0.5, g, d)
+    torch.cuda.synchronize()
+    ctx.close()
+    return float(d.abs().max())
+
+
+CASES = {"precision-small": precision_small, "newton-730": newton_730}
+
+
+def main(argv):
+    if len(argv) != 1 or argv[0] not in CASES:
+        print(__doc__)
+        return 2
+    import paper_2006_03970_gb300 as pkg
+    pkg.load_library()
+    print(argv[0], CASES[argv[0]]())
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

@@ -45,8 +45,8 @@ def test_struct_layouts(lib):
     import paper_2006_03970_gb300 as pkg
     # sizes implied by the header's field lists (LP64)
     assert ctypes.sizeof(pkg.Matrix) == 3 * 8 + 2 * 4 + 3 * 8
-    assert ctypes.sizeof(pkg.Options) == 6 * 8 + 8 * 4 + 8
-    assert ctypes.sizeof(pkg.Result) == 4 * 4 + 8 + 8 * 8
+    assert ctypes.sizeof(pkg.Options) == 6 * 8 + 8 * 4 + 8 + 2 * 4 + 8 + 8
+    assert ctypes.sizeof(pkg.Result) == 4 * 4 + 8 + 8 * 8 + 2 * 4
     assert ctypes.sizeof(pkg.Instance) == 6 * 8
     assert ctypes.sizeof(pkg.TunePoint) == 5 * 8
 
@@ -73,3 +73,12 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     o = pkg.ssnal_en_default_options(mu=0.7)
     ok = pkg.Matrix(m=4, n=5, lda=4, dtype=0, reserved=0, data=16, col_mean=None, col_scale=None)
     assert L.ssnal_en_create(ctypes.byref(ctx), ctypes.byref(ok), ctypes.byref(o), None) == pkg.EINVAL
+
+
+def test_binding_constants_match_the_header_defines():
+    # the binding sizes host buffers from these (a mismatch overruns them)
+    import paper_2006_03970_gb300 as pkg
+    src = open(os.path.join(ROOT, "include", "ssnal_en.h")).read()
+    defines = dict(re.findall(r"#define SSNAL_EN_(\w+)\s+(\d+)", src))
+    assert int(defines["PROFILE_PHASES"]) == pkg.PROFILE_PHASES == len(pkg.PHASES)
+    assert int(defines["STATIC_MAX_N"]) == pkg.STATIC_MAX_N

@@ -211,3 +211,65 @@ def test_fit_genotype_codes(precision, m, n, alpha, c, seed):
     else:
         assert abs(P_gpu - P_or) <= 1e-6 * max(1.0, abs(P_or))
         assert np.abs(xg - ro.x).max() <= 1e-3 * xmax
+
+
+# ---------------------------------------------------------------- 2-bit genotype codes (four per byte)
+def genotype_context_2bit(codes, mean, scale, precision):
+    m = codes.shape[1]
+    A, _ = pkg.device_matrix(codes, pkg.I2_GENO)
+    cm, cs = dev(mean, torch.float32), dev(scale, torch.float32)
+    return pkg.Context(A, m=m, dtype=pkg.I2_GENO, options=pkg.ssnal_en_default_options(precision=precision),
+                       col_mean=cm, col_scale=cs)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 40), (127, 129), (512, 300), (513, 300), (1000, 5000), (2000, 511)])
+def test_stream_genotype_codes_2bit(m, n):
+    codes, mean, scale, As, _ = genotype_problem(m, n, seed=m + n)
+    rng = np.random.default_rng(m)
+    y = rng.normal(size=m)
+    ref = As @ y
+    s = np.abs(scale.astype(np.float64))
+    mag = s * (np.abs(codes.astype(np.float64)) @ np.abs(y) + np.abs(mean.astype(np.float64)) * np.abs(y).sum())
+    ctx2 = genotype_context_2bit(codes, mean, scale, 0)
+    ctx8 = genotype_context(codes, mean, scale, 0)
+    u2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    u8 = torch.empty(n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_y(ctx2.ctx, dev(y), u2)
+    pkg.ssnal_en_op_at_y(ctx8.ctx, dev(y), u8)
+    bound = (2.0 ** -44 + m * 2.0 ** -46) * mag + 1e-300
+    u2h = u2.cpu().numpy()
+    assert np.all(np.abs(u2h - ref) <= bound)
+    # the int8 and 2-bit passes sum the same exact products in a different order (512 rows
+    # per box against 128): both float-float, they agree to the same bound
+    assert np.all(np.abs(u2h - u8.cpu().numpy()) <= 2 * bound)
+    for c in (ctx2, ctx8):
+        c.set_options(pkg.ssnal_en_default_options(precision=1))
+    t2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_d(ctx2.ctx, dev(y), t2)
+    assert np.all(np.abs(t2.cpu().numpy() - ref) <= (m + 4) * 2.0 ** -24 * mag + 1e-300)
+    ctx2.close()
+    ctx8.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("m,n,alpha,c,seed", [(150, 4000, 0.7, 0.3, 51), (400, 3000, 0.95, 0.2, 52),
+                                              (2000, 3000, 0.8, 0.3, 53)])
+def test_fit_genotype_codes_2bit(precision, m, n, alpha, c, seed):
+    codes, mean, scale, As, b = genotype_problem(m, n, seed)
+    lam1, lam2 = R.lambdas(As, b, alpha, c)
+    ctx = genotype_context_2bit(codes, mean, scale, precision)
+    x, y, res = ctx.solve(b, lam1, lam2)
+    xg = x.cpu().numpy()
+    ctx.close()
+    ro = R.solve(As, b, lam1, lam2)
+    assert res.status == pkg.OK and ro.converged
+    assert res.kkt1 <= 1e-6 and res.kkt3 <= 1e-6
+    xmax = np.abs(ro.x).max()
+    P_or = C.primal_objective(As, b, ro.x, lam1, lam2)
+    P_gpu = C.primal_objective(As, b, xg, lam1, lam2)
+    if precision == 0:
+        assert abs(P_gpu - P_or) <= 1e-9 * max(1.0, abs(P_or))
+        assert np.abs(xg - ro.x).max() <= 1e-6 * xmax
+    else:
+        assert abs(P_gpu - P_or) <= 1e-6 * max(1.0, abs(P_or))
+        assert np.abs(xg - ro.x).max() <= 1e-3 * xmax
