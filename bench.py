@@ -230,6 +230,68 @@ def _roofline(kernel, bytes_per_launch, ms, launches, peak, peak_kind, traffic=N
     return out
 
 
+def run_path_headline(args, pkg, rank, world, local, barrier):
+    """--workload path: the FP64 regularization path as the headline line (20 warm-started fits
+    per step), with its e2e number through the C ABI (b in, all 20 solutions out)."""
+    import torch
+    from paper_2006_03970_gb300 import synth
+    p = synth.config2(seed=SEED2, m=M2, n=N2)
+    grid = list(synth.path_grid(K2, 0.05))
+    ctx = pkg.Context(p.At)
+    b = torch.as_tensor(p.b, dtype=torch.float64, device="cuda")
+    X = torch.zeros((len(grid), ctx.n), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        pkg.ssnal_en_path(ctx.ctx, b, ALPHA2, grid, X)
+    torch.cuda.synchronize()
+    barrier()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    prof0 = pkg.ssnal_en_profile(ctx.ctx, True, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fits = newton = 0
+    for _ in range(args.steps):
+        st, res, done = pkg.ssnal_en_path(ctx.ctx, b, ALPHA2, grid, X)
+        fits += _count_fits(res, done)
+        newton += sum(r.newton_iters for r in res[:done])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof1 = pkg.ssnal_en_profile(ctx.ctx, False, False)
+    clk = clocks.stop()
+    ms, fits_all = reduce_over_ranks(e0.elapsed_time(e1), fits, "cuda")
+    b_host = torch.empty(M2, dtype=torch.float64, pin_memory=True)
+    b_host.copy_(torch.from_numpy(p.b))
+    X_host = torch.empty((len(grid), ctx.n), dtype=torch.float64, pin_memory=True)
+    bh, xh = b_host.numpy(), X_host.numpy()
+    pkg.ssnal_en_path_host(ctx.ctx, bh, ALPHA2, grid, xh)
+    barrier()
+    t0 = time.perf_counter()
+    efits = 0
+    for _ in range(args.steps):
+        st, res, done = pkg.ssnal_en_path_host(ctx.ctx, bh, ALPHA2, grid, xh)
+        efits += _count_fits(res, done)
+    edt, efits = reduce_over_ranks(time.perf_counter() - t0, efits, "cuda")
+    peak, peak_kind = _peaks()
+    rl = _roofline("k_stream_lane<kModeT, float pair> (t = A^T d over the pre-split copy, fused line-search trial "
+                   "sums)", 8.0 * M2 * N2 + 3 * 8.0 * N2 + 8.0 * M2, prof1["stream_ms"], prof1["stream_launches"], peak,
+                   peak_kind, TRAFFIC["split_modeT_m500_n1e5"])
+    ctx.close()
+    line = {"metric": "EN fits/s to KKT<=1e-6", "value": fits_all / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD2, "l2": "inputs larger than L2 (A is 400 MB, L2 129 MB)",
+                       "fits_per_step": K2, "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clk, "e2e": {"value": efits / edt, "unit": UNIT, "h2d_bytes_per_step": 8 * M2,
+                                   "d2h_bytes_per_step": 8 * len(grid) * N2},
+            "gpu_launches": prof1["kernel_launches"] - prof0["kernel_launches"], "roofline": rl}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -247,6 +309,12 @@ def run_gpu(args):
             import torch.distributed as dist
             dist.barrier()
 
+    if args.workload == "path":
+        rc = run_path_headline(args, pkg, rank, world, local, barrier)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
     p, bits = precision_problem()
     m, n = M3, N3
     ctx = pkg.Context(bits, dtype=pkg.BF16, options=pkg.ssnal_en_default_options(precision=1))
@@ -498,14 +566,16 @@ def batched_fits(count=512):
             "sequential_fits_per_s": count / dts}
 
 
-def serve_workload(per_rate=400, n_small=16, workers=16, seed=5, keep=None):
+def serve_workload(per_rate=400, n_small=16, workers=16, seed=5, keep=None, group=8):
     """The serving configuration: a resident genotype-like A (m=2000, n=500000 codes
     ~ Binomial(2, p_j), p_j ~ U(0.05, 0.5), stored four per byte, standardized on the fly by
     per-column FP32 mean and scale) plus `n_small` resident FP32 matrices from the precision workload's generator (m
     log-uniform in [200, 1000], n log-uniform in [1e4, 2e5], 50-feature blocks rho 0.5).  Each
     request: its own x* (30 nonzeros +-U[0.5, 2]), b = A x* + noise at snr 2, alpha ~ U[0.5, 1),
     c ~ U[0.1, 0.8]; its matrix is the genotype one with probability 1/2, else uniform over the
-    others.  The server runs the mixed form (precision 1) with `workers` worker streams.  First a
+    others.  The server runs the mixed form (precision 1) with `workers` worker streams, each
+    advancing up to `group` requests on one matrix together with their passes over A merged
+    (A^T [d_1 ... d_k]); requests arriving on that matrix join as places free up.  First a
     burst of `per_rate` requests gives the saturation throughput; then Poisson arrivals at
     {0.25, 0.5, 0.75, 0.9, 1.1} x that rate, `per_rate` requests each, give latency percentiles
     (submission to completion, host transfers included).  Each phase also reports how many
@@ -541,7 +611,7 @@ def serve_workload(per_rate=400, n_small=16, workers=16, seed=5, keep=None):
         b = ax + math.sqrt(ax.var() / 2.0) * rng.standard_normal(m)
         return k, b, float(rng.uniform(0.5, 1.0)), float(rng.uniform(0.1, 0.8))
 
-    srv = pkg.Server(mats, workers=workers, options=pkg.ssnal_en_default_options(precision=1))
+    srv = pkg.Server(mats, workers=workers, options=pkg.ssnal_en_default_options(precision=1), group=group)
 
     def run(reqs, arrivals=None):
         t0 = time.perf_counter()
@@ -583,7 +653,8 @@ def serve_workload(per_rate=400, n_small=16, workers=16, seed=5, keep=None):
         keep.append(("matrices", mats, host_cols, sizes))
     return {"workload": f"resident genotype A 2000x500000 2-bit codes (250 MB) + {n_small} FP32 matrices "
                         f"(m in [200,1000], n in [1e4,2e5]); requests 50% genotype, alpha ~ U[0.5,1), "
-                        f"c ~ U[0.1,0.8], x* 30 nonzeros, snr 2; mixed form, {workers} worker streams",
+                        f"c ~ U[0.1,0.8], x* 30 nonzeros, snr 2; mixed form, {workers} worker streams, groups of "
+                        f"up to {group} requests per matrix with merged passes over A",
             "saturation": burst, "poisson_sweep": sweep}
 
 
@@ -593,8 +664,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle errors and the CPU baseline")
-    ap.add_argument("--no-fp64-form", action="store_true", help="skip the FP64 form of the headline workload")
+    ap.add_argument("--workload", choices=["precision", "path"], default="precision",
+                    help="headline workload: the precision configuration (default) or the FP64 path "
+                         "(path: the headline line only)")
+    ap.add_argument("--no-oracle", "--no-cpu-baseline", action="store_true",
+                    help="skip the oracle errors and the CPU baseline")
+    ap.add_argument("--no-fp64-form", "--no-mixed", action="store_true",
+                    help="skip the FP64 form of the headline workload")
     ap.add_argument("--no-path", action="store_true", help="skip the FP64 regularization path workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")

@@ -281,6 +281,51 @@ typedef struct {
 ssnal_en_status ssnal_en_solve_batch(ssnal_en_instance* inst, int64_t count, int32_t workers,
                                      ssnal_en_result* out, int32_t* workers_used);
 
+/* Solves count independent fits whose contexts share one matrix (created from the same
+ * ssnal_en_matrix: same data, sizes and type; every instance has its own context),
+ * advancing them together one Newton step at a time so that the passes over A of all
+ * fits that need one are merged: one pass forms A^T [d_1 ... d_k] for up to 4 fits, each
+ * with its own fused line search (eq. line_search).  Merging applies to the passes that
+ * accumulate in FP32 (precision 1 with BF16, FP32 or genotype storage); otherwise the
+ * fits take one pass each.  Each fit's kernels are those of ssnal_en_solve, so its
+ * result is bitwise that of ssnal_en_solve on its own.  All work runs on the first
+ * instance's context stream.  out: host array of count results (may be NULL);
+ * passes (host, may be NULL): the passes over A of the Newton steps.  Returns OK when
+ * every fit converged, else the first non-OK status.  Errors: EINVAL (null pointers,
+ * bad lambdas, a context used twice), ECUDA. */
+ssnal_en_status ssnal_en_solve_shared(ssnal_en_instance* inst, int32_t count, ssnal_en_result* out,
+                                      int32_t* passes);
+
+/* One fit of a device-resident batch: A stored as FP32. */
+typedef struct {
+  const float* A;          /* device, column-major m x n, column j at A + j*lda */
+  int64_t m, n, lda;       /* m <= 1024, lda >= m */
+  const double* b;         /* device, length m */
+  double lambda1, lambda2;
+  double* x;               /* device, length n: in = warm start, out = solution */
+} ssnal_en_batch_fit;
+
+/* Solves count independent fits in one launch of a persistent kernel (Algorithm 1 per
+ * fit, entirely on the device): one CTA per SM takes the next fit from a device work
+ * queue (the fits ordered by m*n, largest first) and runs its whole AL / SsN loop --
+ * prox and active set, gradient, Newton matrix (FP32, read from A's columns through J)
+ * with its Cholesky factor, triangular solves and one FP64 refinement step, the
+ * float-float passes over A, the line search, the multiplier update and the KKT test
+ * -- then takes the next.  The loads in flight of the passes over A are tuned on the
+ * batch (three slices of the order with 4, 8 and 16 per lane; the rest with the fastest);
+ * the choice changes no sum's order, so the results do not depend on it.  A fit whose
+ * FP32 Newton solve fails or does not contract is solved again by ssnal_en_solve on a
+ * temporary context (FP64 Newton system) from its warm start.  opts: NULL = defaults
+ * (precision, syrk_tc, cg and ls_fused do not apply).  Device scratch of about
+ * 5 n_max + 9 m_max doubles and m_max^2 floats per SM is allocated and freed inside the
+ * call.  out: host array of count results; info (host, may be NULL): [loads in flight
+ * chosen, fits solved again on the regular path].  Synchronises `stream`.  Returns OK
+ * when every fit converged, else the first non-OK status.
+ * Errors: EINVAL, ENOTSUP (m above 1024), ENOMEM, ECUDA. */
+ssnal_en_status ssnal_en_solve_batch_resident(const ssnal_en_batch_fit* fits, int64_t count,
+                                              const ssnal_en_options* opts, ssnal_en_result* out, int32_t* info,
+                                              void* stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: resident matrices, requests admitted while others run.
  * ------------------------------------------------------------------------- */
@@ -289,15 +334,27 @@ typedef struct ssnal_en_server ssnal_en_server; /* opaque */
 
 /* Starts a server over nmat resident matrices (descriptors copied; the device
  * data stays owned by the caller and must outlive the server) with `workers`
- * worker threads, each with its own CUDA stream.  A worker creates one context
- * per matrix it serves (options opts, NULL = defaults) and keeps it for later
- * requests on that matrix.  Requests are admitted in arrival order as workers
- * free up and while the estimated device bytes of the contexts in use stay
- * within max_bytes (0 = no bound; one request is always admitted).  FP64
+ * worker threads, each with its own CUDA stream.  A free worker takes the oldest
+ * queued request and the queued requests on the same matrix (up to the group
+ * size, ssnal_en_server_set_group) and advances their fits together, one Newton
+ * step at a time, with their passes over A merged (A^T [d_1 ... d_k], as in
+ * ssnal_en_solve_shared); requests on that matrix that arrive meanwhile join the
+ * group as its fits finish.  A worker creates contexts per matrix (options opts,
+ * NULL = defaults) and keeps them for later requests on that matrix, releasing
+ * the panel of a large active set after each request.  Requests are admitted as
+ * workers and group places free up and while the estimated device bytes of the
+ * contexts in use stay within max_bytes (0 = no bound; one request is always
+ * admitted).  A request that runs out of device memory is run once more after
+ * its worker releases its contexts of other matrices.  FP64
  * matrices get a float-pair copy per worker context (see ssnal_en_create); the
  * other storage types are read in place.  Errors: EINVAL, ENOMEM, ECUDA. */
 ssnal_en_status ssnal_en_server_create(ssnal_en_server** srv, const ssnal_en_matrix* mats, int32_t nmat,
                                        const ssnal_en_options* opts, int32_t workers, int64_t max_bytes);
+
+/* Requests on one matrix that a worker advances together, their passes over A
+ * merged (see ssnal_en_solve_shared): 1 (no merging) .. 64, default 8.  Applies to
+ * groups formed after the call.  Errors: EINVAL. */
+ssnal_en_status ssnal_en_server_set_group(ssnal_en_server* srv, int32_t max_group);
 
 /* Queues one fit on matrix `mat` (eq. EN_pb with penalties lambda1, lambda2,
  * started from x = 0): b_host is host memory of length m, copied before

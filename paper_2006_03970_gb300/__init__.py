@@ -20,7 +20,7 @@ __all__ = [
     "F64", "F32", "BF16", "I8_GENO", "I2_GENO", "pack_codes_2bit", "OK", "EINVAL", "ENOMEM", "ENOCONV", "ECUDA", "ETIMEOUT", "ENOTSUP",
     "SsnalError", "Matrix", "Options", "Result", "load_library", "device_matrix", "default_options",
     "ssnal_en_default_options", "ssnal_en_create", "ssnal_en_destroy", "ssnal_en_set_options", "ssnal_en_solve",
-    "ssnal_en_solve_batch", "Instance", "Server", "ssnal_en_server_create", "ssnal_en_server_submit",
+    "ssnal_en_solve_batch", "ssnal_en_solve_shared", "ssnal_en_solve_batch_resident", "BatchFit", "ssnal_en_server_set_group", "Instance", "Server", "ssnal_en_server_create", "ssnal_en_server_submit",
     "ssnal_en_server_poll", "ssnal_en_server_destroy", "ssnal_en_server_submit_scaled", "ssnal_en_tune",
     "TunePoint", "ssnal_en_path", "ssnal_en_path_host", "ssnal_en_op_at_y", "ssnal_en_op_at_d", "ssnal_en_op_prox_active",
     "ssnal_en_op_grad",
@@ -64,6 +64,12 @@ class Instance(ctypes.Structure):
                 ("lambda2", ctypes.c_double), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p)]
 
 
+class BatchFit(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("b", ctypes.c_void_p), ("lambda1", ctypes.c_double), ("lambda2", ctypes.c_double),
+                ("x", ctypes.c_void_p)]
+
+
 class TunePoint(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("rss", ctypes.c_double), ("gcv", ctypes.c_double),
                 ("ebic", ctypes.c_double), ("active", ctypes.c_int64)]
@@ -86,7 +92,8 @@ EXPORTS = ["ssnal_en_default_options", "ssnal_en_status_string", "ssnal_en_creat
            "ssnal_en_op_at_d", "ssnal_en_solve_batch", "ssnal_en_server_create", "ssnal_en_server_submit",
            "ssnal_en_server_submit_scaled", "ssnal_en_server_poll", "ssnal_en_server_destroy", "ssnal_en_tune",
            "ssnal_en_op_prox_active", "ssnal_en_op_grad", "ssnal_en_op_newton", "ssnal_en_profile",
-           "ssnal_en_prox_active_static", "ssnal_en_profile_phases"]
+           "ssnal_en_prox_active_static", "ssnal_en_profile_phases", "ssnal_en_solve_shared",
+           "ssnal_en_server_set_group", "ssnal_en_solve_batch_resident"]
 
 
 def load_library(path: str | None = None):
@@ -110,6 +117,10 @@ def load_library(path: str | None = None):
     L.ssnal_en_solve.argtypes = [vp, vp, dbl, dbl, vp, vp, ctypes.POINTER(Result)]
     L.ssnal_en_solve_batch.argtypes = [ctypes.POINTER(Instance), ctypes.c_int64, i32, ctypes.POINTER(Result),
                                        ctypes.POINTER(i32)]
+    L.ssnal_en_solve_shared.argtypes = [ctypes.POINTER(Instance), i32, ctypes.POINTER(Result), ctypes.POINTER(i32)]
+    L.ssnal_en_server_set_group.argtypes = [vp, i32]
+    L.ssnal_en_solve_batch_resident.argtypes = [ctypes.POINTER(BatchFit), ctypes.c_int64, ctypes.POINTER(Options),
+                                                ctypes.POINTER(Result), ctypes.POINTER(i32), vp]
     L.ssnal_en_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Matrix), i32, ctypes.POINTER(Options), i32,
                                          ctypes.c_int64]
     L.ssnal_en_server_submit.argtypes = [vp, i32, ctypes.POINTER(dbl), dbl, dbl, ctypes.POINTER(ctypes.c_int64)]
@@ -273,6 +284,39 @@ def ssnal_en_solve_batch(instances, workers: int = 0):
     return st, list(res), used.value
 
 
+def ssnal_en_solve_shared(instances):
+    """Fits whose contexts share one matrix, advanced together with merged passes over A.
+    instances: sequence of (ctx, b, lambda1, lambda2, x, y-or-None) with FP64 device tensors.
+    Returns (status, [Result], passes over A of the Newton steps)."""
+    arr = (Instance * len(instances))()
+    for k, (ctx, b, l1, l2, x, y) in enumerate(instances):
+        arr[k] = Instance(ctx, _ptr(b), float(l1), float(l2), _ptr(x), _ptr(y))
+    res = (Result * len(instances))()
+    passes = ctypes.c_int32(0)
+    st = load_library().ssnal_en_solve_shared(arr, len(instances), res, ctypes.byref(passes))
+    _check(st, "ssnal_en_solve_shared", allow=(OK, ENOCONV))
+    return st, list(res), passes.value
+
+
+def ssnal_en_solve_batch_resident(fits, options: Options | None = None, stream=None):
+    """fits: sequence of (A (device tensor (n, lda) float32, column-major A), m, b, lambda1, lambda2, x)
+    with b, x FP64 device tensors.  Returns (status, [Result], (loads in flight chosen, fits solved
+    again on the regular path))."""
+    arr = (BatchFit * len(fits))()
+    for k, (A, m, b, l1, l2, x) in enumerate(fits):
+        arr[k] = BatchFit(A.data_ptr(), int(m), A.shape[0], A.shape[1], _ptr(b), float(l1), float(l2), _ptr(x))
+    res = (Result * len(fits))()
+    info = (ctypes.c_int32 * 2)()
+    st = load_library().ssnal_en_solve_batch_resident(arr, len(fits), ctypes.byref(options) if options else None,
+                                                      res, info, _stream_handle(stream))
+    _check(st, "ssnal_en_solve_batch_resident", allow=(OK, ENOCONV))
+    return st, list(res), (info[0], info[1])
+
+
+def ssnal_en_server_set_group(srv, max_group: int):
+    _check(load_library().ssnal_en_server_set_group(srv, int(max_group)), "ssnal_en_server_set_group")
+
+
 def ssnal_en_server_create(mats, workers=8, options: Options | None = None, max_bytes=0):
     """mats: list of (device tensor (n, lda), m, dtype, col_mean, col_scale).  Returns a handle."""
     arr = (Matrix * len(mats))()
@@ -330,10 +374,12 @@ class Server:
     """Serving loop over resident matrices.  ``mats`` as for ssnal_en_server_create; the
     device tensors must stay alive for the server's lifetime."""
 
-    def __init__(self, mats, workers=8, options: Options | None = None, max_bytes=0):
+    def __init__(self, mats, workers=8, options: Options | None = None, max_bytes=0, group: int | None = None):
         self._keep = mats
         self.n = [A.shape[0] for A, _, _, _, _ in mats]
         self.h = ssnal_en_server_create(mats, workers, options, max_bytes)
+        if group is not None:
+            ssnal_en_server_set_group(self.h, group)
 
     def submit(self, mat, b_host, lambda1, lambda2) -> int:
         return ssnal_en_server_submit(self.h, mat, b_host, lambda1, lambda2)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libssnal_en.so")
-SOURCES = ["api.cu", "kern_stream.cu", "kern_vec.cu", "kern_linalg.cu", "kern_tc.cu", "kern_f64.cu", "kern_cg.cu", "noalloc.cu", "batch.cu", "serve.cu"]
+SOURCES = ["api.cu", "kern_stream.cu", "kern_vec.cu", "kern_linalg.cu", "kern_tc.cu", "kern_f64.cu", "kern_cg.cu", "kern_multi.cu", "kern_batch.cu", "noalloc.cu", "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

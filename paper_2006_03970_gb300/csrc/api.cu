@@ -691,18 +691,68 @@ ssnal_en_status clear_newton_flags(ssnal_en_ctx* c) {
   return SSNAL_EN_OK;
 }
 
+// One fit (Algorithm 1) as a resumable state machine.  fit_begin starts the fit (the
+// initial dual iterate and u = A^T y); fit_advance runs the host side of the SsN / AL
+// loop -- prox / active set / gradient with the state read, the stopping tests, the AL
+// update and the Newton direction -- until the fit needs its pass over A (t = A^T d with
+// the fused line search: NeedPass) or has finished (Done); fit_after_pass queues the
+// line-search trials the pass did not evaluate.  A single fit alternates fit_advance
+// and stream_t (solve_impl); several fits on one matrix share their passes
+// (solve_group).  The kernels each fit launches, and their order, are the same either
+// way, so a fit's iterates do not depend on how its passes are taken.
+enum FitPhase { kFitRunning = 0, kFitNeedPass = 1, kFitDone = 2 };
+
+struct FitState {
+  ssnal_en_ctx* c = nullptr;
+  const double* b = nullptr;
+  double lam1 = 0.0, lam2 = 0.0;
+  double* x = nullptr;
+  double* y_io = nullptr;
+  ssnal_en_result R{};
+  std::chrono::steady_clock::time_point t0;
+  double nb1 = 0.0;
+  ProxParams pp{};
+  double sigma = 0.0, kappa = 0.0;
+  int al = 0, apply = 0, newton_here = 0;
+  bool fresh = true;
+  // Newton systems in FP64: always on request; otherwise from the first step whose FP32
+  // factor failed or whose refinement did not contract to the end of this fit (sigma
+  // only grows within a fit, so the FP32 system would not recover).
+  bool use_f64 = false;
+  int extra_refine = 0;  // refinement steps added after a slowly contracting FP32 solve
+  double kkt1 = INFINITY, kkt3 = INFINITY;
+  int converged = 0, failed = 0;
+  int phase = kFitRunning;
+};
+
+void fit_al_begin(FitState& F) {
+  F.pp = make_pp(F.sigma, F.lam1, F.lam2);
+  F.kappa = F.sigma / (1.0 + F.sigma * F.lam2);
+  F.apply = 0;
+  F.newton_here = 0;
+  F.fresh = true;  // u = A^T y to the stream's full accuracy (false after FP32-accumulated steps)
+}
+
 // nb1_known > 0: 1 + ||b|| of this b, already known (points of one path); else it is
-// computed here (one host round trip).
-ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double lam2, double* x, double* y_io,
-                           ssnal_en_result* out, double nb1_known = 0.0) {
-  auto t0 = std::chrono::steady_clock::now();
+// computed here (one host round trip).  atb (may be null): A^T b of this b, just formed by
+// the ||A^T b||_inf pass with the arithmetic of the u = A^T y pass; when the fit starts at
+// x = 0 (y0 = -b) the initial u is then -atb, bitwise what the pass over A would give (the
+// pass is odd in its vector: the split, the products and every sum change sign exactly).
+ssnal_en_status fit_begin(FitState& F, ssnal_en_ctx* c, const double* b, double lam1, double lam2, double* x,
+                          double* y_io, double nb1_known, const double* atb = nullptr) {
+  F = FitState();
+  F.c = c;
+  F.b = b;
+  F.lam1 = lam1;
+  F.lam2 = lam2;
+  F.x = x;
+  F.y_io = y_io;
+  F.t0 = std::chrono::steady_clock::now();
+  F.R.lambda1 = lam1;
+  F.R.lambda2 = lam2;
   const ssnal_en_options& o = c->opt;
   cudaStream_t s = c->stream;
   const int m = (int)c->m;
-  ssnal_en_result R;
-  memset(&R, 0, sizeof(R));
-  R.lambda1 = lam1;
-  R.lambda2 = lam2;
   launch_solve_begin(c->st, c->bdev, b, m, s);  // state := 0, bdev := b
   ssnal_en_status e = SSNAL_EN_OK;
   double nb1 = nb1_known;
@@ -714,118 +764,229 @@ ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double
     nb1 = 1.0 + sqrt(c->st_host->g2);
   }
   c->last_nb1 = nb1;
+  F.nb1 = nb1;
   // ---- initial dual iterate and u = A^T y (reading: y0 = A x0 - b)
   ProxParams pp = make_pp(o.sigma0, lam1, lam2);
+  bool cold = false;  // x0 = 0, so y0 = -b
   if (o.use_y0 && y_io) {
     CK(cudaMemcpyAsync(c->y, y_io, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   } else {
     if ((e = prox_gather_grad(c, kProxSupport, x, c->bdev, pp, 0)) != SSNAL_EN_OK) return e;
+    cold = c->st_host->r == 0;
   }
-  {
+  if (cold && atb) {
+    launch_neg_f64(c->u, atb, c->n, c->sms, s);
+  } else {
     PhaseTimer timer(c, kPhaseRefresh);
     run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
   }
   CK(cudaGetLastError());
-  double sigma = o.sigma0;
-  int converged = 0, failed = 0;
-  int al = 0;
-  // Newton systems in FP64: always on request; otherwise from the first step whose FP32
-  // factor failed or whose refinement did not contract to the end of this fit (sigma
-  // only grows within a fit, so the FP32 system would not recover).
-  bool use_f64 = o.newton_fp64 == 1;
-  int extra_refine = 0;  // refinement steps added after a slowly contracting FP32 solve
-  double kkt1 = INFINITY, kkt3 = INFINITY;
-  for (al = 1; al <= o.max_al; al++) {
-    pp = make_pp(sigma, lam1, lam2);
-    const double kappa = sigma / (1.0 + sigma * lam2);
-    int apply = 0;
-    int newton_here = 0;
-    bool fresh = true;  // u = A^T y to the stream's full accuracy (false after FP32-accumulated steps)
+  F.sigma = o.sigma0;
+  F.use_f64 = o.newton_fp64 == 1;
+  F.al = 1;
+  fit_al_begin(F);
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status fit_advance(FitState& F) {
+  ssnal_en_ctx* c = F.c;
+  const ssnal_en_options& o = c->opt;
+  cudaStream_t s = c->stream;
+  ssnal_en_status e = SSNAL_EN_OK;
+  F.phase = kFitRunning;
+  while (F.al <= o.max_al) {
+    // ---- SsN loop of AL iteration F.al (Algorithm 1, lower half)
+    bool stop_ssn = false;
     for (;;) {
-      if ((e = prox_gather_grad(c, kProxThreshold, x, c->bdev, pp, apply)) != SSNAL_EN_OK) return e;
+      if ((e = prox_gather_grad(c, kProxThreshold, F.x, c->bdev, F.pp, F.apply)) != SSNAL_EN_OK) return e;
       const DevState& h = *c->st_host;
-      if (apply) R.ls_trials += h.ls_k + 1;
-      apply = 0;
+      if (F.apply) F.R.ls_trials += h.ls_k + 1;
+      F.apply = 0;
       if (h.chol_fail | h.newton_bad | h.f64_fail) {
         // The last direction came from an unreliable FP32 solve (non-positive pivot, or a
         // refinement that does not contract) or a failed FP64 factor; the prox pass above
         // did not apply it, so y and u are those of the step before.
         if (h.f64_fail) {  // the Newton matrix is not positive definite even in FP64
-          failed = 1;
+          F.failed = 1;
+          stop_ssn = true;
           break;
         }
         if ((e = clear_newton_flags(c)) != SSNAL_EN_OK) return e;
-        use_f64 = true;  // recompute this direction, and the rest of the fit, in FP64
-      } else if (h.refine_ratio > kRefineMore && extra_refine < kRefineExtraMax && c->opt.refine_steps > 0) {
-        extra_refine++;  // the FP32 solve contracts slowly: one more refinement step from now on
+        F.use_f64 = true;  // recompute this direction, and the rest of the fit, in FP64
+      } else if (h.refine_ratio > kRefineMore && F.extra_refine < kRefineExtraMax && o.refine_steps > 0) {
+        F.extra_refine++;  // the FP32 solve contracts slowly: one more refinement step from now on
       }
-      const double gn = sqrt(h.g2) / nb1;
-      if (!(gn > o.tol) || newton_here >= o.max_newton) {
-        if (!fresh) {
+      const double gn = sqrt(h.g2) / F.nb1;
+      if (!(gn > o.tol) || F.newton_here >= o.max_newton) {
+        if (!F.fresh) {
           // mixed precision: recompute u = A^T y in float-float before the SsN
           // stopping test is trusted (the KKT residuals and the x update read u)
           {
             PhaseTimer timer(c, kPhaseRefresh);
-            run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, pp);
+            run_stream(c, kModeU, c->y, c->u, nullptr, nullptr, F.pp);
           }
           CK(cudaGetLastError());
-          fresh = true;
+          F.fresh = true;
           continue;
         }
+        stop_ssn = true;
         break;
       }
-      fresh = !mixed_stream(c);
+      F.fresh = !mixed_stream(c);
       const int64_t r = h.r;
       if (use_cg(c, r)) {
         int it = 0;
-        if ((e = newton_direction_cg(c, r, kappa, c->g, c->d, c->y, c->bdev, 1, &it)) != SSNAL_EN_OK) return e;
-        R.cg_iters += it;
-      } else if (use_f64) {
-        if ((e = newton_direction_f64(c, r, kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
-        R.newton_fp64++;
-      } else if ((e = newton_direction(c, r, kappa, c->g, c->d, c->y, c->bdev, 1, extra_refine)) != SSNAL_EN_OK) {
+        if ((e = newton_direction_cg(c, r, F.kappa, c->g, c->d, c->y, c->bdev, 1, &it)) != SSNAL_EN_OK) return e;
+        F.R.cg_iters += it;
+      } else if (F.use_f64) {
+        if ((e = newton_direction_f64(c, r, F.kappa, c->g, c->d, c->y, c->bdev, 1)) != SSNAL_EN_OK) return e;
+        F.R.newton_fp64++;
+      } else if ((e = newton_direction(c, r, F.kappa, c->g, c->d, c->y, c->bdev, 1, F.extra_refine)) !=
+                 SSNAL_EN_OK) {
         return e;
       }
-      if ((e = stream_t(c, x, pp)) != SSNAL_EN_OK) return e;
-      launch_ls_fallback(x, c->u, c->t, c->n, pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st, c->partials,
-                         c->grid_stream, s);
-      CK(cudaGetLastError());
-      apply = 1;
-      newton_here++;
-      R.newton_iters++;
+      F.phase = kFitNeedPass;  // the caller runs t = A^T d with the fused line search
+      return SSNAL_EN_OK;
     }
+    (void)stop_ssn;
     const DevState& h = *c->st_host;
     // AL step (2) via the Moreau decomposition; residuals of eq. kkt_res.
-    kkt1 = sqrt(h.g2) / nb1;
-    const double aty_z = sqrt(h.xw2) / sigma;
-    const double znorm = sqrt(h.vw2) / sigma;
-    kkt3 = aty_z / (1.0 + sqrt(h.y2) + znorm);
-    R.active = h.r;
-    R.primal_obj = 0.5 * h.yg2 + lam1 * h.w1 + 0.5 * lam2 * h.w2;
-    const double dual = -(0.5 * h.y2 + h.by) - (lam2 > 0 ? h.dualpen / (2.0 * lam2) : 0.0);
-    R.dual_gap = lam2 > 0 ? R.primal_obj - dual : NAN;
-    R.sigma = sigma;
+    F.kkt1 = sqrt(h.g2) / F.nb1;
+    const double aty_z = sqrt(h.xw2) / F.sigma;
+    const double znorm = sqrt(h.vw2) / F.sigma;
+    F.kkt3 = aty_z / (1.0 + sqrt(h.y2) + znorm);
+    F.R.active = h.r;
+    F.R.primal_obj = 0.5 * h.yg2 + F.lam1 * h.w1 + 0.5 * F.lam2 * h.w2;
+    const double dual = -(0.5 * h.y2 + h.by) - (F.lam2 > 0 ? h.dualpen / (2.0 * F.lam2) : 0.0);
+    F.R.dual_gap = F.lam2 > 0 ? F.R.primal_obj - dual : NAN;
+    F.R.sigma = F.sigma;
     {
       PhaseTimer timer(c, kPhaseUpdate);
-      launch_set_x(x, c->u, c->n, pp, c->sms, s);
+      launch_set_x(F.x, c->u, c->n, F.pp, c->sms, s);
     }
     CK(cudaGetLastError());
-    if (failed) break;
-    if (kkt1 <= o.tol && kkt3 <= o.tol) {
-      converged = 1;
+    if (F.failed) break;
+    if (F.kkt1 <= o.tol && F.kkt3 <= o.tol) {
+      F.converged = 1;
       break;
     }
-    sigma = fmin(sigma * o.sigma_growth, o.sigma_max);
+    F.sigma = fmin(F.sigma * o.sigma_growth, o.sigma_max);
+    F.al++;
+    if (F.al <= o.max_al) fit_al_begin(F);
   }
-  if (y_io) CK(cudaMemcpyAsync(y_io, c->y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  F.phase = kFitDone;
+  return SSNAL_EN_OK;
+}
+
+// After the pass over A of a Newton step: the trials the pass did not evaluate.
+ssnal_en_status fit_after_pass(FitState& F) {
+  ssnal_en_ctx* c = F.c;
+  const ssnal_en_options& o = c->opt;
+  launch_ls_fallback(F.x, c->u, c->t, c->n, F.pp, o.mu, o.beta, o.max_ls, o.ls_fused, c->st, c->partials,
+                     c->grid_stream, c->stream);
+  CK(cudaGetLastError());
+  F.apply = 1;
+  F.newton_here++;
+  F.R.newton_iters++;
+  return SSNAL_EN_OK;
+}
+
+ssnal_en_status fit_finish(FitState& F, ssnal_en_result* out) {
+  ssnal_en_ctx* c = F.c;
+  const ssnal_en_options& o = c->opt;
+  cudaStream_t s = c->stream;
+  if (F.y_io) CK(cudaMemcpyAsync(F.y_io, c->y, sizeof(double) * c->m, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
-  R.al_iters = al > o.max_al ? o.max_al : al;
-  R.kkt1 = kkt1;
-  R.kkt3 = kkt3;
-  R.status = converged ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
-  R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (out) *out = R;
-  return converged ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
+  F.R.al_iters = F.al > o.max_al ? o.max_al : F.al;
+  F.R.kkt1 = F.kkt1;
+  F.R.kkt3 = F.kkt3;
+  F.R.status = F.converged ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
+  F.R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - F.t0).count();
+  if (out) *out = F.R;
+  return F.converged ? SSNAL_EN_OK : SSNAL_EN_ENOCONV;
+}
+
+// nb1_known > 0: 1 + ||b|| of this b, already known (points of one path); else it is
+// computed here (one host round trip).
+ssnal_en_status solve_impl(ssnal_en_ctx* c, const double* b, double lam1, double lam2, double* x, double* y_io,
+                           ssnal_en_result* out, double nb1_known = 0.0, const double* atb = nullptr) {
+  FitState F;
+  ssnal_en_status e = fit_begin(F, c, b, lam1, lam2, x, y_io, nb1_known, atb);
+  if (e != SSNAL_EN_OK) return e;
+  for (;;) {
+    if ((e = fit_advance(F)) != SSNAL_EN_OK) return e;
+    if (F.phase == kFitDone) break;
+    if ((e = stream_t(c, F.x, F.pp)) != SSNAL_EN_OK) return e;
+    if ((e = fit_after_pass(F)) != SSNAL_EN_OK) return e;
+  }
+  return fit_finish(F, out);
+}
+
+// True when the contexts of fits[0..k) stream the same matrix with the same element
+// type and line-search options, so that their Newton-step passes can be merged.
+bool can_merge(FitState* const* fits, int k) {
+  const ssnal_en_ctx* a = fits[0]->c;
+  if (a->stream_kind != kStreamLane || !a->tmap_ok) return false;
+  const int elt = lane_elt(a, kModeT);
+  if (elt != kLaneBf16 && elt != kLaneF32 && elt != kLaneI8 && elt != kLaneI2) return false;
+  for (int i = 1; i < k; i++) {
+    const ssnal_en_ctx* b = fits[i]->c;
+    if (b->A != a->A || b->m != a->m || b->n != a->n || b->lda != a->lda || b->dtype != a->dtype ||
+        b->col_mean != a->col_mean || b->col_scale != a->col_scale || lane_elt(b, kModeT) != elt ||
+        b->stream_kind != kStreamLane || !b->tmap_ok || b->opt.mu != a->opt.mu || b->opt.beta != a->opt.beta ||
+        b->opt.max_ls != a->opt.max_ls || b->opt.ls_fused != a->opt.ls_fused || b->stream != a->stream)
+      return false;
+  }
+  return true;
+}
+
+// The Newton-step passes of the fits that need one: merged into passes of up to
+// kMultiVectors fits where the contexts allow (same matrix, FP32-accumulated pass,
+// same stream), else one pass per fit; then each fit's remaining trials.  *passes
+// receives the number of passes over A.
+ssnal_en_status run_passes(FitState* const* fits, int k, int* passes) {
+  ssnal_en_status e = SSNAL_EN_OK;
+  int np = 0;
+  const bool merge = k > 1 && can_merge(fits, k);
+  for (int i0 = 0; i0 < k;) {
+    const int nv = merge ? (k - i0 < kMultiVectors ? k - i0 : kMultiVectors) : 1;
+    bool done = false;
+    if (nv > 1) {
+      ssnal_en_ctx* a = fits[i0]->c;
+      const ssnal_en_options& o = a->opt;
+      const double* d[kMultiVectors];
+      double* t[kMultiVectors];
+      const double* x[kMultiVectors];
+      const double* u[kMultiVectors];
+      DevState* st[kMultiVectors];
+      double* part[kMultiVectors];
+      ProxParams pp[kMultiVectors];
+      for (int f = 0; f < nv; f++) {
+        ssnal_en_ctx* c = fits[i0 + f]->c;
+        d[f] = c->d;
+        t[f] = c->t;
+        x[f] = fits[i0 + f]->x;
+        u[f] = c->u;
+        st[f] = c->st;
+        part[f] = c->partials;
+        pp[f] = fits[i0 + f]->pp;
+      }
+      done = launch_stream_multi(lane_elt(a, kModeT), a->tmap, (int)a->m, a->n, nv, d, t, x, u, st, part, pp, o.mu,
+                                 o.beta, o.max_ls, o.ls_fused, a->sms, a->stream, a->col_mean, a->col_scale);
+    }
+    if (!done) {
+      for (int f = 0; f < nv; f++)
+        if ((e = stream_t(fits[i0 + f]->c, fits[i0 + f]->x, fits[i0 + f]->pp)) != SSNAL_EN_OK) return e;
+      np += nv;
+    } else {
+      np += 1;
+    }
+    for (int f = 0; f < nv; f++)
+      if ((e = fit_after_pass(*fits[i0 + f])) != SSNAL_EN_OK) return e;
+    i0 += nv;
+  }
+  if (passes) *passes += np;
+  return SSNAL_EN_OK;
 }
 
 ssnal_en_status check_options(const ssnal_en_options* o) {
@@ -873,6 +1034,50 @@ cudaStream_t ctx_set_stream(ssnal_en_ctx* c, cudaStream_t s) {
   return old;
 }
 double ctx_mn(const ssnal_en_ctx* c) { return (double)c->m * (double)c->n; }
+
+// ---- fits advanced together (the serving loop's groups); see FitState
+struct Fit {
+  FitState F;
+};
+Fit* fit_new() { return new (std::nothrow) Fit(); }
+void fit_delete(Fit* f) { delete f; }
+int fit_phase(const Fit* f) { return f->F.phase; }
+
+// Starts a fit on c: penalties (lambda1, lambda2) = (p1, p2), or with scaled != 0 the
+// parameterisation of Sec. 4.1: lambda1 = c ||A^T b||_inf, lambda2 = (1 - alpha)/alpha c
+// ||A^T b||_inf with (alpha, c) = (p1, p2), ||A^T b||_inf from one pass over A.
+ssnal_en_status fit_start(Fit* f, ssnal_en_ctx* c, const double* b, int scaled, double p1, double p2, double* x,
+                          double* lambdas_out) {
+  double lam1 = p1, lam2 = p2;
+  if (scaled) {
+    CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+    ProxParams pp0 = make_pp(c->opt.sigma0, 0.0, 0.0);
+    run_stream(c, kModeGmax, b, c->t, nullptr, nullptr, pp0);
+    CK(cudaGetLastError());
+    ssnal_en_status e = read_state(c);
+    if (e != SSNAL_EN_OK) return e;
+    const double gmax = c->st_host->gmax;
+    lam1 = p2 * gmax;
+    lam2 = (1.0 - p1) / p1 * p2 * gmax;
+  }
+  if (lambdas_out) {
+    lambdas_out[0] = lam1;
+    lambdas_out[1] = lam2;
+  }
+  const int use_y0 = c->opt.use_y0;
+  c->opt.use_y0 = 0;
+  // after the ||A^T b||_inf pass, t holds A^T b (the initial u of a cold start is -t)
+  ssnal_en_status e = fit_begin(f->F, c, b, lam1, lam2, x, nullptr, 0.0, scaled ? c->t : nullptr);
+  c->opt.use_y0 = use_y0;
+  return e;
+}
+ssnal_en_status fit_step(Fit* f) { return fit_advance(f->F); }
+ssnal_en_status fit_passes(Fit* const* f, int k, int* passes) {
+  std::vector<FitState*> v((size_t)k);
+  for (int i = 0; i < k; i++) v[(size_t)i] = &f[i]->F;
+  return run_passes(v.data(), k, passes);
+}
+ssnal_en_status fit_end(Fit* f, ssnal_en_result* out) { return fit_finish(f->F, out); }
 }  // namespace ssnal
 
 extern "C" {
@@ -1060,6 +1265,73 @@ ssnal_en_status ssnal_en_solve(ssnal_en_ctx* c, const double* b, double lambda1,
   return solve_impl(c, b, lambda1, lambda2, x, y, out);
 }
 
+ssnal_en_status ssnal_en_solve_shared(ssnal_en_instance* inst, int32_t count, ssnal_en_result* out, int32_t* passes) {
+  if (passes) *passes = 0;
+  if (!inst || count < 1) return SSNAL_EN_EINVAL;
+  for (int32_t i = 0; i < count; i++) {
+    const ssnal_en_instance& q = inst[i];
+    if (!q.ctx || !q.b || !q.x || !is_finite_d(q.lambda1) || !is_finite_d(q.lambda2) || q.lambda1 < 0 ||
+        q.lambda2 < 0)
+      return SSNAL_EN_EINVAL;
+    if (q.ctx->opt.use_y0 && !q.y) return SSNAL_EN_EINVAL;
+    for (int32_t j = 0; j < i; j++)
+      if (inst[j].ctx == q.ctx) return SSNAL_EN_EINVAL;  // every fit needs its own workspaces
+  }
+  // all fits run on the first context's stream (their kernels and the merged passes are
+  // ordered on it); the contexts' own streams are restored at the end
+  cudaStream_t s0 = inst[0].ctx->stream;
+  std::vector<cudaStream_t> saved((size_t)count);
+  for (int32_t i = 0; i < count; i++) {
+    saved[(size_t)i] = inst[i].ctx->stream;
+    if (i > 0) {
+      CK(cudaStreamSynchronize(inst[i].ctx->stream));
+      inst[i].ctx->stream = s0;
+    }
+  }
+  std::vector<FitState> F((size_t)count);
+  std::vector<ssnal_en_status> st((size_t)count, SSNAL_EN_OK);
+  for (int32_t i = 0; i < count; i++) {
+    st[(size_t)i] = fit_begin(F[(size_t)i], inst[i].ctx, inst[i].b, inst[i].lambda1, inst[i].lambda2, inst[i].x,
+                              inst[i].y, 0.0);
+    if (st[(size_t)i] != SSNAL_EN_OK) F[(size_t)i].phase = kFitDone;
+  }
+  int np = 0;
+  for (;;) {
+    std::vector<FitState*> need;
+    for (int32_t i = 0; i < count; i++) {
+      FitState& f = F[(size_t)i];
+      if (f.phase == kFitDone || st[(size_t)i] != SSNAL_EN_OK) continue;
+      if ((st[(size_t)i] = fit_advance(f)) != SSNAL_EN_OK) {
+        f.phase = kFitDone;
+        continue;
+      }
+      if (f.phase == kFitNeedPass) need.push_back(&f);
+    }
+    if (need.empty()) break;
+    ssnal_en_status e = run_passes(need.data(), (int)need.size(), &np);
+    if (e != SSNAL_EN_OK) {
+      for (FitState* f : need) st[(size_t)(f - F.data())] = e;
+      for (FitState* f : need) f->phase = kFitDone;
+    }
+  }
+  ssnal_en_status worst = SSNAL_EN_OK;
+  for (int32_t i = 0; i < count; i++) {
+    ssnal_en_result r{};
+    if (st[(size_t)i] == SSNAL_EN_OK) {
+      st[(size_t)i] = fit_finish(F[(size_t)i], &r);
+    } else {
+      r = F[(size_t)i].R;
+      r.status = st[(size_t)i];
+    }
+    if (out) out[i] = r;
+    if (st[(size_t)i] != SSNAL_EN_OK && worst == SSNAL_EN_OK) worst = st[(size_t)i];
+  }
+  CK(cudaStreamSynchronize(s0));
+  for (int32_t i = 0; i < count; i++) inst[i].ctx->stream = saved[(size_t)i];
+  if (passes) *passes = np;
+  return worst;
+}
+
 ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, const double* c_grid, int32_t K,
                               double* X, ssnal_en_result* out, int32_t* n_done) {
   if (n_done) *n_done = 0;
@@ -1086,7 +1358,8 @@ ssnal_en_status ssnal_en_path(ssnal_en_ctx* c, const double* b, double alpha, co
     const double lam1 = c_grid[k] * gmax;
     const double lam2 = (1.0 - alpha) / alpha * c_grid[k] * gmax;
     ssnal_en_result r;
-    e = solve_impl(c, b, lam1, lam2, c->xpath, nullptr, &r, nb1);
+    // the first point starts at x = 0: its initial u is -A^T b from the pass above
+    e = solve_impl(c, b, lam1, lam2, c->xpath, nullptr, &r, nb1, k == 0 ? c->t : nullptr);
     nb1 = c->last_nb1;
     if (e != SSNAL_EN_OK && e != SSNAL_EN_ENOCONV) {
       c->opt = saved;

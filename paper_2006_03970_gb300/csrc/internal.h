@@ -7,7 +7,7 @@
 
 #include <atomic>
 
-struct ssnal_en_ctx;
+#include "../../include/ssnal_en.h"
 
 namespace ssnal {
 
@@ -93,6 +93,8 @@ int vec_grid(long long n, int sms);
 void launch_solve_begin(DevState* st, double* bdev, const double* b, int m, cudaStream_t s);
 // dst[0..n) = src[0..n) on the stream.
 void launch_copy_f64(double* dst, const double* src, long long n, int sms, cudaStream_t s);
+// dst[0..n) = -src[0..n) on the stream.
+void launch_neg_f64(double* dst, const double* src, long long n, int sms, cudaStream_t s);
 // Copies *st to the pinned, device-mapped host mirror and then writes seq to flag
 // (host memory), after a system-scope fence.
 void launch_state_out(const DevState* st, DevState* host, unsigned* flag, unsigned seq, cudaStream_t s);
@@ -165,6 +167,31 @@ void launch_trsv64(const double* L, long long ldl, int N, const double* rhs, dou
 // error of the solution it corrects; above 1/2 the refinement does not contract).
 void launch_refine_update(double* acc, const double* c, int len, double tau, DevState* st, cudaStream_t s);
 
+// ---- one pass over A for several fits on the same matrix (kern_multi.cu): t_f = A^T d_f
+// with each fit's fused line search, nv <= 4 vectors, element types with FP32
+// accumulation (kLaneBf16, kLaneF32, kLaneI8, kLaneI2).  Returns false (nothing
+// launched) for an unsupported element type or size.
+constexpr int kMultiVectors = 4;
+bool launch_stream_multi(int elt, const void* map, int m, long long n, int nv, const double* const* d, double* const* t,
+                         const double* const* x, const double* const* u, DevState* const* st,
+                         double* const* partials, const ProxParams* pp, double mu, double beta, int max_ls, int fused,
+                         int sms, cudaStream_t s, const float* cmean, const float* cscale);
+
+// ---- device-resident batched solver (kern_batch.cu): one persistent kernel, one CTA per
+// instance at a time, the whole AL / SsN loop on the device (FP32 storage)
+constexpr int kBatchMaxM = 1024;  // rows per instance (the Cholesky panel lives in shared memory)
+size_t batch_smem_bytes(int m_max);
+size_t batch_slot_bytes(long long n_max, int m_max);
+size_t batch_inst_bytes();
+size_t batch_out_bytes();
+void batch_fill_inst(void* dst, const float* A, long long lda, long long n, int m, const double* b, double lam1,
+                     double lam2, double* x);
+void batch_read_out(const void* src, ssnal_en_result* r, int* needs_host);
+// opt6: sigma0, sigma_growth, sigma_max, mu, beta, tol; opt4: max_al, max_newton, max_ls, refine
+bool launch_batch_solve(const void* inst_dev, const int* order_dev, int count, int* next_dev, void* out_dev,
+                        const double* opt6, const int* opt4, long long n_max, int m_max, unsigned char* scratch,
+                        int blocks, int threads, cudaStream_t s);
+
 // ---- conjugate-gradient Newton solve (kern_cg.cu), m <= 4096
 // d = 0, res = p = -g, rr = ||g||^2, stop when ||res|| <= rtol ||g||
 void launch_cg_init(const double* g, double* d, double* res, double* p, int m, double rtol, DevState* st,
@@ -203,5 +230,19 @@ double ctx_mn(const ssnal_en_ctx* c);  // m * n of the context's matrix
 int64_t ctx_m(const ssnal_en_ctx* c);  // m of the context's matrix
 // frees a panel wider than keep_cols columns (regrown on demand)
 void ctx_trim(ssnal_en_ctx* c, int64_t keep_cols);
+
+// ---- fits advanced together, one Newton step at a time (api.cu); the passes over A of
+// the fits that need one are merged where their contexts share the matrix
+struct Fit;
+enum { kFitPhaseRunning = 0, kFitPhaseNeedPass = 1, kFitPhaseDone = 2 };
+Fit* fit_new();
+void fit_delete(Fit* f);
+int fit_phase(const Fit* f);
+// scaled = 0: penalties (p1, p2); scaled = 1: (alpha, c) = (p1, p2) relative to ||A^T b||_inf
+ssnal_en_status fit_start(Fit* f, ssnal_en_ctx* c, const double* b, int scaled, double p1, double p2, double* x,
+                          double* lambdas_out);
+ssnal_en_status fit_step(Fit* f);                               // until a pass is needed or the fit is done
+ssnal_en_status fit_passes(Fit* const* f, int k, int* passes);  // the passes of k fits that need one
+ssnal_en_status fit_end(Fit* f, ssnal_en_result* out);          // synchronises the fit's stream
 
 }  // namespace ssnal

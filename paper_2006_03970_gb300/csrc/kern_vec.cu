@@ -710,6 +710,13 @@ __global__ void k_copy_f64(double* __restrict__ dst, const double* __restrict__ 
   for (long long i = tid; i < n; i += nt) dst[i] = src[i];
 }
 
+// dst[0..n) = -src[0..n) (FP64, grid-stride; negation is exact).
+__global__ void k_neg_f64(double* __restrict__ dst, const double* __restrict__ src, long long n) {
+  pdl_entry();
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < n; i += nt) dst[i] = -src[i];
+}
+
 // ---------------------------------------------------------------- launchers
 void launch_solve_begin(DevState* st, double* bdev, const double* b, int m, cudaStream_t s) {
   count_launch();
@@ -723,6 +730,14 @@ void launch_copy_f64(double* dst, const double* src, long long n, int sms, cudaS
   if (g < 1) g = 1;
   count_launch();
   launch_k(k_copy_f64, dim3((int)g), dim3(256), (size_t)0, s, dst, src, n);
+}
+
+void launch_neg_f64(double* dst, const double* src, long long n, int sms, cudaStream_t s) {
+  long long g = (n + 255) / 256;
+  if (g > 4LL * sms) g = 4LL * sms;
+  if (g < 1) g = 1;
+  count_launch();
+  launch_k(k_neg_f64, dim3((int)g), dim3(256), (size_t)0, s, dst, src, n);
 }
 
 void launch_state_out(const DevState* st, DevState* host, unsigned* flag, unsigned seq, cudaStream_t s) {

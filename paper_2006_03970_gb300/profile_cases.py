@@ -10,8 +10,10 @@ or two while its operands still exceed the 129 MB L2 of a GB300:
                    r = 730 (the active-set size of the precision workload at alpha 0.5) on
                    BF16 storage: the BF16 tensor-core SYRK, the cluster Cholesky and the
                    triangular solves with their refinement
+  shared-4         four mixed-form fits on the precision-small matrix advanced together
+                   (ssnal_en_solve_shared): one merged pass over A per Newton step
 
-    python -m paper_2006_03970_gb300.profile_cases precision-small
+    python -m paper_2006_03970_gb300.profile_cases precision-small [newton-730 ...]
 """
 from __future__ import annotations
 
@@ -60,16 +62,43 @@ def newton_730(m=1000, r=730, repeats=3):
     return float(d.abs().max())
 
 
-CASES = {"precision-small": precision_small, "newton-730": newton_730}
+def shared_4(n=100_000, m=1000):
+    """Four mixed-form fits on the precision-small matrix through ssnal_en_solve_shared: their
+    Newton-step passes over A merged into one k_stream_multi launch per step."""
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    p = synth.config3(m=m, n=n)
+    bits = synth.to_bf16_bits(p.At)
+    opts = pkg.ssnal_en_default_options(precision=1)
+    A, mm = pkg.device_matrix(bits, pkg.BF16)
+    ctxs = [pkg.Context(A, m=mm, dtype=pkg.BF16, options=opts) for _ in range(4)]
+    rng = np.random.default_rng(4)
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    inst = []
+    for i, c in enumerate(ctxs):
+        b = torch.as_tensor(p.b + 0.1 * rng.standard_normal(m), device="cuda")
+        pkg.ssnal_en_op_at_y(c.ctx, b, u)
+        g = u.abs().max().item()
+        inst.append((c.ctx, b, 0.3 * g, 0.3 * g, torch.zeros(n, dtype=torch.float64, device="cuda"), None))
+    st, res, passes = pkg.ssnal_en_solve_shared(inst)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.close()
+    return st, [r.newton_iters for r in res], passes
+
+
+CASES = {"precision-small": precision_small, "newton-730": newton_730, "shared-4": shared_4}
 
 
 def main(argv):
-    if len(argv) != 1 or argv[0] not in CASES:
+    if not argv or any(a not in CASES for a in argv):
         print(__doc__)
         return 2
     import paper_2006_03970_gb300 as pkg
     pkg.load_library()
-    print(argv[0], CASES[argv[0]]())
+    for a in argv:
+        print(a, CASES[a]())
     return 0
 
 

@@ -49,6 +49,7 @@ def test_struct_layouts(lib):
     assert ctypes.sizeof(pkg.Result) == 4 * 4 + 8 + 8 * 8 + 2 * 4
     assert ctypes.sizeof(pkg.Instance) == 6 * 8
     assert ctypes.sizeof(pkg.TunePoint) == 5 * 8
+    assert ctypes.sizeof(pkg.BatchFit) == 8 * 8
 
 
 def test_default_options_without_gpu(lib):

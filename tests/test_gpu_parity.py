@@ -408,3 +408,28 @@ def test_profile_times_one_stream_launch_in_eight_and_all_at_level_two():
         if level2:
             assert all(n > 0 for _, n in ph.values())
     ctx.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "bf16"])
+def test_path_first_point_equals_a_cold_solve_bitwise(storage):
+    # the path's first point takes its initial u = A^T(-b) as the negation of the
+    # ||A^T b||_inf pass (the pass is odd in its vector); a cold solve runs the pass itself
+    p = synth.make_problem(90, 4000, k=8, seed=31, block=20, rho=0.6, dtype=np.float32)
+    if storage == "bf16":
+        ctx = pkg.Context(synth.to_bf16_bits(p.At), dtype=pkg.BF16,
+                          options=pkg.ssnal_en_default_options(precision=1))
+    else:
+        ctx = pkg.Context(p.At.astype(np.float64))
+    alpha, c = 0.7, 0.3
+    X, res, done = ctx.path(p.b, alpha, [c])
+    u = torch.empty(ctx.n, dtype=torch.float64, device="cuda")
+    pkg.ssnal_en_op_at_y(ctx.ctx, dev(p.b), u)  # A^T b, the arithmetic of the lambda_max pass
+    gmax = u.abs().max().item()
+    lam1, lam2 = c * gmax, (1.0 - alpha) / alpha * c * gmax
+    x = torch.zeros(ctx.n, dtype=torch.float64, device="cuda")
+    st, r = pkg.ssnal_en_solve(ctx.ctx, dev(p.b), lam1, lam2, x)
+    ctx.close()
+    assert st == pkg.OK and res[0].status == pkg.OK
+    assert (res[0].lambda1, res[0].lambda2) == (lam1, lam2)
+    np.testing.assert_array_equal(X[0].cpu().numpy(), x.cpu().numpy())
+    assert res[0].newton_iters == r.newton_iters

@@ -98,3 +98,25 @@ def test_admission_bound_still_serves_everything():
     for (s0, e0), (s1, e1) in zip(spans, spans[1:]):
         assert s1 >= e0 - 1e-9  # one at a time: no two solves overlap
     assert all(res.status == pkg.OK for _, res, _ in got)
+
+
+@pytest.mark.parametrize("group", [1, 8])
+def test_merged_groups_match_alone(group):
+    # many requests on the same matrices, queued at once: with group 8 the workers advance
+    # up to eight fits of one matrix together and merge their passes over A
+    mats = resident_matrices()
+    opts = pkg.ssnal_en_default_options(precision=1)
+    reqs = requests(mats, 40, 11)
+    srv = pkg.Server([d for d, _ in mats], workers=2, options=opts, group=group)
+    tickets = [srv.submit(k, b, l1, l2) for k, b, l1, l2 in reqs]
+    got = [srv.poll(t, k, wait=True) for t, (k, _, _, _) in zip(tickets, reqs)]
+    srv.close()
+    ctxs = [pkg.Context(A, m=m, dtype=dtype, options=opts, col_mean=cm, col_scale=cs)
+            for (A, m, dtype, cm, cs), _ in mats]
+    for (k, b, l1, l2), (x, res, times) in zip(reqs, got):
+        assert res.status == pkg.OK and res.kkt1 <= 1e-6 and res.kkt3 <= 1e-6
+        xa = torch.zeros(ctxs[k].n, dtype=torch.float64, device="cuda")
+        st, ra = pkg.ssnal_en_solve(ctxs[k].ctx, dev(b), l1, l2, xa)
+        np.testing.assert_array_equal(x, xa.cpu().numpy())
+    for c in ctxs:
+        c.close()
