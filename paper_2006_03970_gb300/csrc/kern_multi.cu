@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_multi(const __grid_cons
     for (long long it = 0; it < total && it < cfg.stages; it++) issue(it);
   __syncwarp();
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  // every vector scaled by its own power of two; DV[f][k] = (dh0, dh1) of rows 2k, 2k + 1
+  // every vector scaled by its own power of two; DV[f][pair_slot(k)] = (dh0, dh1) of rows
+  // 2k, 2k + 1 (the slot order of the single-vector pass)
   for (int f = 0; f < nv; f++) {
     const double* vec = args.f[f].d;
     unsigned long long mb = 0ull;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_multi(const __grid_cons
           const int i = 2 * k + q;
           if (i < m) h[q] = __double2float_rn(vec[i] * scale);
         }
-        DV[(size_t)f * (mpad / 2) + k] =
+        DV[(size_t)f * (mpad / 2) + pair_slot<P>(k)] =
             (unsigned long long)__float_as_uint(h[0]) | ((unsigned long long)__float_as_uint(h[1]) << 32);
       }
     }
@@ -157,11 +158,11 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_multi(const __grid_cons
       const unsigned char* colbase = wring + (size_t)sidx * kLBoxBytes + lane * 128;
       const unsigned long long* DVc = DV + ch * (R / 2);
       // the products of one row pair with every vector, in the single-vector order
-      auto fma_pair = [&](int pair, unsigned long long av, unsigned long long bv) {
+      auto fma_pair = [&](int slot, unsigned long long av, unsigned long long bv) {
 #pragma unroll
         for (int f = 0; f < kMultiMax; f++) {
           if (f < nv) {
-            const unsigned long long d = DVc[(size_t)f * (mpad / 2) + pair];
+            const unsigned long long d = DVc[(size_t)f * (mpad / 2) + slot];
             S2[f] = f2fma(av, d, S2[f]);
             S2b[f] = f2fma(bv, d, S2b[f]);
           }
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_multi(const __grid_cons
                   f2sub((unsigned long long)code_biased(eb[f0], byte) |
                             ((unsigned long long)code_biased(eb[f0 + 1], byte) << 32),
                         bias);
-              fma_pair(P * pp + 8 * qq + e, av, bv);
+              fma_pair(8 * (8 * qq + e) + pp, av, bv);
             }
           }
         } else {
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_multi(const __grid_cons
             bp[1] = (unsigned long long)b.z | ((unsigned long long)b.w << 32);
           }
 #pragma unroll
-          for (int e = 0; e < P; e++) fma_pair(P * pp + e, ap[e], bp[e]);
+          for (int e = 0; e < P; e++) fma_pair(8 * e + pp, ap[e], bp[e]);
         }
       }
       __syncwarp();

@@ -634,7 +634,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     for (long long it = 0; it < total && it < cfg.stages; it++) issue(it);
   __syncwarp();
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  // the vector, scaled by a power of two and split: D4[k] = (dh0, dh1, -dh0, -dh1), DL[k] = (-dl0, -dl1)
+  // the vector, scaled by a power of two and split: row pair k goes to slot pair_slot<P>(k),
+  // D4 = (dh0, dh1, -dh0, -dh1), DL = (-dl0, -dl1)
   unsigned long long mb = 0ull;
   for (int i = tid; i < m; i += blockDim.x) {
     unsigned long long b = (unsigned long long)__double_as_longlong(vec[i]) & 0x7FFFFFFFFFFFFFFFull;
@@ -656,8 +657,9 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
         l[q] = __double2float_rn(v - (double)h[q]);
       }
     }
-    D4[k] = make_float4(h[0], h[1], -h[0], -h[1]);
-    DL[k] = make_float2(-l[0], -l[1]);
+    const int slot = pair_slot<P>(k);
+    D4[slot] = make_float4(h[0], h[1], -h[0], -h[1]);
+    DL[slot] = make_float2(-l[0], -l[1]);
   }
   __syncthreads();
 
@@ -676,7 +678,10 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
   bool timed_out = false;
   long long it = 0;
   for (long long q = 0; q < ngrp; q++) {
+    // float-float: two accumulator pairs per column (odd and even row pairs of a chunk)
+    // for two independent dependency chains; FP32: one FMA chain per column
     unsigned long long S2 = 0ull, L2 = 0ull, S2b = 0ull, L2b = 0ull;
+    unsigned long long S3 = 0ull, L3 = 0ull, S3b = 0ull, L3b = 0ull;
     for (int k = 0; k < nw && !timed_out; k++, it++) {
       const int sidx = (int)(it % cfg.stages);
       if (!mbar_wait(smem_u32(wbars + sidx), (unsigned)((it / cfg.stages) & 1))) {
@@ -686,6 +691,7 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
       const int ch = warp + kLWarps * k;
       const unsigned char* colbase = wring + (size_t)sidx * kLBoxBytes + lane * 128;
       const ulonglong2* D4p = reinterpret_cast<const ulonglong2*>(D4 + ch * (R / 2));
+      const unsigned long long* D4h = reinterpret_cast<const unsigned long long*>(D4 + ch * (R / 2));  // (dh0, dh1)
       const unsigned long long* DLp = reinterpret_cast<const unsigned long long*>(DL + ch * (R / 2));
 #pragma unroll
       for (int p = 0; p < 8; p++) {
@@ -718,14 +724,21 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
                   f2sub((unsigned long long)code_biased(eb[f0], byte) |
                             ((unsigned long long)code_biased(eb[f0 + 1], byte) << 32),
                         bias);
-              const ulonglong2 d = D4p[P * pp + 8 * q + e];
+              const int slot = 8 * (8 * q + e) + pp;
               if constexpr (elt_ff(ELT)) {
-                const unsigned long long dl = DLp[P * pp + 8 * q + e];
-                ff2_madd_exact(S2, L2, av, d.x, d.y, dl);
-                ff2_madd_exact(S2b, L2b, bv, d.x, d.y, dl);
+                const ulonglong2 d = D4p[slot];
+                const unsigned long long dl = DLp[slot];
+                if (e & 1) {
+                  ff2_madd_exact(S3, L3, av, d.x, d.y, dl);
+                  ff2_madd_exact(S3b, L3b, bv, d.x, d.y, dl);
+                } else {
+                  ff2_madd_exact(S2, L2, av, d.x, d.y, dl);
+                  ff2_madd_exact(S2b, L2b, bv, d.x, d.y, dl);
+                }
               } else {
-                S2 = f2fma(av, d.x, S2);
-                S2b = f2fma(bv, d.x, S2b);
+                const unsigned long long dh = D4h[2 * slot];
+                S2 = f2fma(av, dh, S2);
+                S2b = f2fma(bv, dh, S2b);
               }
             }
           }
@@ -734,8 +747,13 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
           const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(colbase + 32 * 128 + pp * 16);
           const ulonglong2 d = D4p[pp];
           const unsigned long long dl = DLp[pp];
-          ff2_madd(S2, L2, a.x, a.y, d.x, d.y, dl);
-          ff2_madd(S2b, L2b, b.x, b.y, d.x, d.y, dl);
+          if (p & 1) {
+            ff2_madd(S3, L3, a.x, a.y, d.x, d.y, dl);
+            ff2_madd(S3b, L3b, b.x, b.y, d.x, d.y, dl);
+          } else {
+            ff2_madd(S2, L2, a.x, a.y, d.x, d.y, dl);
+            ff2_madd(S2b, L2b, b.x, b.y, d.x, d.y, dl);
+          }
         } else {
           const uint4 a = *reinterpret_cast<const uint4*>(colbase + pp * 16);
           const uint4 b = *reinterpret_cast<const uint4*>(colbase + 32 * 128 + pp * 16);
@@ -763,14 +781,21 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
           }
 #pragma unroll
           for (int e = 0; e < P; e++) {
-            const ulonglong2 d = D4p[P * pp + e];
+            const int slot = 8 * e + pp;
             if constexpr (elt_ff(ELT)) {
-              const unsigned long long dl = DLp[P * pp + e];
-              ff2_madd_exact(S2, L2, ap[e], d.x, d.y, dl);
-              ff2_madd_exact(S2b, L2b, bp[e], d.x, d.y, dl);
+              const ulonglong2 d = D4p[slot];
+              const unsigned long long dl = DLp[slot];
+              if (e & 1) {
+                ff2_madd_exact(S3, L3, ap[e], d.x, d.y, dl);
+                ff2_madd_exact(S3b, L3b, bp[e], d.x, d.y, dl);
+              } else {
+                ff2_madd_exact(S2, L2, ap[e], d.x, d.y, dl);
+                ff2_madd_exact(S2b, L2b, bp[e], d.x, d.y, dl);
+              }
             } else {
-              S2 = f2fma(ap[e], d.x, S2);
-              S2b = f2fma(bp[e], d.x, S2b);
+              const unsigned long long dh = D4h[2 * slot];
+              S2 = f2fma(ap[e], dh, S2);
+              S2b = f2fma(bp[e], dh, S2b);
             }
           }
         }
@@ -784,9 +809,15 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     {
       float Sq = lo32f(S2), Lq = lo32f(L2);
       ff_merge(Sq, Lq, hi32f(S2), hi32f(L2));
-      part[q & 1][warp][lane] = make_float2(Sq, Lq);
       float Sb = lo32f(S2b), Lb = lo32f(L2b);
       ff_merge(Sb, Lb, hi32f(S2b), hi32f(L2b));
+      if constexpr (elt_ff(ELT)) {
+        ff_merge(Sq, Lq, lo32f(S3), lo32f(L3));
+        ff_merge(Sq, Lq, hi32f(S3), hi32f(L3));
+        ff_merge(Sb, Lb, lo32f(S3b), lo32f(L3b));
+        ff_merge(Sb, Lb, hi32f(S3b), hi32f(L3b));
+      }
+      part[q & 1][warp][lane] = make_float2(Sq, Lq);
       part[q & 1][warp][lane + 32] = make_float2(Sb, Lb);
     }
     __syncthreads();

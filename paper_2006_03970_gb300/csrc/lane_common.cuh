@@ -122,6 +122,16 @@ __host__ __device__ constexpr int elt_rows(int elt) {
          : (elt == kEltI2FF || elt == kEltI2)         ? 512
                                                       : 32;
 }
+// Shared-memory slot of row pair k of the vector.  A box holds 8P row pairs, P per
+// 16-byte chunk of a column (P = elt_rows / 16); pair e of chunk c sits at slot
+// 8 e + c.  The lanes of a quarter warp read eight different chunks at once (the
+// chunk order is rotated by the lane), so they hit eight consecutive slots: no bank
+// conflicts for 16-byte or 8-byte entries.
+template <int P>
+__device__ __forceinline__ int pair_slot(int k) {
+  const int w = k & (8 * P - 1);
+  return (k - w) + (w & (P - 1)) * 8 + w / P;
+}
 // genotype codes (int8 or 2-bit): the column epilogue applies mean and scale
 __host__ __device__ constexpr bool elt_geno(int elt) {
   return elt == kEltI8FF || elt == kEltI8 || elt == kEltI2FF || elt == kEltI2;
