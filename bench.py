@@ -401,6 +401,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_batch:
         torch.cuda.empty_cache()  # give the library the memory the workloads above left cached
         line["batched"] = batched_fits()
+        line["single_fit"] = small_fit()
     if rank == 0 and world == 1 and not args.no_serve:
         torch.cuda.empty_cache()
         line["serving"] = serve_workload(args.serve_requests, args.serve_matrices)
@@ -583,6 +584,74 @@ def batched_fits(count=512):
                          "loads_in_flight": info[0], "fits_on_regular_path": info[1]},
             "threaded_fits_per_s": ok / dt, "threaded_seconds": dt, "threaded_converged": ok, "workers": used,
             "max_rel_diff_resident_vs_threaded": agree, "sequential_fits_per_s": count / dts}
+
+
+def small_fit(reps=200, copies=None):
+    """The single-fit configuration: m=100, n=2000, iid N(0,1) standardized, 10 nonzeros
+    +-U[1,3], snr 5, alpha 0.8, c 0.5, seed 0, FP64 -- a fit bound by launch latency.
+    Reported: ms per fit of ssnal_en_solve (FP64 storage, each fit from x = 0, one after
+    another), and of the device-resident solver (ssnal_en_solve_batch_resident) on the same
+    matrix stored in FP32: one fit per launch (latency) and one copy per SM in one launch
+    (throughput of independent fits of this size)."""
+    import numpy as np
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    p = synth.config1()
+    m, n = p.At.shape[1], p.At.shape[0]
+    g = np.abs(p.At @ p.b).max()
+    l1, l2 = p.c * g, (1 - p.alpha) / p.alpha * p.c * g
+    ctx = pkg.Context(p.At)
+    b = torch.as_tensor(p.b, device="cuda")
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        x.zero_()
+        pkg.ssnal_en_solve(ctx.ctx, b, l1, l2, x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    kkt = 0.0
+    for _ in range(reps):
+        x.zero_()
+        st, r = pkg.ssnal_en_solve(ctx.ctx, b, l1, l2, x)
+        kkt = max(kkt, r.kkt1, r.kkt3)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    x_reg = x.clone()
+    ctx.close()
+    A32 = torch.as_tensor(np.ascontiguousarray(p.At, dtype=np.float32), device="cuda")
+    copies = copies or torch.cuda.get_device_properties(0).multi_processor_count
+    xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(copies)]
+    one = [(A32, m, b, l1, l2, xs[0])]
+    for _ in range(5):
+        xs[0].zero_()
+        pkg.ssnal_en_solve_batch_resident(one)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        xs[0].zero_()
+        st, res1, info1 = pkg.ssnal_en_solve_batch_resident(one)
+    torch.cuda.synchronize()
+    dt1 = (time.perf_counter() - t0) / reps
+    many = [(A32, m, b, l1, l2, xx) for xx in xs]
+    for xx in xs:
+        xx.zero_()
+    pkg.ssnal_en_solve_batch_resident(many)
+    for xx in xs:
+        xx.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, resm, infom = pkg.ssnal_en_solve_batch_resident(many)
+    torch.cuda.synchronize()
+    dtm = time.perf_counter() - t0
+    okm = sum(1 for r in resm if r.status == 0 and r.kkt1 <= TOL and r.kkt3 <= TOL)
+    diff = float((xs[0] - x_reg).abs().max()) / max(float(x_reg.abs().max()), 1e-300)
+    return {"workload": "m=100, n=2000, iid N(0,1) standardized, 10 nonzeros +-U[1,3], snr 5, alpha 0.8, c 0.5, "
+                        "tol 1e-6, seed 0",
+            "fits_per_s": 1.0 / dt, "ms_per_fit": 1e3 * dt, "storage": "FP64", "max_kkt": kkt,
+            "resident_one_fit": {"ms_per_fit": 1e3 * dt1, "fits_per_s": 1.0 / dt1, "storage": "FP32",
+                                 "active": res1[0].active, "newton_iters": res1[0].newton_iters},
+            "resident_copies": {"copies": copies, "seconds": dtm, "fits_per_s": okm / dtm, "converged": okm},
+            "max_rel_diff_resident_fp32_vs_fp64": diff}
 
 
 def serve_workload(per_rate=400, n_small=16, workers=16, seed=5, keep=None, group=8):

@@ -245,9 +245,10 @@ typedef struct {
 /* Runs ssnal_en_path (same arguments; X is required here) and evaluates the
  * criteria at each computed point: nu from the Cholesky factor of the r x r (or
  * m x m when r > m) matrix as min(r, m) - lambda2 tr(G^{-1}), rss through the
- * SMW Newton solve with kappa = infinity (r < m; rss = 0 when r >= m).  nu is
- * NaN when min(r, m) exceeds 640 and lambda2 > 0 (not supported), rss is NaN
- * when the least-squares normal matrix is not positive definite in FP32.
+ * SMW Newton solve with kappa = infinity (r < m; rss = 0 when r >= m).
+ * tr(G^{-1}) = ||L^{-1}||_F^2 from the FP32 factor (any min(r, m) <= 4096).  nu is
+ * NaN when G is not positive definite in FP32, rss is NaN when the least-squares
+ * normal matrix is not positive definite in FP32 nor in FP64.
  * crit: host array of K.  best_gcv / best_ebic (host, may be NULL): index of the
  * smallest finite criterion, or -1.  Errors: as ssnal_en_path. */
 ssnal_en_status ssnal_en_tune(ssnal_en_ctx* ctx, const double* b, double alpha, const double* c_grid, int32_t K,

@@ -73,6 +73,8 @@ struct ssnal_en_ctx {
   int64_t ldg64 = 0;
   float* tuneS = nullptr;  // tuning: factor and identity for tr(G^{-1}) (2 Np x Np), allocated on first use
   double* tune_dev = nullptr;  // tuning: per-column-block partial sums and the result
+  float* tuneY = nullptr;      // tuning above N = 640: Y = L^{-1} (Np x Np), allocated on first use
+  int64_t tuneY_np = 0;        // its Np
   void* Xtc = nullptr;     // BF16 split panels of the tensor-core SYRK (capacity rcap)
   float* tc_part = nullptr;
   double* Xdev = nullptr;  // path_host output staging
@@ -217,6 +219,7 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->G64);
   dev_free(c->tuneS);
   dev_free(c->tune_dev);
+  dev_free(c->tuneY);
   dev_free(c->Xtc);
   dev_free(c->tc_part);
   dev_free(c->Xdev);
@@ -1421,8 +1424,9 @@ ssnal_en_status ssnal_en_tune(ssnal_en_ctx* c, const double* b, double alpha, co
       nu = (double)N;  // full column (or row) rank assumed: the trace of a projection
     } else {
       const int64_t Np = (N + 31) / 32 * 32;
+      constexpr int kOut = kMaxM / 32;  // tune_dev: partials [0, kOut), result at kOut
+      if (c->tune_dev == nullptr && dev_alloc(&c->tune_dev, kOut + 1) != SSNAL_EN_OK) return SSNAL_EN_ENOMEM;
       if (Np <= 640) {
-        if (c->tune_dev == nullptr && dev_alloc(&c->tune_dev, 64 + 1) != SSNAL_EN_OK) return SSNAL_EN_ENOMEM;
         if (c->tuneS == nullptr && dev_alloc(&c->tuneS, (size_t)2 * 640 * 640) != SSNAL_EN_OK) return SSNAL_EN_ENOMEM;
         const long long ldS = 2 * Np;
         if (r <= m)
@@ -1431,11 +1435,34 @@ ssnal_en_status ssnal_en_tune(ssnal_en_ctx* c, const double* b, double alpha, co
         else
           launch_syrk_tc(c->P, c->ldp, (int)m, (int)r, 1, syrk_splits(c), c->Xtc, c->tc_part, 1.0f, (float)lam2,
                          c->tuneS, ldS, c->st, c->sms, s);
-        if (inv_trace(c->tuneS, ldS, (int)N, c->st, c->Wdiag, c->tune_dev, c->tune_dev + 64, s)) {
+        if (inv_trace(c->tuneS, ldS, (int)N, c->st, c->Wdiag, c->tune_dev, c->tune_dev + kOut, s)) {
           double tr = 0.0;
-          CK(cudaMemcpyAsync(&tr, c->tune_dev + 64, sizeof(double), cudaMemcpyDeviceToHost, s));
+          CK(cudaMemcpyAsync(&tr, c->tune_dev + kOut, sizeof(double), cudaMemcpyDeviceToHost, s));
           if ((e = read_state(c)) != SSNAL_EN_OK) return e;
           tr -= (double)(Np - N);
+          if (!c->st_host->chol_fail) nu = (double)N - lam2 * tr;
+        }
+      } else {
+        // larger systems: the Newton-matrix buffer, the super-block factor and the
+        // blocked inverse of k_inv_frob (Y = L^{-1} in scratch)
+        if (c->tuneY_np < Np) {
+          dev_free(c->tuneY);
+          c->tuneY = nullptr;
+          c->tuneY_np = 0;
+          if (dev_alloc(&c->tuneY, (size_t)Np * (size_t)Np) != SSNAL_EN_OK) return SSNAL_EN_ENOMEM;
+          c->tuneY_np = Np;
+        }
+        if (r <= m)
+          launch_syrk_tc(c->P, c->ldp, (int)m, (int)r, 0, syrk_splits(c), c->Xtc, c->tc_part, 1.0f, (float)lam2,
+                         c->G, c->ldg, c->st, c->sms, s);
+        else
+          launch_syrk_tc(c->P, c->ldp, (int)m, (int)r, 1, syrk_splits(c), c->Xtc, c->tc_part, 1.0f, (float)lam2,
+                         c->G, c->ldg, c->st, c->sms, s);
+        if (inv_trace_large(c->G, c->ldg, (int)N, c->st, c->Wdiag, c->tuneY, Np, c->tune_dev, c->tune_dev + kOut,
+                            s)) {
+          double tr = 0.0;
+          CK(cudaMemcpyAsync(&tr, c->tune_dev + kOut, sizeof(double), cudaMemcpyDeviceToHost, s));
+          if ((e = read_state(c)) != SSNAL_EN_OK) return e;
           if (!c->st_host->chol_fail) nu = (double)N - lam2 * tr;
         }
       }

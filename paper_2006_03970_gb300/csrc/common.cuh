@@ -159,6 +159,10 @@ __device__ __forceinline__ bool is_active(double v, const ProxParams& pp) { retu
 // rounding sequence as the plain elementwise evaluation of the definition.
 __device__ __forceinline__ double v_of(double x, double u, double sigma) { return __dsub_rn(x, __dmul_rn(sigma, u)); }
 
+// x == +0 or -0, tested on the bit pattern (integer pipe, not the FP64 pipe)
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
+
 // Sum p[0], p[stride], ..., p[(count-1) stride] in index order (the same
 // association as a plain loop), with B loads in flight at a time: partial
 // results written by other blocks are read at L2 latency, so a serial chain of
@@ -246,6 +250,16 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const void* map, int x
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           dst),
       "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// 3-D tensor copy (TMA) of one box at (x, y, z) into shared memory, completing on the
+// mbarrier `bar` of this CTA.
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const void* map, int x, int y, int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
 

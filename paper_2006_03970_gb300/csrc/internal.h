@@ -142,6 +142,12 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
 // N <= 640; returns false otherwise or on a launch error.
 bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, double* partial, double* out,
                cudaStream_t s);
+// Any N <= kMaxM: factors the N x N SPD matrix G in place (chol_factor) and writes
+// ||L^{-1}||_F^2 = tr(G^{-1}) to *out (device), Y scratch of ldy x 32 ceil(N / 32)
+// floats (ldy >= 32 ceil(N / 32)), partial of ceil(N / 32) doubles.  Returns false when
+// the factorisation gives no inverse diagonal blocks or on a launch error.
+bool inv_trace_large(float* G, long long ldg, int N, DevState* st, float* Wdiag, float* Y, long long ldy,
+                     double* partial, double* out, cudaStream_t s);
 // N <= kSmallNewton: factor and solve one right-hand side in one launch by one warp (acc = alpha c)
 void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const double* rhs, double* acc,
                              double alpha, cudaStream_t s);

@@ -110,8 +110,12 @@ __device__ __forceinline__ void ffadd(float& S, float& L, float S2, float L2) {
 
 // out_j = sum_i A[i, j] vec_i for j < n, float-float (products of the FP32 entries with
 // the hi / lo split of the vector scaled by a power of two), one warp per column.
-// DEPTH: loads in flight per lane (the products are accumulated in row order whatever
-// DEPTH is, so the result does not depend on it).
+// Columns 16-byte aligned (A and lda): lane l owns rows 4 l .. 4 l + 3 of every stripe of
+// 128 rows and reads them with one 16-byte load; DEPTH / 2 such loads are in flight per
+// lane, over one column or, when a column has at most DEPTH / 4 stripes, over two
+// columns at once.  Otherwise: lane l owns rows l, l + 32, ..., DEPTH 4-byte loads in
+// flight.  Either way every lane accumulates its rows in increasing order and the lanes
+// are merged by the same butterfly, so the result does not depend on DEPTH.
 template <int BT, int DEPTH>
 __device__ void bstream(const float* __restrict__ A, long long lda, int m, long long n, const double* vec,
                         double* out, float* dh, float* dl, unsigned long long* bits) {
@@ -137,24 +141,75 @@ __device__ void bstream(const float* __restrict__ A, long long lda, int m, long 
     dl[i] = __double2float_rn(v - (double)h);
   }
   __syncthreads();
-  for (long long j = warp; j < n; j += NW) {
-    const float* col = A + j * lda;
-    float S = 0.0f, L = 0.0f;
-    int i = lane;
-    for (; i + 32 * (DEPTH - 1) < m; i += 32 * DEPTH) {
-      float a[DEPTH];
-#pragma unroll
-      for (int e = 0; e < DEPTH; e++) a[e] = col[i + 32 * e];
-#pragma unroll
-      for (int e = 0; e < DEPTH; e++) ffmadd(S, L, a[e], dh[i + 32 * e], dl[i + 32 * e]);
-    }
-    for (; i < m; i += 32) ffmadd(S, L, col[i], dh[i], dl[i]);
+  auto finish = [&](long long j, float S, float L) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float S2 = __shfl_xor_sync(0xffffffffu, S, o), L2 = __shfl_xor_sync(0xffffffffu, L, o);
       ffadd(S, L, S2, L2);
     }
     if (lane == 0) out[j] = ((double)S + (double)L) * unscale;
+  };
+  const bool vec4 = ((reinterpret_cast<unsigned long long>(A) & 15ull) == 0) && ((lda & 3) == 0);
+  if (vec4) {
+    // lda >= m and lda % 4 == 0: a 16-byte load that starts inside a column ends inside it
+    constexpr int VD = DEPTH / 2;
+    const int S = (m + 127) / 128;
+    const int per = S <= VD / 2 ? 2 : 1;
+    const int step = per == 2 ? S : VD;
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (long long j = warp; j < n; j += (long long)NW * per) {
+      const long long jb = j + NW;
+      const bool two = per == 2 && jb < n;
+      const float4* c0 = reinterpret_cast<const float4*>(A + j * lda);
+      const float4* c1 = reinterpret_cast<const float4*>(A + (two ? jb : j) * lda);
+      float S0 = 0.0f, L0 = 0.0f, S1 = 0.0f, L1 = 0.0f;
+      for (int s0 = 0; s0 < S; s0 += step) {
+        float4 a[VD];
+#pragma unroll
+        for (int e = 0; e < VD; e++) {
+          const bool second = per == 2 && e >= S;
+          const int st = second ? e - S : s0 + e;
+          const int i4 = lane + 32 * st;
+          const bool ok = st < S && 4 * i4 < m && (!second || two);
+          a[e] = ok ? (second ? c1 : c0)[i4] : zero4;
+        }
+#pragma unroll
+        for (int e = 0; e < VD; e++) {
+          const bool second = per == 2 && e >= S;
+          const int st = second ? e - S : s0 + e;
+          if (st >= S) continue;
+          const int i0 = 4 * (lane + 32 * st);
+          const float av[4] = {a[e].x, a[e].y, a[e].z, a[e].w};
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int i = i0 + q;
+            if (i < m) {
+              if (second)
+                ffmadd(S1, L1, av[q], dh[i], dl[i]);
+              else
+                ffmadd(S0, L0, av[q], dh[i], dl[i]);
+            }
+          }
+        }
+      }
+      finish(j, S0, L0);
+      if (two) finish(jb, S1, L1);
+    }
+  } else {
+    for (long long j = warp; j < n; j += NW) {
+      const float* col = A + j * lda;
+      float S = 0.0f, L = 0.0f;
+      int i = lane;
+      for (; i + 32 * (DEPTH - 1) < m; i += 32 * DEPTH) {
+        float a[DEPTH];
+#pragma unroll
+        for (int e = 0; e < DEPTH; e++) a[e] = col[i + 32 * e];
+#pragma unroll
+        for (int e = 0; e < DEPTH; e++) ffmadd(S, L, a[e], dh[i + 32 * e], dl[i + 32 * e]);
+      }
+      for (; i < m; i += 32) ffmadd(S, L, col[i], dh[i], dl[i]);
+      finish(j, S, L);
+    }
   }
   __syncthreads();
 }
@@ -458,7 +513,7 @@ __device__ PassNorms bprox(const double* x, double* u, const double* t, double* 
     if (j < n) {
       const double xj = x[j];
       if (support) {
-        act = xj != 0.0;
+        act = !is_zero_bits(xj);
         wv = xj;
       } else {
         double uj = u[j];
@@ -478,7 +533,7 @@ __device__ PassNorms bprox(const double* x, double* u, const double* t, double* 
           wv = prox_value(v, pp);
         } else {
           q[3] += v * v;
-          if (xj != 0.0) q[2] += xj * xj;
+          if (!is_zero_bits(xj)) q[2] += xj * xj;
         }
         if (abs_gt(uj, pp.lam1)) {
           const double e = fabs(uj) - pp.lam1;

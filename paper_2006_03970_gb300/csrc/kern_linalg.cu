@@ -1528,8 +1528,8 @@ __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long
   extern __shared__ __align__(16) float tsm[];
   const int ldx = nk + 1;  // odd: conflict-free column walks
   float* Ls = tsm;                 // (nk - 32) x 32: block row J of L, column k at Ls + 32 k
-  float* Ws = Ls + 32 * nk;        // 32 x 32: W_JJ, row-major
-  float* Xs = Ws + 1024;           // 32 x ldx: the rows of this CTA
+  float* Ws = Ls + 32 * nk;        // 32 x 33: W_JJ, row-major, row stride 33 (conflict-free rows)
+  float* Xs = Ws + 32 * 33;        // 32 x ldx: the rows of this CTA
   float* Ys = Xs + 32 * ldx;       // 32 x 33
   const int tid = threadIdx.x;
   const int rb = r0 + 32 * blockIdx.x, nr = min(32, R - 32 * (int)blockIdx.x);
@@ -1547,7 +1547,7 @@ __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long
       const int c4 = e & 7, k = e >> 3;
       cp_async16(Ls + 32 * k + 4 * c4, G + (k0 + 32 * J + 4 * c4) + (long long)(k0 + k) * ld, 16);
     }
-    for (int e = tid; e < 256; e += blockDim.x) cp_async16(Ws + 4 * e, Wd + (long long)J * 1024 + 4 * e, 16);
+    for (int e = tid; e < 1024; e += blockDim.x) Ws[(e >> 5) * 33 + (e & 31)] = Wd[(long long)J * 1024 + e];
     cp_async_commit();
     cp_async_wait0();
     __syncthreads();
@@ -1570,7 +1570,7 @@ __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long
     for (int e = 0; e < 4; e++) {
       float a = 0.0f;
 #pragma unroll 8
-      for (int q = 0; q < 32; q++) a = fmaf(Ys[r * 33 + q], Ws[(4 * cg + e) * 32 + q], a);
+      for (int q = 0; q < 32; q++) a = fmaf(Ys[r * 33 + q], Ws[(4 * cg + e) * 33 + q], a);
       Xs[r * ldx + 32 * J + 4 * cg + e] = a;
     }
     __syncthreads();
@@ -1585,7 +1585,9 @@ __global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long
 // X = G[r0 .., k0 .. k0 + nk): 64 x 64 output tiles, K staged 32 at a time.
 __global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long long ld, int r0, int R, int k0, int nk) {
   pdl_entry();
-  __shared__ float As[64 * 33], Bs[64 * 33];
+  // k-major staging (64 consecutive rows per k): a thread's four rows are one 16-byte
+  // load and the sixteen column groups of a warp read 256 consecutive bytes
+  __shared__ __align__(16) float As[32 * 64], Bs[32 * 64];
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
   const int i0 = 64 * ti, j0 = 64 * tj;
@@ -1597,9 +1599,9 @@ __global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long lo
       const bool kin = kc + k < nk, ain = i0 + i < R && kin, bin = j0 + i < R && kin;
       const float* sa = ain ? G + (r0 + i0 + i) + (long long)(k0 + kc + k) * ld : G;
       const float* sb = bin ? G + (r0 + j0 + i) + (long long)(k0 + kc + k) * ld : G;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(As + i * 33 + k)), "l"(sa),
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(As + k * 64 + i)), "l"(sa),
                    "r"(ain ? 4 : 0) : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(Bs + i * 33 + k)), "l"(sb),
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(Bs + k * 64 + i)), "l"(sb),
                    "r"(bin ? 4 : 0) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -1607,12 +1609,9 @@ __global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long lo
     __syncthreads();
 #pragma unroll 4
     for (int k = 0; k < 32; k++) {
-      float a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        a[u] = As[(4 * tr + u) * 33 + k];
-        b[u] = Bs[(4 * tc + u) * 33 + k];
-      }
+      const float4 a4 = reinterpret_cast<const float4*>(As + k * 64)[tr];
+      const float4 b4 = reinterpret_cast<const float4*>(Bs + k * 64)[tc];
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int u = 0; u < 4; u++)
 #pragma unroll
@@ -1846,15 +1845,128 @@ bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, doubl
   if (dev < 0 || dev >= 64 || !done[dev]) {
     cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
     cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)(32 * kClusterN + 1024 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float)));
+                         (int)((size_t)(32 * kClusterN + 32 * 33 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float)));
     if (dev >= 0 && dev < 64) done[dev] = true;
   }
   count_launch(4);
   launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
   launch_k(k_inv_trace_setup, dim3(64), dim3(256), (size_t)(0), s, S, ldS, N, Np);
-  const size_t tsm = (size_t)(32 * Np + 1024 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
+  const size_t tsm = (size_t)(32 * Np + 32 * 33 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
   launch_k(k_trsm_blocks, dim3(Np / 32), dim3(256), (size_t)(tsm), s, S, ldS, 0, Np, Np, Np, Wdiag);
   launch_k(k_frob2, dim3(Np / 32), dim3(256), (size_t)(0), s, S + Np, ldS, Np, partial, out, st);
+  return cudaGetLastError() == cudaSuccess;
+}
+
+// ||L^{-1}||_F^2 for a factor of any size up to kMaxM (the super-block factor of
+// chol_factor, with the inverses W_II of all its 32 x 32 diagonal blocks): column block
+// J of Y = L^{-1} by blocked forward substitution,
+//   Y_IJ = W_II (delta_IJ I - sum_{K=J}^{I-1} L_IK Y_KJ),   I = J .. T-1,
+// one CTA per column block (the blocks are independent).  Y lives in global scratch
+// (column-major, ldy >= 32 T; the CTA reads back only what it wrote before a block
+// barrier); the K sums run in chunks of 64 staged in shared memory, the next chunk
+// fetched into registers while the current one is used.  Entries of L outside N x N
+// are read as zero; the padded part of the last diagonal block is the identity (as
+// the factor kernels pad it), so Y is exact there and only entries inside N x N are
+// summed.  Per CTA the FP64 sum of squares goes to partial[J]; the last CTA adds the
+// partials in order into *out.
+constexpr int kInvKC = 64;
+constexpr int kInvKP = kInvKC + 1;
+__global__ void __launch_bounds__(256) k_inv_frob(const float* __restrict__ L, long long ld, int N,
+                                                  const float* __restrict__ Wd, float* __restrict__ Yall,
+                                                  long long ldy, double* __restrict__ partial,
+                                                  double* __restrict__ out, DevState* st) {
+  pdl_entry();
+  __shared__ __align__(16) float Ls[2][kInvKC * 32];  // L[32 I + row, kc + k] at [32 k + row]
+  __shared__ float Ys[2][32 * kInvKP];                // Y[kc + k, 32 J + col] at [col * kInvKP + k]
+  __shared__ float Ws[32 * 33];                        // W_II transposed: W[i][q] at [q * 33 + i]
+  __shared__ float Bs[32 * 33];                        // delta - sum, row-major
+  __shared__ double red[32];
+  const int J = blockIdx.x, T = (N + 31) / 32;
+  const int tid = threadIdx.x, rg = tid & 7, c = tid >> 3;  // rows 4 rg .. 4 rg + 3, column c
+  float* Y = Yall + (long long)J * 32 * ldy;
+  double ss = 0.0;
+  float pl[8], py[8];
+  auto fetch = [&](int I, int kc, int nk) {
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      const int e = tid + 256 * t, row = e & 31, k = e >> 5;
+      const int gi = 32 * I + row, gk = kc + k;
+      pl[t] = (k < nk && gi < N && gk < N) ? L[gi + (long long)gk * ld] : 0.0f;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      const int e = tid + 256 * t, k = e % kInvKC, col = e / kInvKC;
+      py[t] = k < nk ? Y[(kc + k) + (long long)col * ldy] : 0.0f;
+    }
+  };
+  auto put = [&](int buf) {
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+      const int e = tid + 256 * t;
+      Ls[buf][32 * (e >> 5) + (e & 31)] = pl[t];
+      Ys[buf][(e / kInvKC) * kInvKP + e % kInvKC] = py[t];
+    }
+  };
+  for (int I = J; I < T; I++) {
+    for (int e = tid; e < 1024; e += 256) Ws[(e & 31) * 33 + (e >> 5)] = Wd[(long long)I * 1024 + e];
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int kbeg = 32 * J, kend = 32 * I;
+    const int nch = (kend - kbeg + kInvKC - 1) / kInvKC;
+    if (nch > 0) {
+      fetch(I, kbeg, min(kInvKC, kend - kbeg));
+      put(0);
+    }
+    __syncthreads();
+    for (int ch = 0; ch < nch; ch++) {
+      const int buf = ch & 1, kc = kbeg + ch * kInvKC, nk = min(kInvKC, kend - kc);
+      if (ch + 1 < nch) fetch(I, kc + kInvKC, min(kInvKC, kend - kc - kInvKC));
+      const float* Lb = Ls[buf];
+      const float* Yb = Ys[buf] + c * kInvKP;
+#pragma unroll 4
+      for (int k = 0; k < nk; k++) {
+        const float y = Yb[k];
+        const float4 l = reinterpret_cast<const float4*>(Lb + 32 * k)[rg];
+        acc[0] = fmaf(l.x, y, acc[0]);
+        acc[1] = fmaf(l.y, y, acc[1]);
+        acc[2] = fmaf(l.z, y, acc[2]);
+        acc[3] = fmaf(l.w, y, acc[3]);
+      }
+      if (ch + 1 < nch) put(buf ^ 1);  // read in the previous chunk, before the last barrier
+      __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int row = 4 * rg + e;
+      Bs[row * 33 + c] = ((I == J && row == c) ? 1.0f : 0.0f) - acc[e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int row = 4 * rg + e;
+      float a = 0.0f;
+#pragma unroll 8
+      for (int q = 0; q < 32; q++) a = fmaf(Ws[q * 33 + row], Bs[q * 33 + c], a);
+      const int gi = 32 * I + row;
+      Y[gi + (long long)c * ldy] = a;
+      if (gi < N && 32 * J + c < N) ss = fma((double)a, (double)a, ss);
+    }
+    __syncthreads();  // block I of Y is written before a later block stages it; Ws, Bs free
+  }
+  ss = block_sum(ss, red);
+  if (tid == 0) partial[J] = ss;
+  if (!last_block(&st->counters[kCtrMisc])) return;
+  if (tid == 0) *out = ordered_sum_cg(partial, 1, (int)gridDim.x);
+  reset_counter(&st->counters[kCtrMisc]);
+}
+
+bool inv_trace_large(float* G, long long ldg, int N, DevState* st, float* Wdiag, float* Y, long long ldy,
+                     double* partial, double* out, cudaStream_t s) {
+  const int T = (N + 31) / 32;
+  if (N <= 0 || N > kMaxM || ldy < 32LL * T || !Wdiag) return false;
+  if (!chol_factor(G, ldg, N, st, Wdiag, s)) return false;  // no inverse diagonal blocks
+  count_launch();
+  launch_k(k_inv_frob, dim3(T), dim3(256), (size_t)0, s, (const float*)G, ldg, N, (const float*)Wdiag, Y, ldy,
+           partial, out, st);
   return cudaGetLastError() == cudaSuccess;
 }
 
@@ -1934,7 +2046,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
     static bool done_sb[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    const size_t trsm_smem_max = (size_t)(32 * kClusterN + 1024 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float);
+    const size_t trsm_smem_max = (size_t)(32 * kClusterN + 32 * 33 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float);
     if (dev < 0 || dev >= 64 || !done_sb[dev]) {
       cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
       cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem_max);
@@ -1952,7 +2064,7 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       const int r0 = k0 + nk, R = N - r0;
       if (R > 0) {
         count_launch(2);
-        const size_t tsm = (size_t)(32 * nk + 1024 + 32 * (nk + 1) + 32 * 33) * sizeof(float);
+        const size_t tsm = (size_t)(32 * nk + 32 * 33 + 32 * (nk + 1) + 32 * 33) * sizeof(float);
         launch_k(k_trsm_blocks, dim3((R + 31) / 32), dim3(256), (size_t)(tsm), s, G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024);
         const int nt = (R + 63) / 64;
         launch_k(k_syrk_sub, dim3(nt * (nt + 1) / 2), dim3(256), (size_t)(0), s, G, ldg, r0, R, k0, nk);

@@ -678,10 +678,11 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
   bool timed_out = false;
   long long it = 0;
   for (long long q = 0; q < ngrp; q++) {
-    // float-float: two accumulator pairs per column (odd and even row pairs of a chunk)
-    // for two independent dependency chains; FP32: one FMA chain per column
-    unsigned long long S2 = 0ull, L2 = 0ull, S2b = 0ull, L2b = 0ull;
-    unsigned long long S3 = 0ull, L3 = 0ull, S3b = 0ull, L3b = 0ull;
+    // float-float: four accumulator pairs per column (row pair index mod 4) for four
+    // independent dependency chains; FP32: one FMA chain per column
+    unsigned long long S2 = 0ull, S2b = 0ull;
+    unsigned long long FS[4] = {0ull, 0ull, 0ull, 0ull}, FL[4] = {0ull, 0ull, 0ull, 0ull};
+    unsigned long long FSb[4] = {0ull, 0ull, 0ull, 0ull}, FLb[4] = {0ull, 0ull, 0ull, 0ull};
     for (int k = 0; k < nw && !timed_out; k++, it++) {
       const int sidx = (int)(it % cfg.stages);
       if (!mbar_wait(smem_u32(wbars + sidx), (unsigned)((it / cfg.stages) & 1))) {
@@ -728,13 +729,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
               if constexpr (elt_ff(ELT)) {
                 const ulonglong2 d = D4p[slot];
                 const unsigned long long dl = DLp[slot];
-                if (e & 1) {
-                  ff2_madd_exact(S3, L3, av, d.x, d.y, dl);
-                  ff2_madd_exact(S3b, L3b, bv, d.x, d.y, dl);
-                } else {
-                  ff2_madd_exact(S2, L2, av, d.x, d.y, dl);
-                  ff2_madd_exact(S2b, L2b, bv, d.x, d.y, dl);
-                }
+                ff2_madd_exact(FS[e & 3], FL[e & 3], av, d.x, d.y, dl);
+                ff2_madd_exact(FSb[e & 3], FLb[e & 3], bv, d.x, d.y, dl);
               } else {
                 const unsigned long long dh = D4h[2 * slot];
                 S2 = f2fma(av, dh, S2);
@@ -747,13 +743,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
           const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(colbase + 32 * 128 + pp * 16);
           const ulonglong2 d = D4p[pp];
           const unsigned long long dl = DLp[pp];
-          if (p & 1) {
-            ff2_madd(S3, L3, a.x, a.y, d.x, d.y, dl);
-            ff2_madd(S3b, L3b, b.x, b.y, d.x, d.y, dl);
-          } else {
-            ff2_madd(S2, L2, a.x, a.y, d.x, d.y, dl);
-            ff2_madd(S2b, L2b, b.x, b.y, d.x, d.y, dl);
-          }
+          ff2_madd(FS[p & 3], FL[p & 3], a.x, a.y, d.x, d.y, dl);
+          ff2_madd(FSb[p & 3], FLb[p & 3], b.x, b.y, d.x, d.y, dl);
         } else {
           const uint4 a = *reinterpret_cast<const uint4*>(colbase + pp * 16);
           const uint4 b = *reinterpret_cast<const uint4*>(colbase + 32 * 128 + pp * 16);
@@ -785,13 +776,9 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
             if constexpr (elt_ff(ELT)) {
               const ulonglong2 d = D4p[slot];
               const unsigned long long dl = DLp[slot];
-              if (e & 1) {
-                ff2_madd_exact(S3, L3, ap[e], d.x, d.y, dl);
-                ff2_madd_exact(S3b, L3b, bp[e], d.x, d.y, dl);
-              } else {
-                ff2_madd_exact(S2, L2, ap[e], d.x, d.y, dl);
-                ff2_madd_exact(S2b, L2b, bp[e], d.x, d.y, dl);
-              }
+              const int ch4 = (p * P + e) & 3;
+              ff2_madd_exact(FS[ch4], FL[ch4], ap[e], d.x, d.y, dl);
+              ff2_madd_exact(FSb[ch4], FLb[ch4], bp[e], d.x, d.y, dl);
             } else {
               const unsigned long long dh = D4h[2 * slot];
               S2 = f2fma(ap[e], dh, S2);
@@ -807,15 +794,24 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
       }
     }
     {
-      float Sq = lo32f(S2), Lq = lo32f(L2);
-      ff_merge(Sq, Lq, hi32f(S2), hi32f(L2));
-      float Sb = lo32f(S2b), Lb = lo32f(L2b);
-      ff_merge(Sb, Lb, hi32f(S2b), hi32f(L2b));
+      float Sq, Lq, Sb, Lb;
       if constexpr (elt_ff(ELT)) {
-        ff_merge(Sq, Lq, lo32f(S3), lo32f(L3));
-        ff_merge(Sq, Lq, hi32f(S3), hi32f(L3));
-        ff_merge(Sb, Lb, lo32f(S3b), lo32f(L3b));
-        ff_merge(Sb, Lb, hi32f(S3b), hi32f(L3b));
+        Sq = lo32f(FS[0]), Lq = lo32f(FL[0]);
+        ff_merge(Sq, Lq, hi32f(FS[0]), hi32f(FL[0]));
+        Sb = lo32f(FSb[0]), Lb = lo32f(FLb[0]);
+        ff_merge(Sb, Lb, hi32f(FSb[0]), hi32f(FLb[0]));
+#pragma unroll
+        for (int c4 = 1; c4 < 4; c4++) {
+          ff_merge(Sq, Lq, lo32f(FS[c4]), lo32f(FL[c4]));
+          ff_merge(Sq, Lq, hi32f(FS[c4]), hi32f(FL[c4]));
+          ff_merge(Sb, Lb, lo32f(FSb[c4]), lo32f(FLb[c4]));
+          ff_merge(Sb, Lb, hi32f(FSb[c4]), hi32f(FLb[c4]));
+        }
+      } else {
+        Sq = lo32f(S2), Lq = 0.0f;
+        ff_merge(Sq, Lq, hi32f(S2), 0.0f);
+        Sb = lo32f(S2b), Lb = 0.0f;
+        ff_merge(Sb, Lb, hi32f(S2b), 0.0f);
       }
       part[q & 1][warp][lane] = make_float2(Sq, Lq);
       part[q & 1][warp][lane + 32] = make_float2(Sb, Lb);

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
   for (long long j = start + threadIdx.x; j < stop; j += blockDim.x) {
     const double xj = x[j];
     if (MODE == kProxSupport) {
-      if (xj != 0.0) cnt++;
+      if (!is_zero_bits(xj)) cnt++;
       continue;
     }
     double uj = u[j];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
       vw2 += (v - w) * (v - w);
     } else {  // w = 0
       vw2 += v * v;
-      if (xj != 0.0) xw2 += xj * xj;
+      if (!is_zero_bits(xj)) xw2 += xj * xj;
     }
     if (abs_gt(uj, pp.lam1)) {
       const double e = fabs(uj) - pp.lam1;
@@ -184,11 +184,11 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
       const double xj = x[j];
       if (MODE == kProxSupport) {
         w = xj;
-        act = xj != 0.0;
+        act = !is_zero_bits(xj);
       } else {
         const double v = v_of(xj, u[j], pp.sigma);
         act = is_active(v, pp);
-        w = prox_value(v, pp);
+        if (act) w = prox_value(v, pp);  // zero exactly when inactive
       }
     }
   };

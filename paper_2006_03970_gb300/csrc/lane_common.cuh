@@ -25,8 +25,9 @@ __device__ __forceinline__ double trial_term(double v, double tj, double sk, con
 
 // True when no trial step can move column j across the threshold: for s in
 // (0, 1] the argument lies between v and v - sigma t.
+// (The comparisons run on the bit patterns, off the FP64 pipe.)
 __device__ __forceinline__ bool trial_skip(double v, double tj, const ProxParams& pp) {
-  return fabs(v) <= pp.thr && fabs(__dsub_rn(v, __dmul_rn(pp.sigma, tj))) <= pp.thr;
+  return !abs_gt(v, pp.thr) && !abs_gt(__dsub_rn(v, __dmul_rn(pp.sigma, tj)), pp.thr);
 }
 
 // Armijo selection over trials [k0, k1) given the trial sums; returns the

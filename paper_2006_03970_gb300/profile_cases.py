@@ -10,6 +10,10 @@ or two while its operands still exceed the 129 MB L2 of a GB300:
                    r = 730 (the active-set size of the precision workload at alpha 0.5) on
                    BF16 storage: the BF16 tensor-core SYRK, the cluster Cholesky and the
                    triangular solves with their refinement
+  newton-1000      one Newton direction of the m x m form (eq. AJ_system) at m = 1000,
+                   r = 1500 on BF16 storage: SYRK over K = r, the super-block Cholesky
+                   (cluster factors, block solve, trailing update) and the cluster solves
+  prox-1e6         the active-set pass and its compaction at n = 1e6, ~0.1 % active
   shared-4         four mixed-form fits on the precision-small matrix advanced together
                    (ssnal_en_solve_shared): one merged pass over A per Newton step
 
@@ -62,6 +66,34 @@ def newton_730(m=1000, r=730, repeats=3):
     return float(d.abs().max())
 
 
+def newton_1000(m=1000, r=1500, repeats=3):
+    """One Newton direction of the m x m form (eq. AJ_system) at m = 1000, r = 1500 (the
+    first Newton steps of the precision workload, where r > m): the tensor-core SYRK over
+    K = r, the super-block Cholesky (two 512-column cluster factors, the block solve and
+    the trailing update) and the cluster triangular solves."""
+    return newton_730(m=m, r=r, repeats=repeats)
+
+
+def prox_1e6(n=1_000_000, m=64, repeats=3):
+    """The active-set pass (eq. Q_def, eq. prox_elastic) and its ordered compaction at
+    n = 1e6 with about 0.1 % of the columns active (the precision workload's r ~ 730)."""
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    rng = np.random.default_rng(6)
+    bits = np.zeros((n, m), dtype=np.uint16)
+    ctx = pkg.Context(bits, dtype=pkg.BF16, options=pkg.ssnal_en_default_options(precision=1))
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    u = torch.as_tensor(rng.normal(size=n), device="cuda")
+    J = torch.empty(n, dtype=torch.int32, device="cuda")
+    wJ = torch.empty(n, dtype=torch.float64, device="cuda")
+    r = 0
+    for _ in range(repeats):
+        r = pkg.ssnal_en_op_prox_active(ctx.ctx, x, u, 1.0, 3.3, 0.1, J, wJ)
+    torch.cuda.synchronize()
+    ctx.close()
+    return r
+
+
 def shared_4(n=100_000, m=1000):
     """Four mixed-form fits on the precision-small matrix through ssnal_en_solve_shared: their
     Newton-step passes over A merged into one k_stream_multi launch per step."""
@@ -88,7 +120,8 @@ def shared_4(n=100_000, m=1000):
     return st, [r.newton_iters for r in res], passes
 
 
-CASES = {"precision-small": precision_small, "newton-730": newton_730, "shared-4": shared_4}
+CASES = {"precision-small": precision_small, "newton-730": newton_730, "newton-1000": newton_1000,
+         "shared-4": shared_4, "prox-1e6": prox_1e6}
 
 
 def main(argv):

@@ -54,3 +54,28 @@ def test_tuning_criteria_match_oracle(m, n, alpha, K, seed):
     es = np.sort(e[np.isfinite(e)])
     if es.size > 1 and es[1] - es[0] > 1e-4 * max(1.0, abs(es[0])):
         assert be == int(np.nanargmin(np.where(np.isfinite(e), e, np.inf)))
+
+
+def test_degrees_of_freedom_above_640_match_oracle():
+    # min(r, m) > 640: tr(G^{-1}) from the super-block factor and the blocked inverse
+    # (k_inv_frob) instead of the single-cluster path
+    m, n, alpha = 700, 2400, 0.5
+    p = synth.make_problem(m, n, k=8, seed=74, block=20, rho=0.5, snr=3.0, alpha=alpha)
+    grid = synth.path_grid(7, 0.004)
+    ctx = pkg.Context(p.At)
+    b = torch.as_tensor(p.b, device="cuda")
+    X = torch.zeros((len(grid), n), dtype=torch.float64, device="cuda")
+    st, res, crit, bg, be, done = pkg.ssnal_en_tune(ctx.ctx, b, alpha, grid, X)
+    ctx.close()
+    assert done == len(grid)
+    Xh = X.cpu().numpy()
+    large = 0
+    for k in range(done):
+        r = np.count_nonzero(Xh[k])
+        nu, rss, gcv, ebic = R.tuning_criteria(p.At, p.b, Xh[k], res[k].lambda2)
+        c = crit[k]
+        assert c.active == r
+        assert np.isfinite(c.nu)
+        assert c.nu == pytest.approx(nu, rel=1e-5, abs=1e-6)
+        large += min(r, m) > 640
+    assert large >= 1
