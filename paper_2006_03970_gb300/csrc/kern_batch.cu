@@ -48,7 +48,7 @@ struct BatchOpts {
 // Byte offsets of the per-CTA scratch (sized for the largest n and m of the batch).
 struct BatchLayout {
   size_t slot_bytes;
-  size_t u, t, w, rv, xw, J, y, d, g, tm, q, h, rs, cr, G;
+  size_t u, t, w, rv, xw, J, y, d, g, tm, q, h, rs, cr, G, cs;
   int m_max;
 };
 
@@ -108,14 +108,57 @@ __device__ __forceinline__ void ffadd(float& S, float& L, float S2, float L2) {
   L = __fadd_rn(__fadd_rn(L, L2), t);
 }
 
+// Columns of a 16-byte-aligned A, CW = VD / PS at a time per warp: lane l owns rows
+// 4 l .. 4 l + 3 of each 128-row stripe (PS stripes per column, compile time, at least
+// the S stripes of a column), so the VD 16-byte loads of a batch are all in flight
+// before the first product.  Every lane accumulates its rows of a column in increasing
+// order whatever VD and PS are.
+template <int NW, int VD, int PS, typename Finish>
+__device__ __forceinline__ void bstream_cols(const float* __restrict__ A, long long lda, int m, long long n, int S,
+                                             const float* dh, const float* dl, int warp, int lane, Finish finish) {
+  constexpr int CW = VD / PS;
+  static_assert(CW >= 1 && CW * PS == VD, "whole columns per batch");
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (long long j0 = (long long)warp * CW; j0 < n; j0 += (long long)NW * CW) {
+    float4 a[VD];
+#pragma unroll
+    for (int e = 0; e < VD; e++) {
+      const int c = e / PS, st = e % PS;
+      const long long j = j0 + c;
+      const int i4 = lane + 32 * st;
+      a[e] = (j < n && st < S && 4 * i4 < m) ? reinterpret_cast<const float4*>(A + j * lda)[i4] : zero4;
+    }
+    float FS[CW], FL[CW];
+#pragma unroll
+    for (int c = 0; c < CW; c++) FS[c] = FL[c] = 0.0f;
+#pragma unroll
+    for (int e = 0; e < VD; e++) {
+      const int c = e / PS, st = e % PS;
+      if (st >= S) continue;
+      const int i0 = 4 * (lane + 32 * st);
+      if (i0 >= m) continue;
+      const float av[4] = {a[e].x, a[e].y, a[e].z, a[e].w};
+      // 16-byte reads of the split vector (rows up to a multiple of 4 past m are in the buffer)
+      const float4 h4 = *reinterpret_cast<const float4*>(dh + i0), l4 = *reinterpret_cast<const float4*>(dl + i0);
+      const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (i0 + q < m) ffmadd(FS[c], FL[c], av[q], hv[q], lv[q]);
+    }
+#pragma unroll
+    for (int c = 0; c < CW; c++)
+      if (j0 + c < n) finish(j0 + c, FS[c], FL[c]);
+  }
+}
+
 // out_j = sum_i A[i, j] vec_i for j < n, float-float (products of the FP32 entries with
 // the hi / lo split of the vector scaled by a power of two), one warp per column.
 // Columns 16-byte aligned (A and lda): lane l owns rows 4 l .. 4 l + 3 of every stripe of
 // 128 rows and reads them with one 16-byte load; DEPTH / 2 such loads are in flight per
-// lane, over one column or, when a column has at most DEPTH / 4 stripes, over two
-// columns at once.  Otherwise: lane l owns rows l, l + 32, ..., DEPTH 4-byte loads in
-// flight.  Either way every lane accumulates its rows in increasing order and the lanes
-// are merged by the same butterfly, so the result does not depend on DEPTH.
+// lane, over several short columns at once (bstream_cols) or over stripes of one long
+// column.  Otherwise: lane l owns rows l, l + 32, ..., DEPTH 4-byte loads in flight.
+// Either way every lane accumulates its rows in increasing order and the lanes are merged
+// by the same butterfly, so the result does not depend on DEPTH.
 template <int BT, int DEPTH>
 __device__ void bstream(const float* __restrict__ A, long long lda, int m, long long n, const double* vec,
                         double* out, float* dh, float* dl, unsigned long long* bits) {
@@ -150,50 +193,45 @@ __device__ void bstream(const float* __restrict__ A, long long lda, int m, long 
     if (lane == 0) out[j] = ((double)S + (double)L) * unscale;
   };
   const bool vec4 = ((reinterpret_cast<unsigned long long>(A) & 15ull) == 0) && ((lda & 3) == 0);
-  if (vec4) {
+  constexpr int VD = DEPTH / 2;
+  const int S = (m + 127) / 128;
+  if (vec4 && S <= VD) {
     // lda >= m and lda % 4 == 0: a 16-byte load that starts inside a column ends inside it
-    constexpr int VD = DEPTH / 2;
-    const int S = (m + 127) / 128;
-    const int per = S <= VD / 2 ? 2 : 1;
-    const int step = per == 2 ? S : VD;
+    if (S <= 1)
+      bstream_cols<NW, VD, 1>(A, lda, m, n, S, dh, dl, warp, lane, finish);
+    else if (S <= 2)
+      bstream_cols<NW, VD, (VD >= 2 ? 2 : VD)>(A, lda, m, n, S, dh, dl, warp, lane, finish);
+    else if (S <= 4)
+      bstream_cols<NW, VD, (VD >= 4 ? 4 : VD)>(A, lda, m, n, S, dh, dl, warp, lane, finish);
+    else
+      bstream_cols<NW, VD, VD>(A, lda, m, n, S, dh, dl, warp, lane, finish);
+  } else if (vec4) {
+    // long columns: stripes in chunks of VD loads
     const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (long long j = warp; j < n; j += (long long)NW * per) {
-      const long long jb = j + NW;
-      const bool two = per == 2 && jb < n;
+    for (long long j = warp; j < n; j += NW) {
       const float4* c0 = reinterpret_cast<const float4*>(A + j * lda);
-      const float4* c1 = reinterpret_cast<const float4*>(A + (two ? jb : j) * lda);
-      float S0 = 0.0f, L0 = 0.0f, S1 = 0.0f, L1 = 0.0f;
-      for (int s0 = 0; s0 < S; s0 += step) {
+      float S0 = 0.0f, L0 = 0.0f;
+      for (int s0 = 0; s0 < S; s0 += VD) {
         float4 a[VD];
 #pragma unroll
         for (int e = 0; e < VD; e++) {
-          const bool second = per == 2 && e >= S;
-          const int st = second ? e - S : s0 + e;
-          const int i4 = lane + 32 * st;
-          const bool ok = st < S && 4 * i4 < m && (!second || two);
-          a[e] = ok ? (second ? c1 : c0)[i4] : zero4;
+          const int i4 = lane + 32 * (s0 + e);
+          a[e] = (s0 + e < S && 4 * i4 < m) ? c0[i4] : zero4;
         }
 #pragma unroll
         for (int e = 0; e < VD; e++) {
-          const bool second = per == 2 && e >= S;
-          const int st = second ? e - S : s0 + e;
-          if (st >= S) continue;
-          const int i0 = 4 * (lane + 32 * st);
+          if (s0 + e >= S) continue;
+          const int i0 = 4 * (lane + 32 * (s0 + e));
+          if (i0 >= m) continue;
           const float av[4] = {a[e].x, a[e].y, a[e].z, a[e].w};
+          const float4 h4 = *reinterpret_cast<const float4*>(dh + i0), l4 = *reinterpret_cast<const float4*>(dl + i0);
+          const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const int i = i0 + q;
-            if (i < m) {
-              if (second)
-                ffmadd(S1, L1, av[q], dh[i], dl[i]);
-              else
-                ffmadd(S0, L0, av[q], dh[i], dl[i]);
-            }
-          }
+          for (int q = 0; q < 4; q++)
+            if (i0 + q < m) ffmadd(S0, L0, av[q], hv[q], lv[q]);
         }
       }
       finish(j, S0, L0);
-      if (two) finish(jb, S1, L1);
     }
   } else {
     for (long long j = warp; j < n; j += NW) {
@@ -214,7 +252,32 @@ __device__ void bstream(const float* __restrict__ A, long long lda, int m, long 
   __syncthreads();
 }
 
-// out_i = ca a_i + cb b_i + cs sum_k A[i, J_k] coef_k for i < m (FP64; a, b may be null).
+// Power-of-two scale of a vector for the float-float products: every thread returns the
+// scale that brings max |v_k| (k < len) into [1, 2) and its inverse (bits: one shared
+// 64-bit word).  Ends with a block barrier.
+template <int BT>
+__device__ __forceinline__ void bscale(const double* v, long long len, unsigned long long* bits, double& scale,
+                                       double& unscale) {
+  if (threadIdx.x == 0) *bits = 0ull;
+  __syncthreads();
+  unsigned long long mb = 0ull;
+  for (long long k = threadIdx.x; k < len; k += BT) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v[k]) & 0x7FFFFFFFFFFFFFFFull;
+    mb = b > mb ? b : mb;
+  }
+  atomicMax(bits, mb);
+  __syncthreads();
+  int ex = (int)((*bits >> 52) & 0x7FF);
+  if (ex == 0 || ex == 0x7FF) ex = 1023;
+  scale = __longlong_as_double((long long)(2046 - ex) << 52);
+  unscale = __longlong_as_double((long long)ex << 52);
+}
+
+// out_i = ca a_i + cb b_i + cs sum_k A[i, J_k] coef_k for i < m (a, b may be null).  The
+// sum runs in float-float on the FP32 pipe (one SM's FP64 pipe retires about two FMAs
+// per clock): coef is scaled by a power of two and split into FP32 hi / lo parts (csplit,
+// r entries of scratch), every product of an FP32 entry with the split coefficient keeps
+// its error (about 2^-46 relative per product), and the FP64 combination follows.
 // With which != 0 also the dots used by the SsN step: which = 1 (gradient): ||out||^2,
 // ||y||^2, ||y - out||^2, b^T y; which = 2 (direction): g^T out, y^T out, ||out||^2,
 // b^T out, returned in dots[4] (every thread).
@@ -222,20 +285,33 @@ template <int BT>
 __device__ void bgemv_n(const float* __restrict__ A, long long lda, int m, const int* __restrict__ J, long long r,
                         const double* coef, double* out, const double* a, double ca, const double* b, double cb,
                         double cs, int which, const double* yv, const double* bv, const double* gv, double* dots,
-                        double* red) {
+                        double* red, float2* csplit, unsigned long long* bits) {
+  double scale, unscale;
+  bscale<BT>(coef, r, bits, scale, unscale);
+  for (long long k = threadIdx.x; k < r; k += BT) {
+    const double v = coef[k] * scale;
+    const float hi = __double2float_rn(v);
+    csplit[k] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+  __syncthreads();
   double q[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < m; i += BT) {
-    double acc = 0.0;
+    float S = 0.0f, Lo = 0.0f;
     long long k = 0;
     for (; k + 4 <= r; k += 4) {
       const float p0 = A[(long long)J[k] * lda + i], p1 = A[(long long)J[k + 1] * lda + i];
       const float p2 = A[(long long)J[k + 2] * lda + i], p3 = A[(long long)J[k + 3] * lda + i];
-      acc = fma((double)p0, coef[k], acc);
-      acc = fma((double)p1, coef[k + 1], acc);
-      acc = fma((double)p2, coef[k + 2], acc);
-      acc = fma((double)p3, coef[k + 3], acc);
+      const float2 c0 = csplit[k], c1 = csplit[k + 1], c2 = csplit[k + 2], c3 = csplit[k + 3];
+      ffmadd(S, Lo, p0, c0.x, c0.y);
+      ffmadd(S, Lo, p1, c1.x, c1.y);
+      ffmadd(S, Lo, p2, c2.x, c2.y);
+      ffmadd(S, Lo, p3, c3.x, c3.y);
     }
-    for (; k < r; k++) acc = fma((double)A[(long long)J[k] * lda + i], coef[k], acc);
+    for (; k < r; k++) {
+      const float2 c = csplit[k];
+      ffmadd(S, Lo, A[(long long)J[k] * lda + i], c.x, c.y);
+    }
+    const double acc = ((double)S + (double)Lo) * unscale;
     double lin = 0.0;
     if (a) lin = ca * a[i];
     if (b) lin = a ? lin + cb * b[i] : cb * b[i];
@@ -263,20 +339,35 @@ __device__ void bgemv_n(const float* __restrict__ A, long long lda, int m, const
   }
 }
 
-// out_k = ch h_k + cq q_k + cd sum_i A[i, J_k] v_i for k < r (FP64), one warp per k.
+// out_k = ch h_k + cq q_k + cd sum_i A[i, J_k] v_i for k < r, one warp per k, the sum in
+// float-float as in bstream (v scaled by a power of two and split into vh, vl: m floats of
+// shared memory each).
 template <int BT>
 __device__ void bgemv_t(const float* __restrict__ A, long long lda, int m, const int* __restrict__ J, long long r,
                         const double* v, double* out, const double* h, double ch, const double* q, double cq,
-                        double cd) {
+                        double cd, float* vh, float* vl, unsigned long long* bits) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = BT / 32;
+  double scale, unscale;
+  bscale<BT>(v, m, bits, scale, unscale);
+  for (int i = threadIdx.x; i < m; i += BT) {
+    const double z = v[i] * scale;
+    const float hi = __double2float_rn(z);
+    vh[i] = hi;
+    vl[i] = __double2float_rn(z - (double)hi);
+  }
+  __syncthreads();
   for (long long k = warp; k < r; k += NW) {
     const float* col = A + (long long)J[k] * lda;
-    double acc = 0.0;
-    for (int i = lane; i < m; i += 32) acc = fma((double)col[i], v[i], acc);
-    acc = warp_sum(acc);
+    float S = 0.0f, Lo = 0.0f;
+    for (int i = lane; i < m; i += 32) ffmadd(S, Lo, col[i], vh[i], vl[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float S2 = __shfl_xor_sync(0xffffffffu, S, o), L2 = __shfl_xor_sync(0xffffffffu, Lo, o);
+      ffadd(S, Lo, S2, L2);
+    }
     if (lane == 0) {
-      double o = cd * acc;
+      double o = cd * (((double)S + (double)Lo) * unscale);
       if (h) o = ch * h[k] + o;
       if (q) o = cq * q[k] + o;
       out[k] = o;
@@ -431,33 +522,38 @@ __device__ bool bchol(float* G, int N, float* tile, float* panel, int* flag) {
   return true;
 }
 
-// acc = alpha x (first) or acc += alpha x with L L^T x = rhs (FP32 factor, FP64 vectors;
-// L row-major lower, ld = N).  xs: N doubles of scratch (global).
+// acc = alpha x (first) or acc += alpha x with L L^T x = rhs (L row-major lower, ld = N):
+// FP32 arithmetic throughout (the FP32 factor bounds the solve's accuracy; the caller's
+// refinement through A recovers the rest), with rhs scaled by a power of two into FP32's
+// range.  xs: N doubles of scratch (global, used as N floats).
 template <int BT>
 __device__ void btrsv(const float* __restrict__ L, int N, const double* rhs, double* acc, int first, double alpha,
-                      double* xs) {
+                      double* xs_scratch, unsigned long long* bits) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = BT / 32;
-  for (int i = tid; i < N; i += BT) xs[i] = rhs[i];
+  float* xs = reinterpret_cast<float*>(xs_scratch);
+  double scale, unscale;
+  bscale<BT>(rhs, N, bits, scale, unscale);
+  for (int i = tid; i < N; i += BT) xs[i] = __double2float_rn(rhs[i] * scale);
   __syncthreads();
   for (int b0 = 0; b0 < N; b0 += 32) {  // forward: L y = rhs
     const int nb = N - b0 < 32 ? N - b0 : 32;
     if (warp == 0) {
-      double v = lane < nb ? xs[b0 + lane] : 0.0;
+      float v = lane < nb ? xs[b0 + lane] : 0.0f;
       for (int p = 0; p < nb; p++) {
-        double xp = __shfl_sync(0xffffffffu, v, p);
-        xp = xp / (double)L[(long long)(b0 + p) * N + b0 + p];
+        float xp = __shfl_sync(0xffffffffu, v, p);
+        xp = __fdiv_rn(xp, L[(long long)(b0 + p) * N + b0 + p]);
         if (lane == p) v = xp;
-        if (lane > p && lane < nb) v = fma(-(double)L[(long long)(b0 + lane) * N + b0 + p], xp, v);
+        if (lane > p && lane < nb) v = fmaf(-L[(long long)(b0 + lane) * N + b0 + p], xp, v);
       }
       if (lane < nb) xs[b0 + lane] = v;
     }
     __syncthreads();
     for (int i = b0 + nb + tid; i < N; i += BT) {
-      double s = xs[i];
+      float sacc = xs[i];
       const float* row = L + (long long)i * N + b0;
-      for (int p = 0; p < nb; p++) s = fma(-(double)row[p], xs[b0 + p], s);
-      xs[i] = s;
+      for (int p = 0; p < nb; p++) sacc = fmaf(-row[p], xs[b0 + p], sacc);
+      xs[i] = sacc;
     }
     __syncthreads();
   }
@@ -465,25 +561,29 @@ __device__ void btrsv(const float* __restrict__ L, int N, const double* rhs, dou
     const int b0 = bb * 32;
     const int nb = N - b0 < 32 ? N - b0 : 32;
     for (int c = warp; c < nb; c += NW) {  // column b0 + c: the rows below the block
-      double s = 0.0;
-      for (int i = b0 + nb + lane; i < N; i += 32) s = fma((double)L[(long long)i * N + b0 + c], xs[i], s);
-      s = warp_sum(s);
-      if (lane == 0) xs[b0 + c] -= s;
+      float sacc = 0.0f;
+      for (int i = b0 + nb + lane; i < N; i += 32) sacc = fmaf(L[(long long)i * N + b0 + c], xs[i], sacc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) xs[b0 + c] -= sacc;
     }
     __syncthreads();
     if (warp == 0) {
-      double v = lane < nb ? xs[b0 + lane] : 0.0;
+      float v = lane < nb ? xs[b0 + lane] : 0.0f;
       for (int p = nb - 1; p >= 0; p--) {
-        double xp = __shfl_sync(0xffffffffu, v, p);
-        xp = xp / (double)L[(long long)(b0 + p) * N + b0 + p];
+        float xp = __shfl_sync(0xffffffffu, v, p);
+        xp = __fdiv_rn(xp, L[(long long)(b0 + p) * N + b0 + p]);
         if (lane == p) v = xp;
-        if (lane < p) v = fma(-(double)L[(long long)(b0 + p) * N + b0 + lane], xp, v);
+        if (lane < p) v = fmaf(-L[(long long)(b0 + p) * N + b0 + lane], xp, v);
       }
       if (lane < nb) xs[b0 + lane] = v;
     }
     __syncthreads();
   }
-  for (int i = tid; i < N; i += BT) acc[i] = first ? alpha * xs[i] : fma(alpha, xs[i], acc[i]);
+  for (int i = tid; i < N; i += BT) {
+    const double xi = (double)xs[i] * unscale;
+    acc[i] = first ? alpha * xi : fma(alpha, xi, acc[i]);
+  }
   __syncthreads();
 }
 
@@ -623,6 +723,7 @@ __device__ void solve_one(const BatchInst& P, BatchOut& O, const BatchOpts& o, c
   double* rs = reinterpret_cast<double*>(my + L.rs);
   double* cr = reinterpret_cast<double*>(my + L.cr);
   float* G = reinterpret_cast<float*>(my + L.G);
+  float2* csp = reinterpret_cast<float2*>(my + L.cs);
   const double* b = P.b;
   // the fit works on a copy of x: an instance handed back to the host keeps its warm start
   double* x = reinterpret_cast<double*>(my + L.xw);
@@ -647,7 +748,7 @@ __device__ void solve_one(const BatchInst& P, BatchOut& O, const BatchOpts& o, c
   pp.onep = 1.0 + pp.sigma * pp.lam2;
   pp.inv_onep = 1.0 / pp.onep;
   PassNorms pn = bprox<BT>(x, u, t, y, d, n, m, pp, 0, 0.0, 1, J, w, sh.wcnt, red);
-  bgemv_n<BT>(A, lda, m, J, pn.r, w, y, nullptr, 0.0, b, -1.0, 1.0, 0, nullptr, nullptr, nullptr, nullptr, red);
+  bgemv_n<BT>(A, lda, m, J, pn.r, w, y, nullptr, 0.0, b, -1.0, 1.0, 0, nullptr, nullptr, nullptr, nullptr, red, csp, &sh.bits);
   bstream<BT, DEPTH>(A, lda, m, n, y, u, dh, dl, &sh.bits);
   double sigma = o.sigma0;
   int al = 0, newton = 0, trials = 0, converged = 0, host = 0;
@@ -667,28 +768,28 @@ __device__ void solve_one(const BatchInst& P, BatchOut& O, const BatchOpts& o, c
       apply = 0;
       const long long r = pn.r;
       // g = y + b - A_J w_J with ||g||^2, ||y||^2, ||y - g||^2, b^T y
-      bgemv_n<BT>(A, lda, m, J, r, w, g, y, 1.0, b, 1.0, -1.0, 1, y, b, nullptr, gdots, red);
+      bgemv_n<BT>(A, lda, m, J, r, w, g, y, 1.0, b, 1.0, -1.0, 1, y, b, nullptr, gdots, red, csp, &sh.bits);
       const double gn = sqrt(gdots[0]) / nb1;
       if (!(gn > o.tol) || here >= o.max_newton) break;
       // ---- Newton direction: (I + kappa A_J A_J^T) d = -g
       if (r == 0) {
-        bgemv_n<BT>(A, lda, m, J, 0, w, d, nullptr, 0.0, g, -1.0, 0.0, 2, y, b, g, dots, red);
+        bgemv_n<BT>(A, lda, m, J, 0, w, d, nullptr, 0.0, g, -1.0, 0.0, 2, y, b, g, dots, red, csp, &sh.bits);
       } else if (r < m) {
         const int N = (int)r;
         bsyrk<BT>(A, lda, m, J, r, 0, (float)(1.0 / kappa), 1.0f, G, As, Bs);
-        bgemv_t<BT>(A, lda, m, J, r, g, h, nullptr, 0.0, nullptr, 0.0, 1.0);
+        bgemv_t<BT>(A, lda, m, J, r, g, h, nullptr, 0.0, nullptr, 0.0, 1.0, dh, dl, &sh.bits);
         if (!bchol<BT>(G, N, As, panel, &sh.flag)) {
           host = 1;
           break;
         }
-        btrsv<BT>(G, N, h, q, 1, 1.0, cr);
+        btrsv<BT>(G, N, h, q, 1, 1.0, cr, &sh.bits);
         double rho = 0.0;
         for (int it = 0; it < o.refine; it++) {
           // rs = h - kappa^{-1} q - A_J^T (A_J q); correction cr2 = G^{-1} rs
           bgemv_n<BT>(A, lda, m, J, r, q, tm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr, nullptr, nullptr, nullptr,
-                      red);
-          bgemv_t<BT>(A, lda, m, J, r, tm, rs, h, 1.0, q, -1.0 / kappa, -1.0);
-          btrsv<BT>(G, N, rs, rv, 1, 1.0, cr);
+                      red, csp, &sh.bits);
+          bgemv_t<BT>(A, lda, m, J, r, tm, rs, h, 1.0, q, -1.0 / kappa, -1.0, dh, dl, &sh.bits);
+          btrsv<BT>(G, N, rs, rv, 1, 1.0, cr, &sh.bits);
           double v2[2] = {0.0, 0.0};
           for (int k = tid; k < N; k += BT) {
             const double c = rv[k], nq = q[k] + c;
@@ -703,20 +804,20 @@ __device__ void solve_one(const BatchInst& P, BatchOut& O, const BatchOpts& o, c
           host = 1;
           break;
         }
-        bgemv_n<BT>(A, lda, m, J, r, q, d, nullptr, 0.0, g, -1.0, 1.0, 2, y, b, g, dots, red);
+        bgemv_n<BT>(A, lda, m, J, r, q, d, nullptr, 0.0, g, -1.0, 1.0, 2, y, b, g, dots, red, csp, &sh.bits);
       } else {
         bsyrk<BT>(A, lda, m, J, r, 1, 1.0f, (float)kappa, G, As, Bs);
         if (!bchol<BT>(G, m, As, panel, &sh.flag)) {
           host = 1;
           break;
         }
-        btrsv<BT>(G, m, g, d, 1, -1.0, cr);
+        btrsv<BT>(G, m, g, d, 1, -1.0, cr, &sh.bits);
         double rho = 0.0;
         for (int it = 0; it < o.refine; it++) {
           // tm = -g - d - kappa A_J (A_J^T d); d += M^{-1} tm
-          bgemv_t<BT>(A, lda, m, J, r, d, rv, nullptr, 0.0, nullptr, 0.0, 1.0);
-          bgemv_n<BT>(A, lda, m, J, r, rv, tm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr, nullptr, nullptr, red);
-          btrsv<BT>(G, m, tm, rs, 1, 1.0, cr);
+          bgemv_t<BT>(A, lda, m, J, r, d, rv, nullptr, 0.0, nullptr, 0.0, 1.0, dh, dl, &sh.bits);
+          bgemv_n<BT>(A, lda, m, J, r, rv, tm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr, nullptr, nullptr, red, csp, &sh.bits);
+          btrsv<BT>(G, m, tm, rs, 1, 1.0, cr, &sh.bits);
           double v2[2] = {0.0, 0.0};
           for (int i = tid; i < m; i += BT) {
             const double c = rs[i], nd = d[i] + c;
@@ -829,18 +930,24 @@ __global__ void __launch_bounds__(BT, 1) k_batch_solve(const BatchInst* __restri
 }  // namespace
 
 // Host side: sizes the scratch, builds the descriptors, launches the persistent kernel.
+// m_max rounded up to a multiple of 4: the split vector (dh, dl) is read 16 bytes at a time
+static int m_max4(int m_max) { return (m_max + 3) & ~3; }
+
 size_t batch_smem_bytes(int m_max) {
+  m_max = m_max4(m_max);
   return sizeof(float) * ((size_t)2 * kTile * 33 + (size_t)2 * m_max + (size_t)m_max * 33);
 }
 
 static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 size_t batch_slot_bytes(long long n_max, int m_max) {
+  m_max = m_max4(m_max);
   size_t off = 0;
   off += 5 * align256(sizeof(double) * (size_t)n_max);  // u, t, w, rv, xw
   off += align256(sizeof(int) * (size_t)n_max);          // J
   off += 9 * align256(sizeof(double) * (size_t)m_max);   // y, d, g, tm, q, h, rs, cr, spare
   off += align256(sizeof(float) * (size_t)m_max * (size_t)m_max);
+  off += align256(sizeof(float2) * (size_t)n_max);      // cs: split coefficients of the panel products
   return off;
 }
 
@@ -850,6 +957,7 @@ size_t batch_slot_bytes(long long n_max, int m_max) {
 bool launch_batch_solve(const void* inst_dev, const int* order_dev, int count, int* next_dev, void* out_dev,
                         const double* opt6, const int* opt4, long long n_max, int m_max, unsigned char* scratch,
                         int blocks, int depth, cudaStream_t s) {
+  m_max = m_max4(m_max);
   BatchOpts o;
   o.sigma0 = opt6[0];
   o.sigma_growth = opt6[1];
@@ -884,6 +992,7 @@ bool launch_batch_solve(const void* inst_dev, const int* order_dev, int count, i
   L.cr = take(sizeof(double) * (size_t)m_max);
   take(sizeof(double) * (size_t)m_max);
   L.G = take(sizeof(float) * (size_t)m_max * (size_t)m_max);
+  L.cs = take(sizeof(float2) * (size_t)n_max);
   L.slot_bytes = off;
   L.m_max = m_max;
   const size_t smem = batch_smem_bytes(m_max);

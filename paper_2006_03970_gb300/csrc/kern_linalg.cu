@@ -747,6 +747,21 @@ __device__ __forceinline__ void push_tile(unsigned src, unsigned dst, unsigned b
     bulk_s2c(cluster_addr(dst, lane), src, bytes, cluster_addr(bar, lane));
 }
 
+// W = L^{-1} for the factored 32 x 32 diagonal tile D (lower, row stride 33) by one warp:
+// lane j forms column j by forward substitution; W is stored row-major at Wout.
+__device__ __forceinline__ void inverse_diag_warp(const float* D, float* __restrict__ Wout, int lane) {
+  float w[32];
+#pragma unroll
+  for (int i = 0; i < 32; i++) {
+    float s = (i == lane) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int q = 0; q < i; q++) s = fmaf(-D[i * 33 + q], w[q], s);
+    w[i] = s * __frcp_rn(D[i * 33 + i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 32; i++) Wout[i * 32 + lane] = w[i];
+}
+
 // Named barrier of the four diagonal warps (0-3) of a CTA.
 __device__ __forceinline__ void diag_quad_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -987,17 +1002,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
     for (int e = 0; m; e++, m &= m - 1) {
       if ((e & 7) != warp) continue;
       const int sl = __ffs(m) - 1, k = __shfl_sync(0xffffffffu, my_i, sl);
-      const float* D = own + sl * kTileF;
-      float w[32];
-#pragma unroll
-      for (int i = 0; i < 32; i++) {
-        float s = (i == lane) ? 1.0f : 0.0f;
-#pragma unroll
-        for (int q = 0; q < i; q++) s = fmaf(-D[i * 33 + q], w[q], s);
-        w[i] = s * __frcp_rn(D[i * 33 + i]);
-      }
-#pragma unroll
-      for (int i = 0; i < 32; i++) Wdiag[(long long)k * 1024 + i * 32 + lane] = w[i];
+      inverse_diag_warp(own + sl * kTileF, Wdiag + (long long)k * 1024, lane);
     }
   }
   // ---- write the factor back (lower part, inside N); consecutive threads take

@@ -14,6 +14,8 @@ or two while its operands still exceed the 129 MB L2 of a GB300:
                    r = 1500 on BF16 storage: SYRK over K = r, the super-block Cholesky
                    (cluster factors, block solve, trailing update) and the cluster solves
   prox-1e6         the active-set pass and its compaction at n = 1e6, ~0.1 % active
+  batch-152        the device-resident batched solver, 152 instances of the batched
+                   workload's generator with n <= 5000 (one launch of k_batch_solve)
   shared-4         four mixed-form fits on the precision-small matrix advanced together
                    (ssnal_en_solve_shared): one merged pass over A per Newton step
 
@@ -94,6 +96,27 @@ def prox_1e6(n=1_000_000, m=64, repeats=3):
     return r
 
 
+def batch_152(count=152):
+    """The device-resident batched solver on one instance per SM: the batched workload's
+    generator (m log-uniform [50, 500], n log-uniform [1e3, 5e4], FP32) with n capped at
+    5000, so that one launch of k_batch_solve runs a few milliseconds."""
+    import torch
+    import paper_2006_03970_gb300 as pkg
+    from paper_2006_03970_gb300 import synth
+    probs = [p for p in synth.config4_instances(4 * count) if p.At.shape[0] <= 5000][:count]
+    fits, keep = [], []
+    for p in probs:
+        A = torch.as_tensor(np.ascontiguousarray(p.At, dtype=np.float32), device="cuda")
+        b = torch.as_tensor(p.b, dtype=torch.float64, device="cuda")
+        x = torch.zeros(p.At.shape[0], dtype=torch.float64, device="cuda")
+        g = float(np.abs(p.At.astype(np.float64) @ p.b).max())
+        fits.append((A, p.At.shape[1], b, p.c * g, (1 - p.alpha) / p.alpha * p.c * g, x))
+        keep.append(A)
+    st, res, info = pkg.ssnal_en_solve_batch_resident(fits)
+    torch.cuda.synchronize()
+    return st, sum(1 for r in res if r.status == 0), info
+
+
 def shared_4(n=100_000, m=1000):
     """Four mixed-form fits on the precision-small matrix through ssnal_en_solve_shared: their
     Newton-step passes over A merged into one k_stream_multi launch per step."""
@@ -121,7 +144,7 @@ def shared_4(n=100_000, m=1000):
 
 
 CASES = {"precision-small": precision_small, "newton-730": newton_730, "newton-1000": newton_1000,
-         "shared-4": shared_4, "prox-1e6": prox_1e6}
+         "shared-4": shared_4, "prox-1e6": prox_1e6, "batch-152": batch_152}
 
 
 def main(argv):
