@@ -1365,7 +1365,7 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 // shared memory and a local mbarrier arrival, the other CTAs through st.async
 // completing on their per-block mbarriers.  Every wait is bounded
 // (DevState::timeout).
-constexpr int kTrsvPairMaxT = 27;
+constexpr int kTrsvPairMaxT = 32;  // 32 tile rows: N <= 1024 (the m x m systems of m = 1000 included)
 constexpr int kTrsvQ = 4;     // CTAs per cluster
 constexpr int kTrsvRing = 6;  // tiles in flight per warp
 constexpr int kTrsvMaxT0 = (kTrsvPairMaxT + kTrsvQ - 1) / kTrsvQ;
