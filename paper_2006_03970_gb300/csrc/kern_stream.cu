@@ -910,8 +910,7 @@ static size_t lane_smem(int m, int stages, int elt) {
   return (size_t)kLWarps * stages * kLBoxBytes + (size_t)mpad * 12 + (size_t)kLWarps * stages * 8 + 1024;
 }
 
-static int lane_stages(int m, int elt) {
-  const size_t budget = kLDynMax;  // dynamic shared memory left beside the static part
+static int lane_stages(int m, int elt, size_t budget = kLDynMax) {  // budget: dynamic bytes beside the static part
   const int mpad = lane_mpad(m, elt);
   int st = (int)((budget - (size_t)mpad * 12 - 1024) / ((size_t)kLWarps * kLBoxBytes + kLWarps * 8));
   if (st > 8) st = 8;
@@ -1014,13 +1013,18 @@ static void launch_lane(const void* map, int m, long long n, const double* vec, 
                         const double* u, LsParams lp, DevState* st, double* partials, int sms, cudaStream_t s,
                         const float* cmean, const float* cscale) {
   static bool configured[64] = {};
+  static size_t dyn_max = kLDynMax;  // per-block shared memory minus this instantiation's static part
   int dev = 0;
   cudaGetDevice(&dev);
-  const int stages = lane_stages(m, ELT);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaFuncSetAttribute(k_stream_lane<MODE, ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLDynMax);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_stream_lane<MODE, ELT>) == cudaSuccess && fa.sharedSizeBytes < 232448)
+      dyn_max = 232448 - fa.sharedSizeBytes;
+    cudaGetLastError();
+    cudaFuncSetAttribute(k_stream_lane<MODE, ELT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
+  const int stages = lane_stages(m, ELT, dyn_max);
   LaneCfg cfg;
   cfg.stages = stages;
   cfg.chunks = ELT == kEltSplit ? (((m + 1) & ~1) + 15) / 16 : (m + elt_rows(ELT) - 1) / elt_rows(ELT);
