@@ -46,10 +46,14 @@ WORKLOAD = ("precision configuration: m=1000, n=1000000, 50-feature AR(1) blocks
 M2, N2, K2, ALPHA2, SEED2 = 500, 100_000, 20, 0.6, 2
 WORKLOAD2 = ("FP64 warm-started Elastic Net path: m=500, n=100000, 100-feature AR(1) blocks rho=0.7, "
              "20 nonzeros +-U[1,3], snr 5, alpha=0.6, c 1.0->0.05 geometric (20 points), tol 1e-6, seed 2")
-# dram__bytes_read.sum + dram__bytes_write.sum per launch (ncu), see profiles/
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from ncu captures of the
+# current kernels.  The pre-split FP64 Newton pass is captured at the path's own size; the
+# BF16 passes at n = 1e5 (profiling case precision-small) and scaled to n = 1e6 by the columns
+# processed (the per-launch m-vector reads are under 1 %).
 TRAFFIC = {
-    # k_stream_lane<kModeT> over the pre-split float-pair copy, m=500 n=1e5
-    "split_modeT_m500_n1e5": 401668352 + 3752704,
+    "split_modeT_m500_n1e5": 405469312,
+    "bf16_modeT_m1000_n1e6": 205587712 * 10,
+    "bf16ff_modeU_m1000_n1e6": 204056448 * 10,
 }
 
 
