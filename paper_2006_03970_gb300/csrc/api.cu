@@ -66,6 +66,7 @@ struct ssnal_en_ctx {
   float* G = nullptr;
   int64_t ldg = 0;
   float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
+  double* rpart = nullptr; // per-row-block norms of the refinement step fused into the pair solve
   int last_wdiag = 0;      // the last FP32 factor wrote Wdiag
   double* corr = nullptr;  // first refinement correction (capacity max(m, rcap))
   double* cgp = nullptr;   // search direction of the CG Newton solve (m)
@@ -214,6 +215,7 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->P32);
   dev_free(c->G);
   dev_free(c->Wdiag);
+  dev_free(c->rpart);
   dev_free(c->corr);
   dev_free(c->cgp);
   dev_free(c->G64);
@@ -525,8 +527,7 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
                     nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
       launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
       if (it == 0) {  // the first correction is the FP32 solve's error: test the contraction
-        launch_trsv_llt(c->G, c->ldg, N, c->resr, c->corr, 1, 1.0, wd, c->st, s);
-        launch_refine_update(c->q, c->corr, N, kRefineTau, c->st, s);
+        launch_trsv_refine(c->G, c->ldg, N, c->resr, c->q, c->corr, wd, c->rpart, kRefineTau, c->st, s);
       } else {
         launch_trsv_llt(c->G, c->ldg, N, c->resr, c->q, 0, 1.0, wd, c->st, s);
       }
@@ -555,8 +556,7 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
                     nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
       if (it == 0) {
-        launch_trsv_llt(c->G, c->ldg, m, c->tmpm, c->corr, 1, 1.0, wd, c->st, s);
-        launch_refine_update(d, c->corr, m, kRefineTau, c->st, s);
+        launch_trsv_refine(c->G, c->ldg, m, c->tmpm, d, c->corr, wd, c->rpart, kRefineTau, c->st, s);
       } else {
         launch_trsv_llt(c->G, c->ldg, m, c->tmpm, d, 0, 1.0, wd, c->st, s);
       }
@@ -581,16 +581,14 @@ ssnal_en_status refine_once(ssnal_en_ctx* c, int64_t r, double kappa, const doub
     launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, c->tmpm, nullptr, 0.0, nullptr, 0.0, 1.0, 0, nullptr,
                   nullptr, nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
     launch_gemv_t(c->P, c->ldp, m, r, c->tmpm, c->resr, c->h, 1.0, c->q, -1.0 / kappa, -1.0, c->sms, s);
-    launch_trsv_llt(c->G, c->ldg, N, c->resr, c->corr, 1, 1.0, wd, c->st, s);
-    launch_refine_update(c->q, c->corr, N, kRefineTau, c->st, s);
+    launch_trsv_refine(c->G, c->ldg, N, c->resr, c->q, c->corr, wd, c->rpart, kRefineTau, c->st, s);
     launch_gemv_n(c->P, c->ldp, m, c->q, c->st, r, c->rcap, d, nullptr, 0.0, g, -1.0, 1.0, 0, nullptr, nullptr,
                   nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
   } else {
     launch_gemv_t(c->P, c->ldp, m, r, d, c->h, nullptr, 0.0, nullptr, 0.0, 1.0, c->sms, s);
     launch_gemv_n(c->P, c->ldp, m, c->h, c->st, r, c->rcap, c->tmpm, g, -1.0, d, -1.0, -kappa, 0, nullptr, nullptr,
                   nullptr, c->st, c->comb_scratch, c->cpart, c->tile_ctr, s);
-    launch_trsv_llt(c->G, c->ldg, m, c->tmpm, c->corr, 1, 1.0, wd, c->st, s);
-    launch_refine_update(d, c->corr, m, kRefineTau, c->st, s);
+    launch_trsv_refine(c->G, c->ldg, m, c->tmpm, d, c->corr, wd, c->rpart, kRefineTau, c->st, s);
   }
   CK(cudaGetLastError());
   return SSNAL_EN_OK;
@@ -1189,6 +1187,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->comb_scratch, 4 * ((m + 31) / 32) + 4);
   AL(c->cpart, (size_t)kGemvSplitMax * m);
   AL(c->tile_ctr, (m + 31) / 32);
+  AL(c->rpart, 2 * ((m + 31) / 32) + 2);
   AL(c->G, c->ldg * m);
   AL(c->Wdiag, (size_t)((m + 31) / 32) * 1024);
   AL(c->tc_part, syrk_tc_part_floats(c->sms));

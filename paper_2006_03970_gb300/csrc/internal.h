@@ -26,7 +26,8 @@ constexpr int kNumCounters = 16;  // last-block-done counters
 enum CounterSlot {
   kCtrProx = 0, kCtrCombine = 1, kCtrStream = 2, kCtrFallback = 3, kCtrGmax = 4, kCtrMisc = 5,
   kCtrBarrier = 6,  // two words: arrival count and generation of the cooperative grid barrier
-  kCtrGemv = 8
+  kCtrGemv = 8,
+  kCtrRefine = 9  // the refinement step fused into the pair triangular solve
 };
 constexpr int kSmallNewton = 32;  // Newton systems up to this size (one tile) are factored by one CTA
 
@@ -156,6 +157,13 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 bool make_factor_tensor_map(void* map_out, const float* L, long long ld, int N);
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s);
+// One refinement step of an FP32 solve with its contraction test: acc += c with
+// (L L^T) c = rhs, st->refine_ratio = ||c|| / ||acc + c|| and st->newton_bad when it exceeds
+// tau.  One launch of the pair solve where it applies (rpart: 2 ceil(N / 32) doubles of
+// scratch for its per-row-block partial norms); otherwise the solve into corr (N doubles)
+// followed by launch_refine_update.
+void launch_trsv_refine(const float* L, long long ldl, int N, const double* rhs, double* acc, double* corr,
+                        const float* Wdiag, double* rpart, double tau, DevState* st, cudaStream_t s);
 
 // ---- FP64 Newton system (kern_f64.cu): the Newton matrix formed, factored and solved in FP64,
 // used when the FP32 factor fails or its refinement does not contract, or always on request.

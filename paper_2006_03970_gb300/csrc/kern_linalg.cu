@@ -1372,7 +1372,8 @@ constexpr int kTrsvMaxT0 = (kTrsvPairMaxT + kTrsvQ - 1) / kTrsvQ;
 
 __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0)
     k_trsv_pair(const __grid_constant__ CUtensorMap tmL, int N, const double* __restrict__ rhs,
-                double* __restrict__ acc, int first, double alpha, const float* __restrict__ Wd, DevState* st) {
+                double* __restrict__ acc, int first, double alpha, const float* __restrict__ Wd, DevState* st,
+                double* __restrict__ rpart, double tau2) {
   pdl_entry();
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -1502,7 +1503,22 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
       if (t + kTrsvRing < ntile) issue(t + kTrsvRing);
     }
     r = wr_product();  // c_J = W_JJ^T r_J: lane l takes column l of W
-    if (live) acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
+    if (rpart) {
+      // refinement step: acc += c, and this row block's ||c||^2, ||acc + c||^2 (fixed order)
+      double ci = 0.0, ai = 0.0;
+      if (live) {
+        ci = (double)r;
+        ai = acc[row] + ci;
+        acc[row] = ai;
+      }
+      const double q0 = warp_sum(ci * ci), q1 = warp_sum(ai * ai);
+      if (lane == 0) {
+        rpart[2 * J] = q0;
+        rpart[2 * J + 1] = q1;
+      }
+    } else if (live) {
+      acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
+    }
     publish(cbuf, bars + T + J);
   }
   // every value sent to this CTA has landed before it exits (the ring copies of a
@@ -1510,6 +1526,19 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
   for (int k = tid; k < 2 * T; k += blockDim.x)
     if (ok && !mbar_wait(smem_u32(bars + k), 0u)) ok = false;
   if (!ok) st->timeout = 1;
+  if (rpart && last_block(&st->counters[kCtrRefine])) {
+    // the contraction test of the refinement: the row blocks' partial norms in order
+    if (tid == 0) {
+      double c2 = 0.0, a2 = 0.0;
+      for (int j = 0; j < T; j++) {
+        c2 += ld_cg(rpart + 2 * j);
+        a2 += ld_cg(rpart + 2 * j + 1);
+      }
+      st->refine_ratio = a2 > 0.0 ? sqrt(c2 / a2) : (c2 > 0.0 ? INFINITY : 0.0);
+      if (!(c2 <= tau2 * a2)) st->newton_bad = 1;
+    }
+    reset_counter(&st->counters[kCtrRefine]);
+  }
   __syncthreads();
   cluster.sync();
 }
@@ -2118,6 +2147,41 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
   launch_k(k_tile1_solve, dim3(1), dim3(32), 0, s, G, ldg, N, 1, st, rhs, acc, 1, alpha);
 }
 
+// The pair solve (k_trsv_pair) when N <= 32 kTrsvPairMaxT and a tensor map over L can be made;
+// false when it does not apply or the launch failed.  rpart != nullptr: the refinement mode
+// (acc += c with the contraction test, see k_trsv_pair).
+static bool launch_trsv_pair(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
+                             double alpha, const float* Wdiag, DevState* st, double* rpart, double tau2,
+                             cudaStream_t s) {
+  CUtensorMap tmL;
+  if (N <= kSmallNewton || N > 32 * kTrsvPairMaxT || !make_factor_tensor_map(&tmL, L, ldl, N)) return false;
+  const int T = (N + 31) / 32, T0 = (T + kTrsvQ - 1) / kTrsvQ;
+  const size_t smem = 1024 + (size_t)T0 * kTrsvRing * 4096 + (size_t)2 * T * 32 * sizeof(float) +
+                      (size_t)(2 * T + T0 * kTrsvRing) * 8 + (size_t)T0 * 32 * sizeof(float);
+  static bool done_pr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !done_pr[dev]) {
+    const int T0m = kTrsvMaxT0;
+    cudaFuncSetAttribute(k_trsv_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(1024 + (size_t)T0m * kTrsvRing * 4096 + (size_t)2 * kTrsvPairMaxT * 32 * sizeof(float) +
+                               (size_t)(2 * kTrsvPairMaxT + T0m * kTrsvRing) * 8 + (size_t)T0m * 32 * sizeof(float)));
+    if (dev >= 0 && dev < 64) done_pr[dev] = true;
+  }
+  count_launch();
+  launch_k(k_trsv_pair, dim3(kTrsvQ), dim3(32 * T0), smem, s, tmL, N, rhs, acc, first, alpha, Wdiag, st, rpart,
+           tau2);
+  return cudaGetLastError() == cudaSuccess;
+}
+
+void launch_trsv_refine(const float* L, long long ldl, int N, const double* rhs, double* acc, double* corr,
+                        const float* Wdiag, double* rpart, double tau, DevState* st, cudaStream_t s) {
+  if (N <= 0) return;
+  if (Wdiag && rpart && launch_trsv_pair(L, ldl, N, rhs, acc, 0, 1.0, Wdiag, st, rpart, tau * tau, s)) return;
+  launch_trsv_llt(L, ldl, N, rhs, corr, 1, 1.0, Wdiag, st, s);
+  launch_refine_update(acc, corr, N, tau, st, s);
+}
+
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s) {
   if (N <= 0) return;
@@ -2132,25 +2196,7 @@ void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, do
     launch_k(k_trsv_small, dim3(1), dim3(kSmallThreads), (size_t)(kSmallSmem), s, L, ldl, N, rhs, acc, first, alpha);
     return;
   }
-  CUtensorMap tmL;
-  if (Wdiag && N <= 32 * kTrsvPairMaxT && make_factor_tensor_map(&tmL, L, ldl, N)) {
-    const int T = (N + 31) / 32, T0 = (T + kTrsvQ - 1) / kTrsvQ;
-    const size_t smem = 1024 + (size_t)T0 * kTrsvRing * 4096 + (size_t)2 * T * 32 * sizeof(float) +
-                        (size_t)(2 * T + T0 * kTrsvRing) * 8 + (size_t)T0 * 32 * sizeof(float);
-    static bool done_pr[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || !done_pr[dev]) {
-      const int T0m = kTrsvMaxT0;
-      cudaFuncSetAttribute(k_trsv_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(1024 + (size_t)T0m * kTrsvRing * 4096 + (size_t)2 * kTrsvPairMaxT * 32 * sizeof(float) +
-                                 (size_t)(2 * kTrsvPairMaxT + T0m * kTrsvRing) * 8 + (size_t)T0m * 32 * sizeof(float)));
-      if (dev >= 0 && dev < 64) done_pr[dev] = true;
-    }
-    count_launch();
-    launch_k(k_trsv_pair, dim3(kTrsvQ), dim3(32 * T0), smem, s, tmL, N, rhs, acc, first, alpha, Wdiag, st);
-    if (cudaGetLastError() == cudaSuccess) return;
-  }
+  if (Wdiag && launch_trsv_pair(L, ldl, N, rhs, acc, first, alpha, Wdiag, st, nullptr, 0.0, s)) return;
   if (Wdiag && N <= 32 * kTrsvCLMaxT) {
     const int T = (N + 31) / 32;
     const int warps = (T + kTrsvCL - 1) / kTrsvCL;
