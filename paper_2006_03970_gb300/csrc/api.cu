@@ -66,6 +66,7 @@ struct ssnal_en_ctx {
   float* G = nullptr;
   int64_t ldg = 0;
   float* Wdiag = nullptr;  // inverses of the factor's 32 x 32 diagonal blocks
+  float* zf = nullptr;     // z = L^{-1} h from a factor that ran the forward substitution (m floats)
   double* rpart = nullptr; // per-row-block norms of the refinement step fused into the pair solve
   int last_wdiag = 0;      // the last FP32 factor wrote Wdiag
   double* corr = nullptr;  // first refinement correction (capacity max(m, rcap))
@@ -215,6 +216,7 @@ void free_all(ssnal_en_ctx* c) {
   dev_free(c->P32);
   dev_free(c->G);
   dev_free(c->Wdiag);
+  dev_free(c->zf);
   dev_free(c->rpart);
   dev_free(c->corr);
   dev_free(c->cgp);
@@ -517,9 +519,12 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_chol_solve_small(c->G, c->ldg, N, c->st, c->h, c->q, 1.0, s);
       c->last_wdiag = 0;
     } else {
-      wd = chol_factor(c->G, c->ldg, N, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
+      // the factor runs the forward substitution of h where it can (z in zf)
+      bool fused = false;
+      wd = chol_factor(c->G, c->ldg, N, c->st, c->Wdiag, s, c->h, c->zf, &fused) ? c->Wdiag : nullptr;
       c->last_wdiag = wd != nullptr;
-      launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, wd, c->st, s);
+      if (!(fused && wd && launch_trsv_back(c->G, c->ldg, N, c->zf, c->q, 1, 1.0, wd, c->st, s)))
+        launch_trsv_llt(c->G, c->ldg, N, c->h, c->q, 1, 1.0, wd, c->st, s);
     }
     for (int it = 0; it < refine; it++) {
       // resr = h - kappa^{-1} q - A_J^T (A_J q)
@@ -546,9 +551,11 @@ ssnal_en_status newton_direction(ssnal_en_ctx* c, int64_t r, double kappa, const
       launch_chol_solve_small(c->G, c->ldg, m, c->st, g, d, -1.0, s);
       c->last_wdiag = 0;
     } else {
-      wd = chol_factor(c->G, c->ldg, m, c->st, c->Wdiag, s) ? c->Wdiag : nullptr;
+      bool fused = false;
+      wd = chol_factor(c->G, c->ldg, m, c->st, c->Wdiag, s, g, c->zf, &fused) ? c->Wdiag : nullptr;
       c->last_wdiag = wd != nullptr;
-      launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, wd, c->st, s);
+      if (!(fused && wd && launch_trsv_back(c->G, c->ldg, m, c->zf, d, 1, -1.0, wd, c->st, s)))
+        launch_trsv_llt(c->G, c->ldg, m, g, d, 1, -1.0, wd, c->st, s);
     }
     for (int it = 0; it < refine; it++) {
       // tmpm = -g - d - kappa A_J (A_J^T d)
@@ -1190,6 +1197,7 @@ ssnal_en_status ssnal_en_create(ssnal_en_ctx** out, const ssnal_en_matrix* A, co
   AL(c->rpart, 2 * ((m + 31) / 32) + 2);
   AL(c->G, c->ldg * m);
   AL(c->Wdiag, (size_t)((m + 31) / 32) * 1024);
+  AL(c->zf, m);
   AL(c->tc_part, syrk_tc_part_floats(c->sms));
 #undef AL
   if (s == SSNAL_EN_OK && cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) s = SSNAL_EN_ENOMEM;

@@ -136,8 +136,12 @@ void launch_syrk_nt(const float* P32, long long ldp32, int m, long long r, doubl
                     cudaStream_t s);
 // Wdiag (may be null): receives the inverses of the 32 x 32 diagonal blocks of L
 // when the factorisation produces them (the cluster kernel).  Returns whether
-// they were written.
-bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s);
+// they were written.  hrow, zout (may be null): the right-hand side h (N doubles) of
+// the first solve; where the factor can run the forward substitution itself (one
+// cluster launch, N % 32 != 0, Wdiag given) it writes z = L^{-1} h (FP32) to zout and
+// sets *fused, so that launch_trsv_back finishes the solve.
+bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s,
+                 const double* hrow = nullptr, float* zout = nullptr, bool* fused = nullptr);
 // *out = tr(G^{-1}) - (Np - N) + ... see kern_linalg.cu: factors the N x N SPD matrix in S (row
 // stride ldS >= 2 * round_up(N, 32)) and writes ||L^{-1}||_F^2 + (Np - N) to *out (device).
 // N <= 640; returns false otherwise or on a launch error.
@@ -157,6 +161,11 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 bool make_factor_tensor_map(void* map_out, const float* L, long long ld, int N);
 void launch_trsv_llt(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                      double alpha, const float* Wdiag, DevState* st, cudaStream_t s);
+// The backward half of that solve, L^T c = z (z = L^{-1} h from chol_factor, FP32):
+// acc = (first ? alpha c : acc + alpha c).  Returns false when the pair solve does not
+// apply or its launch failed (the caller then solves with launch_trsv_llt from h).
+bool launch_trsv_back(const float* L, long long ldl, int N, const float* z, double* acc, int first, double alpha,
+                      const float* Wdiag, DevState* st, cudaStream_t s);
 // One refinement step of an FP32 solve with its contraction test: acc += c with
 // (L L^T) c = rhs, st->refine_ratio = ||c|| / ||acc + c|| and st->newton_bad when it exceeds
 // tau.  One launch of the pair solve where it applies (rpart: 2 ceil(N / 32) doubles of

@@ -546,6 +546,13 @@ __global__ void __launch_bounds__(kMidThreads) k_trsv_mid(const float* __restric
 // stored transposed with row stride 32 once solved), the panel buffer(s) of
 // transposed tiles (32 x 32), L^T of the current diagonal tile with its
 // reciprocal diagonal, and a staging copy of it; the mbarriers are static.
+// With hrow (N not a multiple of 32) the forward substitution z = L^{-1} h runs inside
+// the factor: h^T is appended as row N of the matrix (a padding row of the last tile
+// row) with the diagonal entry kAugDiag, so the right-looking factor of the augmented
+// matrix forms row N of its factor as z^T (the panel solves of the last tile row apply
+// the same substitution to it), at no extra tile.  z goes to zout; that row is then reset
+// to a unit row, so the factor and its inverse diagonal blocks of the first N rows are
+// those of G alone.
 namespace cgx = cooperative_groups;
 constexpr int kClusterCTAs = 8;
 // Threads per CTA of k_chol_cluster: warps 0-3 keep the diagonal tiles (warp 0
@@ -562,6 +569,9 @@ constexpr size_t kClusterSmemLimit = 232448 - 2048;       // dynamic shared memo
 constexpr int kTileF = 32 * 33;                           // floats per padded tile
 constexpr unsigned kTileBytes = kTileF * sizeof(float);   // 4224, a multiple of 16
 constexpr unsigned kPanelBytes = 1024 * sizeof(float);    // a transposed panel tile
+// diagonal entry of the appended row h^T: its pivot kAugDiag - ||z||^2 stays positive
+// and finite (L_NN about 1e15, 1 / L_NN about 1e-15)
+constexpr float kAugDiag = 1e30f;
 
 __host__ __device__ constexpr int cluster_slots(int T, int C = kClusterCTAs) { return (T * (T + 1) / 2 + C - 1) / C; }
 // bytes of shared memory with nb panel buffers
@@ -767,7 +777,8 @@ __device__ __forceinline__ void diag_quad_sync() { asm volatile("bar.sync 1, 128
 
 template <int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
-    k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag) {
+    k_chol_cluster(float* __restrict__ G, long long ld, int N, DevState* st, float* __restrict__ Wdiag,
+                   const double* __restrict__ hrow, float* __restrict__ zout) {
   pdl_entry();
   __shared__ __align__(16) float fcol[128];                  // column exchange of the diagonal factor
   __shared__ __align__(8) unsigned long long tbar_s[2 * kClusterTMax];  // panel tile arrivals per (buffer, tile row)
@@ -824,9 +835,13 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
+  const bool aug = hrow != nullptr;  // the host passes h only when N % 32 != 0
+  const int rN = N - 32 * (T - 1);   // row N within the last tile row (with aug)
   for (int sl = 0; sl < nslots; sl++) {
     const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
-    if (ti == tj && tid < 32 && ti * 32 + tid >= N) own[sl * kTileF + tid * 33 + tid] = 1.0f;
+    if (ti == tj && tid < 32 && ti * 32 + tid >= N)
+      own[sl * kTileF + tid * 33 + tid] = (aug && ti * 32 + tid == N) ? kAugDiag : 1.0f;
+    if (aug && ti == T - 1 && tid < 32 && tj * 32 + tid < N) own[sl * kTileF + rN * 33 + tid] = (float)hrow[tj * 32 + tid];
   }
   // panel-column ownership of column j: the CTAs owning a tile (i, j), i > j
   auto receivers_of = [&](int j) {
@@ -994,6 +1009,22 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
   if (bad) st->chol_fail = 1;
   if (!ok) st->timeout = 1;
   __syncthreads();
+  if (aug) {
+    // z = row N of the factor (solved off-diagonal tiles are stored transposed); then
+    // row N of the last diagonal tile becomes a unit row again
+    for (int sl = 0; sl < nslots; sl++) {
+      const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+      if (ti != T - 1 || tid >= 32 || tj * 32 + tid >= N) continue;
+      const float* src = own + sl * kTileF;
+      zout[tj * 32 + tid] = (ti == tj) ? src[rN * 33 + tid] : src[tid * 32 + rN];
+    }
+    __syncthreads();
+    for (int sl = 0; sl < nslots; sl++) {
+      const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+      if (ti == T - 1 && tj == T - 1 && tid < 32) own[sl * kTileF + rN * 33 + tid] = tid == rN ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+  }
   // ---- inverse diagonal blocks for the triangular solves, W_kk = L_kk^{-1}:
   //      one warp per owned diagonal tile, lane j forms column j of W by forward
   //      substitution; W is stored row-major
@@ -1017,8 +1048,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
     }
   }
 }
-template __global__ void k_chol_cluster<kClusterCTAs>(float*, long long, int, DevState*, float*);
-template __global__ void k_chol_cluster<kCluster16CTAs>(float*, long long, int, DevState*, float*);
+template __global__ void k_chol_cluster<kClusterCTAs>(float*, long long, int, DevState*, float*, const double*, float*);
+template __global__ void k_chol_cluster<kCluster16CTAs>(float*, long long, int, DevState*, float*, const double*,
+                                                         float*);
 
 // ---------------------------------------------------------------------------
 // One-tile Newton systems (N <= 32) by one warp.  The lower triangle of G is
@@ -1364,7 +1396,8 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 // are free of bank conflicts).  z_J and c_J reach the owner's warps through
 // shared memory and a local mbarrier arrival, the other CTAs through st.async
 // completing on their per-block mbarriers.  Every wait is bounded
-// (DevState::timeout).
+// (DevState::timeout).  With zin the forward pass is already done (z = L^{-1} h from the
+// factor): each warp starts from z_J and streams only the backward tiles.
 constexpr int kTrsvPairMaxT = 32;  // 32 tile rows: N <= 1024 (the m x m systems of m = 1000 included)
 constexpr int kTrsvQ = 4;     // CTAs per cluster
 constexpr int kTrsvRing = 6;  // tiles in flight per warp
@@ -1373,7 +1406,7 @@ constexpr int kTrsvMaxT0 = (kTrsvPairMaxT + kTrsvQ - 1) / kTrsvQ;
 __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0)
     k_trsv_pair(const __grid_constant__ CUtensorMap tmL, int N, const double* __restrict__ rhs,
                 double* __restrict__ acc, int first, double alpha, const float* __restrict__ Wd, DevState* st,
-                double* __restrict__ rpart, double tau2) {
+                double* __restrict__ rpart, double tau2, const float* __restrict__ zin) {
   pdl_entry();
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -1403,12 +1436,14 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
   if (J < T) {
     const int row = 32 * J + lane;
     const bool live = row < N;
-    float r = live ? (float)rhs[row] : 0.0f;
+    float r = live ? (zin ? zin[row] : (float)rhs[row]) : 0.0f;
     const float* Wb = Wd + (long long)J * 1024;
     // tile t of this warp: forward L[J, t] for t < J, then backward L[I, J], I = T-1 .. J+1
+    // (with zin only the backward ones: t from t0 = J); ring slots count from t0
+    const int t0 = zin ? J : 0;
     auto issue = [&](int t) {
       if (lane == 0) {
-        const int slot = t % kTrsvRing;
+        const int slot = (t - t0) % kTrsvRing;
         const unsigned bar = smem_u32(rbars + slot);
         mbar_expect_tx(bar, 4096);
         if (t < J)
@@ -1418,13 +1453,19 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
       }
     };
     const int ntile = T - 1;
-    for (int t = 0; t < kTrsvRing && t < ntile; t++) issue(t);
+    for (int t = t0; t < t0 + kTrsvRing && t < ntile; t++) issue(t);
     // W_JJ row l (forward) in registers
     float w[32];
 #pragma unroll
     for (int g = 0; g < 8; g++) {
       const float4 v = reinterpret_cast<const float4*>(Wb + lane * 32)[g];
       w[4 * g] = v.x; w[4 * g + 1] = v.y; w[4 * g + 2] = v.z; w[4 * g + 3] = v.w;
+    }
+    if (zin) {
+      // z_J is given: publish it (the forward barriers complete as in a forward pass) and
+      // take column l of W for the backward pass
+#pragma unroll
+      for (int q = 0; q < 32; q++) w[q] = Wb[q * 32 + lane];
     }
     auto publish = [&](float* buf, unsigned long long* bar) {
       const unsigned dst = smem_u32(buf + J * 32 + lane), b = smem_u32(bar);
@@ -1461,12 +1502,15 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
 #pragma unroll
       for (int q = 0; q < 32; q++) w[q] = Wb[q * 32 + lane];  // column l of W for the backward pass
     };
-    if (J == 0) form_z();
+    if (zin)
+      publish(zbuf, bars + J);
+    else if (J == 0)
+      form_z();
     const int sw = lane >> 2, se = lane & 3;  // forward: chunk and element of row `lane` in a tile column
-    for (int t = 0; t < ntile; t++) {
-      const int slot = t % kTrsvRing;
+    for (int t = t0; t < ntile; t++) {
+      const int slot = (t - t0) % kTrsvRing;
       // always waited (bounded), so that no copy is in flight when the CTA leaves
-      if (!mbar_wait(smem_u32(rbars + slot), (unsigned)((t / kTrsvRing) & 1))) ok = false;
+      if (!mbar_wait(smem_u32(rbars + slot), (unsigned)(((t - t0) / kTrsvRing) & 1))) ok = false;
       const float* tile = ring + slot * 1024;
       float s0 = 0.0f, s1 = 0.0f;
       if (t < J) {
@@ -1552,114 +1596,236 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
 // so the solves run in k_trsv_cluster.
 
 // X L^T = A for the R x nk block A = G[r0 .., k0 ..] (in place), L = the factored
-// super-block G[k0 .., k0 ..] with inverse diagonal blocks Wd: blocked forward
-// substitution, X_J = (A_J - sum_{I<J} X_I L_JI^T) W_JJ^T.  One CTA per 32 rows.
-// Block row J of L is staged k-major (32 consecutive rows per column of L) with
-// cp.async, all chunks in flight at once, so one 128-bit load gives 4 rows.
-__global__ void __launch_bounds__(256) k_trsm_blocks(float* __restrict__ G, long long ld, int k0, int nk, int r0,
-                                                     int R, const float* __restrict__ Wd) {
+// super-block G[k0 .., k0 ..] (nk a multiple of 32) with inverse diagonal blocks Wd:
+// blocked forward substitution, X_J = (A_J - sum_{I<J} X_I L_JI^T) W_JJ^T.  One CTA per
+// RB rows of A, which stay in shared memory (k-major: the RB rows of one column are
+// contiguous).  The block rows of L stream through a ring of kTrsmStages slots filled by
+// 16-byte cp.async, kTrsmChunk columns of one block row per slot, W_JJ in the slot after
+// the chunks of block row J; the copies run kTrsmStages - 1 slots ahead of the arithmetic.
+// The 256 threads form 64 / RB k-groups; thread (tr, tc) of a group holds the 2 x 4
+// register tile of rows 2tr, 2tr+1 and columns 4tc..4tc+3 of the block column and takes
+// every (64 / RB)-th column of each chunk; at the end of block row J the groups' partial
+// sums are added in a fixed order.
+constexpr int kTrsmThreads = 256;
+constexpr int kTrsmRows = 8;    // RB
+constexpr int kTrsmChunk = 128;
+constexpr int kTrsmStages = 8;
+constexpr int kTrsmSlot = kTrsmChunk * 32;  // floats per slot (a W tile takes 32 x 33)
+__host__ __device__ constexpr size_t trsm_smem(int nk, int RB = kTrsmRows) {
+  return ((size_t)nk * RB + (size_t)kTrsmStages * kTrsmSlot + (size_t)(64 / RB) * 32 * (RB + 1) + (size_t)RB * 33) *
+         sizeof(float);
+}
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait_n() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kTrsmThreads) k_trsm_blocks(float* __restrict__ G, long long ld, int k0, int nk,
+                                                              int r0, int R, const float* __restrict__ Wd) {
   pdl_entry();
+  constexpr int KG = 64 / RB;  // k-groups of 4 RB threads
   extern __shared__ __align__(16) float tsm[];
-  const int ldx = nk + 1;  // odd: conflict-free column walks
-  float* Ls = tsm;                 // (nk - 32) x 32: block row J of L, column k at Ls + 32 k
-  float* Ws = Ls + 32 * nk;        // 32 x 33: W_JJ, row-major, row stride 33 (conflict-free rows)
-  float* Xs = Ws + 32 * 33;        // 32 x ldx: the rows of this CTA
-  float* Ys = Xs + 32 * ldx;       // 32 x 33
+  float* Xs = tsm;                                // nk x RB, k-major
+  float* ring = Xs + nk * RB;                     // kTrsmStages slots
+  float* red = ring + kTrsmStages * kTrsmSlot;    // KG x 32 x (RB + 1): partial sums, column-major
+  float* Ys = red + KG * 32 * (RB + 1);           // RB x 33
   const int tid = threadIdx.x;
-  const int rb = r0 + 32 * blockIdx.x, nr = min(32, R - 32 * (int)blockIdx.x);
-  for (int e = tid; e < 32 * nk; e += blockDim.x) {  // 4-byte async copies: all in flight at once
-    const int r = e & 31, k = e >> 5;
-    const unsigned d = (unsigned)__cvta_generic_to_shared(Xs + r * ldx + k);
-    const float* src = G + (r < nr ? (rb + r) : rb) + (long long)(k0 + k) * ld;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(r < nr ? 4 : 0) : "memory");
-  }
-  const int r = tid >> 3, cg = tid & 7;
+  const int rb = RB * blockIdx.x;                 // first row of this CTA within the R rows
   const int Tk = nk / 32;
-  for (int J = 0; J < Tk; J++) {
-    // stage L[k0 + 32J .. +31, k0 .. k0 + 32J) and W_JJ (16-byte chunks, all in flight)
-    for (int e = tid; e < 8 * 32 * J; e += blockDim.x) {
-      const int c4 = e & 7, k = e >> 3;
-      cp_async16(Ls + 32 * k + 4 * c4, G + (k0 + 32 * J + 4 * c4) + (long long)(k0 + k) * ld, 16);
-    }
-    for (int e = tid; e < 1024; e += blockDim.x) Ws[(e >> 5) * 33 + (e & 31)] = Wd[(long long)J * 1024 + e];
-    cp_async_commit();
-    cp_async_wait0();
-    __syncthreads();
-    float y[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) y[e] = Xs[r * ldx + 32 * J + 4 * cg + e];
-#pragma unroll 4
-    for (int k = 0; k < 32 * J; k++) {
-      const float x = Xs[r * ldx + k];
-      const float4 l = reinterpret_cast<const float4*>(Ls + 32 * k)[cg];
-      y[0] = fmaf(-x, l.x, y[0]);
-      y[1] = fmaf(-x, l.y, y[1]);
-      y[2] = fmaf(-x, l.z, y[2]);
-      y[3] = fmaf(-x, l.w, y[3]);
-    }
-#pragma unroll
-    for (int e = 0; e < 4; e++) Ys[r * 33 + 4 * cg + e] = y[e];
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      float a = 0.0f;
-#pragma unroll 8
-      for (int q = 0; q < 32; q++) a = fmaf(Ys[r * 33 + q], Ws[(4 * cg + e) * 33 + q], a);
-      Xs[r * ldx + 32 * J + 4 * cg + e] = a;
-    }
-    __syncthreads();
+  // ---- the CTA's rows of A (rows past R read as zeros)
+  for (int e = tid; e < (RB / 4) * nk; e += kTrsmThreads) {
+    const int q = e % (RB / 4), k = e / (RB / 4);
+    const int row = rb + 4 * q;
+    const int valid = R - row >= 4 ? 4 : (R - row > 0 ? R - row : 0);
+    cp_async16(Xs + k * RB + 4 * q, valid ? G + (r0 + row) + (long long)(k0 + k) * ld : G, 4 * valid);
   }
-  for (int e = tid; e < 32 * nk; e += blockDim.x) {
-    const int rr = e & 31, k = e >> 5;
-    if (rr < nr) G[(rb + rr) + (long long)(k0 + k) * ld] = Xs[rr * ldx + k];
+  // ---- the ring: item (J, c), c < nch(J): columns [kTrsmChunk c, ..) of block row J of L;
+  //      c == nch(J): W_JJ (row stride 33)
+  auto nch = [](int J) { return (32 * J + kTrsmChunk - 1) / kTrsmChunk; };
+  auto issue = [&](int J, int c, int slot) {
+    float* dst = ring + slot * kTrsmSlot;
+    if (c == nch(J)) {
+      for (int e = tid; e < 1024; e += kTrsmThreads) cp_async4(dst + (e >> 5) * 33 + (e & 31), Wd + (long long)J * 1024 + e);
+    } else {
+      const int kb = c * kTrsmChunk, kn = min(kTrsmChunk, 32 * J - kb);
+      for (int e = tid; e < 8 * kn; e += kTrsmThreads) {
+        const int q = e & 7, kk = e >> 3;
+        cp_async16(dst + kk * 32 + 4 * q, G + (k0 + 32 * J + 4 * q) + (long long)(k0 + kb + kk) * ld, 16);
+      }
+    }
+  };
+  int pJ = 0, pc = 0, pslot = 0;  // next item to issue
+  auto advance = [&](int& J, int& c) {
+    if (c < nch(J)) {
+      c++;
+    } else {
+      J++;
+      c = 0;
+    }
+  };
+  for (int s = 0; s < kTrsmStages - 1; s++) {
+    if (pJ < Tk) {
+      issue(pJ, pc, pslot);
+      advance(pJ, pc);
+      pslot = pslot + 1 == kTrsmStages ? 0 : pslot + 1;
+    }
+    cp_async_commit();
+  }
+  const int kg = tid / (4 * RB), t = tid % (4 * RB), tr = t >> 3, tc = t & 7;
+  float acc[2][4] = {};
+  int cslot = 0;
+  for (int J = 0, c = 0; J < Tk; advance(J, c), cslot = cslot + 1 == kTrsmStages ? 0 : cslot + 1) {
+    cp_async_wait_n<kTrsmStages - 2>();  // item (J, c) has landed (this thread's copies)
+    __syncthreads();                     // everyone's copies; everyone is done with the previous slot
+    if (pJ < Tk) {
+      issue(pJ, pc, pslot);
+      advance(pJ, pc);
+      pslot = pslot + 1 == kTrsmStages ? 0 : pslot + 1;
+    }
+    cp_async_commit();
+    const float* sl = ring + cslot * kTrsmSlot;
+    if (c < nch(J)) {
+      const int kb = c * kTrsmChunk, kn = min(kTrsmChunk, 32 * J - kb);
+#pragma unroll 4
+      for (int kk = kg; kk < kn; kk += KG) {
+        const float2 x = *reinterpret_cast<const float2*>(Xs + (kb + kk) * RB + 2 * tr);
+        const float4 l = *reinterpret_cast<const float4*>(sl + kk * 32 + 4 * tc);
+        acc[0][0] = fmaf(x.x, l.x, acc[0][0]);
+        acc[0][1] = fmaf(x.x, l.y, acc[0][1]);
+        acc[0][2] = fmaf(x.x, l.z, acc[0][2]);
+        acc[0][3] = fmaf(x.x, l.w, acc[0][3]);
+        acc[1][0] = fmaf(x.y, l.x, acc[1][0]);
+        acc[1][1] = fmaf(x.y, l.y, acc[1][1]);
+        acc[1][2] = fmaf(x.y, l.z, acc[1][2]);
+        acc[1][3] = fmaf(x.y, l.w, acc[1][3]);
+      }
+      continue;
+    }
+    // ---- end of block row J: Y = A_J - (sum over the k-groups, in order), X_J = Y W_JJ^T
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        red[(kg * 32 + 4 * tc + v) * (RB + 1) + 2 * tr + u] = acc[u][v];
+        acc[u][v] = 0.0f;
+      }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < RB / 8; p++) {
+      const int o = tid + kTrsmThreads * p, r = o % RB, cc = o / RB;
+      float s = 0.0f;
+#pragma unroll
+      for (int g = 0; g < KG; g++) s += red[(g * 32 + cc) * (RB + 1) + r];
+      Ys[r * 33 + cc] = Xs[(32 * J + cc) * RB + r] - s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < RB / 8; p++) {
+      const int o = tid + kTrsmThreads * p, r = o % RB, cc = o / RB;
+      float x = 0.0f;
+#pragma unroll 8
+      for (int q = 0; q < 32; q++) x = fmaf(Ys[r * 33 + q], sl[cc * 33 + q], x);
+      Xs[(32 * J + cc) * RB + r] = x;
+    }
+  }
+  cp_async_wait_n<0>();
+  __syncthreads();
+  for (int e = tid; e < RB * nk; e += kTrsmThreads) {
+    const int r = e % RB, k = e / RB;
+    if (rb + r < R) G[(r0 + rb + r) + (long long)(k0 + k) * ld] = Xs[k * RB + r];
   }
 }
 
 // C -= X X^T on the lower triangle of the R x R block C = G[r0 .., r0 ..], with
-// X = G[r0 .., k0 .. k0 + nk): 64 x 64 output tiles, K staged 32 at a time.
-__global__ void __launch_bounds__(256) k_syrk_sub(float* __restrict__ G, long long ld, int r0, int R, int k0, int nk) {
+// X = G[r0 .., k0 .. k0 + nk): one CTA per 32 x 32 lower tile.  Both row blocks of X
+// are staged whole (k-major: the 32 rows of one column are one 128-byte line; 16-byte
+// cp.async, all in flight at once, rows past R as zeros); four k-groups of 64 threads
+// take every fourth k with a 4 x 4 register tile each, and the groups' partial sums are
+// added in a fixed order.
+constexpr int kSubThreads = 256;
+__host__ __device__ constexpr size_t syrk_sub_smem(int nk) {
+  return ((size_t)2 * 32 * nk + (size_t)3 * 32 * 33) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(kSubThreads) k_syrk_sub(float* __restrict__ G, long long ld, int r0, int R, int k0,
+                                                          int nk) {
   pdl_entry();
-  // k-major staging (64 consecutive rows per k): a thread's four rows are one 16-byte
-  // load and the sixteen column groups of a warp read 256 consecutive bytes
-  __shared__ __align__(16) float As[32 * 64], Bs[32 * 64];
+  extern __shared__ __align__(16) float ssm[];
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
-  const int i0 = 64 * ti, j0 = 64 * tj;
-  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  const int i0 = 32 * ti, j0 = 32 * tj;
+  float* As = ssm;
+  float* Bs = ti == tj ? As : As + 32 * nk;
+  float* red = ssm + 64 * nk;  // 3 x 32 x 33
+  const int tid = threadIdx.x;
+  auto stage = [&](float* dst, int b0) {
+    for (int e = tid; e < 8 * nk; e += kSubThreads) {
+      const int q = e & 7, k = e >> 3, row = b0 + 4 * q;
+      const int valid = R - row >= 4 ? 4 : (R - row > 0 ? R - row : 0);
+      cp_async16(dst + k * 32 + 4 * q, valid ? G + (r0 + row) + (long long)(k0 + k) * ld : G, 4 * valid);
+    }
+  };
+  stage(As, i0);
+  if (ti != tj) stage(Bs, j0);
+  cp_async_commit();
+  cp_async_wait0();
+  __syncthreads();
+  const int kg = tid >> 6, t = tid & 63, tr = t >> 3, tc = t & 7;
   float acc[4][4] = {};
-  for (int kc = 0; kc < nk; kc += 32) {
-    for (int e = tid; e < 64 * 32; e += blockDim.x) {  // 4-byte async copies, zero fill outside
-      const int i = e & 63, k = e >> 6;
-      const bool kin = kc + k < nk, ain = i0 + i < R && kin, bin = j0 + i < R && kin;
-      const float* sa = ain ? G + (r0 + i0 + i) + (long long)(k0 + kc + k) * ld : G;
-      const float* sb = bin ? G + (r0 + j0 + i) + (long long)(k0 + kc + k) * ld : G;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(As + k * 64 + i)), "l"(sa),
-                   "r"(ain ? 4 : 0) : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(Bs + k * 64 + i)), "l"(sb),
-                   "r"(bin ? 4 : 0) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
 #pragma unroll 4
-    for (int k = 0; k < 32; k++) {
-      const float4 a4 = reinterpret_cast<const float4*>(As + k * 64)[tr];
-      const float4 b4 = reinterpret_cast<const float4*>(Bs + k * 64)[tc];
-      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+  for (int k = kg; k < nk; k += 4) {
+    const float4 a4 = reinterpret_cast<const float4*>(As + k * 32)[tr];
+    const float4 b4 = reinterpret_cast<const float4*>(Bs + k * 32)[tc];
+    const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-      for (int u = 0; u < 4; u++)
+    for (int u = 0; u < 4; u++)
 #pragma unroll
-        for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-    }
-    __syncthreads();
+      for (int v = 0; v < 4; v++) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
   }
+  if (kg > 0)
 #pragma unroll
-  for (int u = 0; u < 4; u++)
+    for (int u = 0; u < 4; u++)
 #pragma unroll
-    for (int v = 0; v < 4; v++) {
-      const int gi = i0 + 4 * tr + u, gj = j0 + 4 * tc + v;
-      if (gi < R && gj < R && gi >= gj) G[(r0 + gi) + (long long)(r0 + gj) * ld] -= acc[u][v];
-    }
+      for (int v = 0; v < 4; v++) red[((kg - 1) * 32 + 4 * tr + u) * 33 + 4 * tc + v] = acc[u][v];
+  __syncthreads();
+  if (kg == 0)
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int v = 0; v < 4; v++) {
+        const int gi = i0 + 4 * tr + u, gj = j0 + 4 * tc + v;
+        float s = acc[u][v];
+#pragma unroll
+        for (int g = 0; g < 3; g++) s += red[(g * 32 + 4 * tr + u) * 33 + 4 * tc + v];
+        if (gi < R && gj < R && gi >= gj) G[(r0 + gi) + (long long)(r0 + gj) * ld] -= s;
+      }
+}
+
+// Shared-memory limits of the super-block kernels (k_chol_cluster<8>, k_trsm_blocks,
+// k_syrk_sub), set once per device.
+static void super_block_attrs() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && done[dev]) return;
+  cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)cluster_smem_max());
+  cudaFuncSetAttribute(k_trsm_blocks<kTrsmRows>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)trsm_smem(kClusterN));
+  cudaFuncSetAttribute(k_syrk_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_sub_smem(kClusterN));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
+// X L^T = A on the R x nk block at (r0, k0) (nk a multiple of 32, at most kClusterN).
+static void launch_trsm_blocks(float* G, long long ld, int k0, int nk, int r0, int R, const float* Wd,
+                               cudaStream_t s) {
+  launch_k(k_trsm_blocks<kTrsmRows>, dim3((R + kTrsmRows - 1) / kTrsmRows), dim3(kTrsmThreads), trsm_smem(nk), s, G,
+           ld, k0, nk, r0, R, Wd);
 }
 
 // ---------------------------------------------------------------------------
@@ -1873,20 +2039,12 @@ bool inv_trace(float* S, long long ldS, int N, DevState* st, float* Wdiag, doubl
                cudaStream_t s) {
   const int Np = (N + 31) / 32 * 32;
   if (N <= 0 || Np > kClusterN) return false;
-  static bool done[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !done[dev]) {
-    cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
-    cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)(32 * kClusterN + 32 * 33 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float)));
-    if (dev >= 0 && dev < 64) done[dev] = true;
-  }
+  super_block_attrs();
   count_launch(4);
-  launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag);
+  launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, S, ldS, N, st, Wdiag,
+           (const double*)nullptr, (float*)nullptr);
   launch_k(k_inv_trace_setup, dim3(64), dim3(256), (size_t)(0), s, S, ldS, N, Np);
-  const size_t tsm = (size_t)(32 * Np + 32 * 33 + 32 * (Np + 1) + 32 * 33) * sizeof(float);
-  launch_k(k_trsm_blocks, dim3(Np / 32), dim3(256), (size_t)(tsm), s, S, ldS, 0, Np, Np, Np, Wdiag);
+  launch_trsm_blocks(S, ldS, 0, Np, Np, Np, Wdiag, s);
   launch_k(k_frob2, dim3(Np / 32), dim3(256), (size_t)(0), s, S + Np, ldS, Np, partial, out, st);
   return cudaGetLastError() == cudaSuccess;
 }
@@ -2039,7 +2197,8 @@ static bool chol16_ok() {
   return ok == 1;
 }
 
-bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s) {
+bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cudaStream_t s, const double* hrow,
+                 float* zout, bool* fused) {
   // one tile: one CTA; up to kSmallN also without inverse diagonal blocks.  From two
   // tiles on, the cluster factor and the 4-CTA solves are faster (N = 64: 20 us
   // against 61 us for the single-CTA factor and solves; N = 128: 37 against 131)
@@ -2057,11 +2216,19 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
   // above 16 tile rows the 8-CTA kernel holds one panel buffer (a full cluster barrier per step);
   // the 16-CTA kernel keeps two up to 19 tile rows and covers N <= kCluster16N
   const bool wide = Wdiag && N > 512 && N <= kCluster16N && chol16_ok();
+  // the forward substitution inside the factor (an appended row h^T): one cluster launch,
+  // N not a multiple of 32, inverse diagonal blocks for the backward solve
+  const bool aug = hrow && zout && Wdiag && N % 32 != 0;
+  const double* h = aug ? hrow : nullptr;
+  if (fused) *fused = false;
   if (wide) {
     count_launch();
     launch_k(k_chol_cluster<kCluster16CTAs>, dim3(kCluster16CTAs), dim3(kCholThreads),
-             (size_t)(cluster_smem((N + 31) / 32, kCluster16CTAs)), s, G, ldg, N, st, Wdiag);
-    if (cudaGetLastError() == cudaSuccess) return true;
+             (size_t)(cluster_smem((N + 31) / 32, kCluster16CTAs)), s, G, ldg, N, st, Wdiag, h, zout);
+    if (cudaGetLastError() == cudaSuccess) {
+      if (fused) *fused = aug;
+      return true;
+    }
   }
   if (N <= kClusterN) {
     static bool done[64] = {};
@@ -2072,20 +2239,16 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       if (dev >= 0 && dev < 64) done[dev] = true;
     }
     count_launch();
-    launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag);
-    if (cudaGetLastError() == cudaSuccess) return Wdiag != nullptr;
+    launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((N + 31) / 32)), s, G, ldg, N, st, Wdiag,
+             h, zout);
+    if (cudaGetLastError() == cudaSuccess) {
+      if (fused) *fused = aug;
+      return Wdiag != nullptr;
+    }
   }
   if (Wdiag && N <= kMaxM) {
     // super-blocks of equal size (a multiple of 32, at most kClusterN)
-    static bool done_sb[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const size_t trsm_smem_max = (size_t)(32 * kClusterN + 32 * 33 + 32 * (kClusterN + 1) + 32 * 33) * sizeof(float);
-    if (dev < 0 || dev >= 64 || !done_sb[dev]) {
-      cudaFuncSetAttribute(k_chol_cluster<kClusterCTAs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cluster_smem_max());
-      cudaFuncSetAttribute(k_trsm_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem_max);
-      if (dev >= 0 && dev < 64) done_sb[dev] = true;
-    }
+    super_block_attrs();
     const int nb = (N + kClusterN - 1) / kClusterN;
     const int B = ((N + nb - 1) / nb + 31) / 32 * 32;
     bool launched = true;
@@ -2094,14 +2257,13 @@ bool chol_factor(float* G, long long ldg, int N, DevState* st, float* Wdiag, cud
       float* Gkk = G + k0 + (long long)k0 * ldg;
       count_launch();
       launch_k(k_chol_cluster<kClusterCTAs>, dim3(kClusterCTAs), dim3(kCholThreads), (size_t)(cluster_smem((nk + 31) / 32)), s, Gkk, ldg, nk, st,
-                                                                             Wdiag + (long long)(k0 / 32) * 1024);
+               Wdiag + (long long)(k0 / 32) * 1024, (const double*)nullptr, (float*)nullptr);
       const int r0 = k0 + nk, R = N - r0;
       if (R > 0) {
         count_launch(2);
-        const size_t tsm = (size_t)(32 * nk + 32 * 33 + 32 * (nk + 1) + 32 * 33) * sizeof(float);
-        launch_k(k_trsm_blocks, dim3((R + 31) / 32), dim3(256), (size_t)(tsm), s, G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024);
-        const int nt = (R + 63) / 64;
-        launch_k(k_syrk_sub, dim3(nt * (nt + 1) / 2), dim3(256), (size_t)(0), s, G, ldg, r0, R, k0, nk);
+        launch_trsm_blocks(G, ldg, k0, nk, r0, R, Wdiag + (long long)(k0 / 32) * 1024, s);
+        const int nt = (R + 31) / 32;
+        launch_k(k_syrk_sub, dim3(nt * (nt + 1) / 2), dim3(kSubThreads), syrk_sub_smem(nk), s, G, ldg, r0, R, k0, nk);
       }
       launched = cudaGetLastError() == cudaSuccess;
     }
@@ -2152,7 +2314,7 @@ void launch_chol_solve_small(float* G, long long ldg, int N, DevState* st, const
 // (acc += c with the contraction test, see k_trsv_pair).
 static bool launch_trsv_pair(const float* L, long long ldl, int N, const double* rhs, double* acc, int first,
                              double alpha, const float* Wdiag, DevState* st, double* rpart, double tau2,
-                             cudaStream_t s) {
+                             cudaStream_t s, const float* zin = nullptr) {
   CUtensorMap tmL;
   if (N <= kSmallNewton || N > 32 * kTrsvPairMaxT || !make_factor_tensor_map(&tmL, L, ldl, N)) return false;
   const int T = (N + 31) / 32, T0 = (T + kTrsvQ - 1) / kTrsvQ;
@@ -2170,8 +2332,14 @@ static bool launch_trsv_pair(const float* L, long long ldl, int N, const double*
   }
   count_launch();
   launch_k(k_trsv_pair, dim3(kTrsvQ), dim3(32 * T0), smem, s, tmL, N, rhs, acc, first, alpha, Wdiag, st, rpart,
-           tau2);
+           tau2, zin);
   return cudaGetLastError() == cudaSuccess;
+}
+
+bool launch_trsv_back(const float* L, long long ldl, int N, const float* z, double* acc, int first, double alpha,
+                      const float* Wdiag, DevState* st, cudaStream_t s) {
+  if (N <= 0 || !Wdiag || !z) return false;
+  return launch_trsv_pair(L, ldl, N, nullptr, acc, first, alpha, Wdiag, st, nullptr, 0.0, s, z);
 }
 
 void launch_trsv_refine(const float* L, long long ldl, int N, const double* rhs, double* acc, double* corr,

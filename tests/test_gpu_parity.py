@@ -184,7 +184,8 @@ def test_grad_gather(m, n, r):
 @pytest.mark.parametrize("syrk_tc", [1, 0])
 @pytest.mark.parametrize("m,r", [(30, 0), (30, 1), (30, 29), (30, 30), (30, 31), (5, 7), (40, 32), (32, 40), (100, 250), (257, 65),
                                  (500, 120), (128, 129), (129, 300), (300, 200), (200, 400), (700, 600),
-                                 (720, 680), (900, 800), (760, 800), (1000, 999)])
+                                 (720, 680), (900, 800), (760, 800), (1000, 999),
+                                 (1500, 1400)])
 def test_newton_direction(m, r, syrk_tc):
     # syrk_tc = 1: Newton matrix on the tensor cores (three-way BF16 split, FP32 accumulation);
     # 0: FP32 FMA.  Both feed an FP32 factor refined through the FP64 panel.
