@@ -608,21 +608,30 @@ __device__ PassNorms bprox(const double* x, double* u, const double* t, double* 
   long long pos = 0;
   for (long long base = 0; base < n; base += BT) {
     const long long j = base + tid;
-    bool act = false;
-    double wv = 0.0;
+    bool act = false, rare = false;
+    double wv = 0.0, xj = 0.0, uj = 0.0, v = 0.0;
     if (j < n) {
-      const double xj = x[j];
+      xj = x[j];
       if (support) {
         act = !is_zero_bits(xj);
         wv = xj;
       } else {
-        double uj = u[j];
+        uj = u[j];
         if (apply) {
           uj = fma(s, t[j], uj);
           u[j] = uj;
         }
-        const double v = v_of(xj, uj, pp.sigma);
+        v = v_of(xj, uj, pp.sigma);
         act = abs_gt(v, pp.thr);
+        rare = act || !is_zero_bits(xj) || abs_gt(uj, pp.lam1);
+      }
+    }
+    // the rare terms (active entries, nonzero x, |u| > lam1) behind a warp-uniform
+    // branch: as predicated instructions they would occupy the FP64 pipe for every entry
+    if (!support) {
+      if (!__any_sync(0xffffffffu, rare)) {
+        if (j < n) q[3] += v * v;
+      } else if (j < n) {
         if (act) {
           const double mag = __dsub_rn(fabs(v), pp.thr) * pp.inv_onep;
           const double wn = v < 0.0 ? -mag : mag;
@@ -877,7 +886,15 @@ __device__ void solve_one(const BatchInst& P, BatchOut& O, const BatchOpts& o, c
     pobj = 0.5 * gdots[2] + pp.lam1 * pn.w1 + 0.5 * pp.lam2 * pn.w2;
     const double dual = -(0.5 * gdots[1] + gdots[3]) - (pp.lam2 > 0 ? pn.pen / (2.0 * pp.lam2) : 0.0);
     gap = pp.lam2 > 0 ? pobj - dual : NAN;
-    for (long long j = tid; j < n; j += BT) x[j] = prox_value(v_of(x[j], u[j], pp.sigma), pp);
+    for (long long base = 0; base < n; base += BT) {  // the division behind a warp-uniform branch
+      const long long j = base + tid;
+      const bool in = j < n;
+      const double v = in ? v_of(x[j], u[j], pp.sigma) : 0.0;
+      const bool act = in && abs_gt(v, pp.thr);
+      double w = 0.0;
+      if (__any_sync(0xffffffffu, act) && act) w = prox_value(v, pp);  // zero exactly when inactive
+      if (in) x[j] = w;
+    }
     __syncthreads();
     if (kkt1 <= o.tol && kkt3 <= o.tol) {
       converged = 1;

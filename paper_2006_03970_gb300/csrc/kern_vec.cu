@@ -95,14 +95,20 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
   }
   unsigned cnt = 0;
   double w2 = 0, w1 = 0, xw2 = 0, vw2 = 0, pen = 0;
-  for (long long j = start + threadIdx.x; j < stop; j += blockDim.x) {
-    const double xj = x[j];
+  // every lane of a warp runs the same iterations (entries past `stop` masked), so that
+  // the rare terms sit behind warp-uniform branches: as predicated instructions they
+  // would occupy the FP64 pipe, the slow one here, for every entry
+  const int lane = threadIdx.x & 31;
+  for (long long base = start + (threadIdx.x & ~31); base < stop; base += blockDim.x) {
+    const long long j = base + lane;
+    const bool in = j < stop;
+    const double xj = in ? x[j] : 0.0;
     if (MODE == kProxSupport) {
       if (!is_zero_bits(xj)) cnt++;
       continue;
     }
-    double uj = u[j];
-    if (apply_update) {
+    double uj = in ? u[j] : 0.0;
+    if (apply_update && in) {
       uj = fma(s, t[j], uj);
       u[j] = uj;
     }
@@ -110,21 +116,26 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_count(const double* __rest
     // the count uses the active test itself (eq. Q_def); w only feeds the norms,
     // so the reciprocal of 1 + sigma*lam2 replaces the division here.  Terms that
     // are exactly zero (w = 0, x = 0, |u| <= lam1) are skipped: FP64 is slow here
-    if (is_active(v, pp)) {
-      cnt++;
-      const double mag = __dsub_rn(fabs(v), pp.thr) * pp.inv_onep;  // > 0
-      const double w = v < 0.0 ? -mag : mag;
-      w2 += w * w;
-      w1 += mag;
-      xw2 += (xj - w) * (xj - w);
-      vw2 += (v - w) * (v - w);
-    } else {  // w = 0
+    const bool act = in && is_active(v, pp), xnz = !is_zero_bits(xj), pu = in && abs_gt(uj, pp.lam1);
+    if (__any_sync(0xffffffffu, act || xnz || pu)) {
+      if (act) {
+        cnt++;
+        const double mag = __dsub_rn(fabs(v), pp.thr) * pp.inv_onep;  // > 0
+        const double w = v < 0.0 ? -mag : mag;
+        w2 += w * w;
+        w1 += mag;
+        xw2 += (xj - w) * (xj - w);
+        vw2 += (v - w) * (v - w);
+      } else if (in) {  // w = 0
+        vw2 += v * v;
+        if (xnz) xw2 += xj * xj;
+      }
+      if (pu) {
+        const double e = fabs(uj) - pp.lam1;
+        pen += e * e;
+      }
+    } else if (in) {  // w = 0, x = 0, |u| <= lam1
       vw2 += v * v;
-      if (!is_zero_bits(xj)) xw2 += xj * xj;
-    }
-    if (abs_gt(uj, pp.lam1)) {
-      const double e = fabs(uj) - pp.lam1;
-      pen += e * e;
     }
   }
   const unsigned wc = __reduce_add_sync(0xffffffffu, cnt);
@@ -177,20 +188,23 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
   block_range(n, start, stop);
   // the entries of the first tile are loaded and classified before the counts of
   // the blocks ahead are read, so that the two latencies overlap
+  // called by every thread of the block alike: the prox value (a division) is formed
+  // behind a warp-uniform branch, so inactive warps issue no FP64 division
   auto classify = [&](long long j, double& w, bool& act) {
     w = 0.0;
     act = false;
+    double v = 0.0;
     if (j < stop) {
       const double xj = x[j];
       if (MODE == kProxSupport) {
         w = xj;
         act = !is_zero_bits(xj);
       } else {
-        const double v = v_of(xj, u[j], pp.sigma);
+        v = v_of(xj, u[j], pp.sigma);
         act = is_active(v, pp);
-        if (act) w = prox_value(v, pp);  // zero exactly when inactive
       }
     }
+    if (MODE != kProxSupport && __any_sync(0xffffffffu, act) && act) w = prox_value(v, pp);  // zero exactly when inactive
   };
   double w0;
   bool act0;
@@ -239,10 +253,21 @@ __global__ void __launch_bounds__(kVecThreads) k_prox_scatter(const double* __re
 
 // x <- prox_{sigma p}(x - sigma u): the multiplier update of eq. update_x
 // written through the Moreau decomposition.
+// The lanes of a warp run the same iterations, and the prox value (a division) is formed
+// behind a warp-uniform branch: warps without an active entry issue no FP64 division.
 __global__ void k_set_x(double* __restrict__ x, const double* __restrict__ u, long long n, ProxParams pp) {
   pdl_entry();
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
-    x[j] = prox_value(v_of(x[j], u[j], pp.sigma), pp);
+  const int lane = threadIdx.x & 31;
+  for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long j = base + lane;
+    const bool in = j < n;
+    const double v = in ? v_of(x[j], u[j], pp.sigma) : 0.0;
+    const bool act = in && is_active(v, pp);
+    double w = 0.0;
+    if (__any_sync(0xffffffffu, act) && act) w = prox_value(v, pp);  // zero exactly when inactive
+    if (in) x[j] = w;
+  }
 }
 
 // Element loaders for the gather: value of A(i, col) as double.
