@@ -759,14 +759,16 @@ __device__ __forceinline__ void push_tile(unsigned src, unsigned dst, unsigned b
 
 // W = L^{-1} for the factored 32 x 32 diagonal tile D (lower, row stride 33) by one warp:
 // lane j forms column j by forward substitution; W is stored row-major at Wout.
+// (Four partial sums per entry keep the dependent chain of each step short.)
 __device__ __forceinline__ void inverse_diag_warp(const float* D, float* __restrict__ Wout, int lane) {
   float w[32];
+  const float rd = __frcp_rn(D[lane * 33 + lane]);  // 1 / L_ll, formed off the chain
 #pragma unroll
   for (int i = 0; i < 32; i++) {
-    float s = (i == lane) ? 1.0f : 0.0f;
+    float s[4] = {(i == lane) ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int q = 0; q < i; q++) s = fmaf(-D[i * 33 + q], w[q], s);
-    w[i] = s * __frcp_rn(D[i * 33 + i]);
+    for (int q = 0; q < i; q++) s[q & 3] = fmaf(-D[i * 33 + q], w[q], s[q & 3]);
+    w[i] = ((s[0] + s[1]) + (s[2] + s[3])) * __shfl_sync(0xffffffffu, rd, i);
   }
 #pragma unroll
   for (int i = 0; i < 32; i++) Wout[i * 32 + lane] = w[i];
@@ -816,24 +818,49 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
   // (k+1, k+1) for the first tile, else the owner of (i, k+1), which solves it next
   auto first_of = [&](int i, int k) { return i == k + 1 ? owner(k + 1, k + 1) : owner(i, k + 1); };
 
-  // ---- load the owned tiles with 4-byte async copies (all in flight at once;
-  //      consecutive threads read consecutive rows of a column), zero outside
-  //      N x N; then the identity on the padded diagonal.  The strict upper
-  //      triangle of a diagonal tile is copied too and never read.
-  for (int sl = 0; sl < nslots; sl++) {
-    const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
-    float* dst = own + sl * kTileF;
-    for (int e = tid; e < 1024; e += blockDim.x) {
-      const int r = e & 31, c = e >> 5;
-      const int gi = ti * 32 + r, gj = tj * 32 + c;
-      const bool in = gi < N && gj < N;
-      const unsigned d = smem_u32(dst + r * 33 + c);
-      const float* src = in ? G + gi + (long long)gj * ld : G;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(in ? 4 : 0) : "memory");
+  // ---- load the owned tiles, zero outside N x N; then the identity on the padded
+  //      diagonal.  Item e is rows 4q .. 4q+3 of column c of slot e / 256 (q = e mod 8,
+  //      c = (e / 8) mod 32): one 16-byte load where G and ld allow it, eight loads in
+  //      flight per thread before their shared-memory stores (bank 4q + c + row within
+  //      the four: conflict-free).  The strict upper triangle of a diagonal tile is
+  //      loaded too and never read.
+  {
+    const bool v4 = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+    const int items = nslots * 256;
+    for (int b0 = 0; b0 < items; b0 += 8 * (int)blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int e = b0 + k * (int)blockDim.x + tid;
+        v[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (e >= items) continue;
+        const int sl = e >> 8, q = e & 7, c = (e >> 3) & 31;
+        const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+        const int gi = ti * 32 + 4 * q, gj = tj * 32 + c;
+        if (gj >= N) continue;
+        const float* src = G + gi + (long long)gj * ld;
+        if (v4 && gi + 3 < N) {
+          v[k] = *reinterpret_cast<const float4*>(src);
+        } else {
+          if (gi < N) v[k].x = src[0];
+          if (gi + 1 < N) v[k].y = src[1];
+          if (gi + 2 < N) v[k].z = src[2];
+          if (gi + 3 < N) v[k].w = src[3];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int e = b0 + k * (int)blockDim.x + tid;
+        if (e >= items) continue;
+        const int sl = e >> 8, q = e & 7, c = (e >> 3) & 31;
+        float* dst = own + sl * kTileF + (4 * q) * 33 + c;
+        dst[0] = v[k].x;
+        dst[33] = v[k].y;
+        dst[66] = v[k].z;
+        dst[99] = v[k].w;
+      }
     }
   }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   const bool aug = hrow != nullptr;  // the host passes h only when N % 32 != 0
   const int rN = N - 32 * (T - 1);   // row N within the last tile row (with aug)
@@ -849,17 +876,20 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
     for (int i = j + 1; i < T; i++) m |= 1u << (tri_index(i, j) % C);
     return m;
   };
-  if (tid == 0) {
-    for (int b = 0; b < nbuf; b++)
-      for (int i = 0; i < T; i++) mbar_init(smem_u32(&tbar_s[b * kClusterTMax + i]), 1);
+  // one barrier per thread.  Armed for the first diagonal push and the first panel(s)
+  // (tile i of panel b, i > b): panel k + nbuf is armed at the end of step k, once every
+  // tile of panel k has arrived
+  if (tid < nbuf * T) {
+    const int b = tid / T, i = tid % T;
+    const unsigned bar = smem_u32(&tbar_s[b * kClusterTMax + i]);
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (i > b) mbar_expect_tx(bar, kPanelBytes);
+  }
+  if (tid == kCholThreads - 1) {
     mbar_init(dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    // arm for the first diagonal push and the first panel(s): panel k + nbuf is
-    // armed at the end of step k, once every tile of panel k has arrived
     if (receivers_of(0) >> rank & 1u) mbar_expect_tx(dbar, kTileBytes);
-    for (int i = 1; i < T; i++) mbar_expect_tx(tbar(0, i), kPanelBytes);
-    if (nbuf == 2)
-      for (int i = 2; i < T; i++) mbar_expect_tx(tbar(1, i), kPanelBytes);
   }
   __syncthreads();
   cluster.sync();
@@ -1036,15 +1066,37 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCholThreads)
       inverse_diag_warp(own + sl * kTileF, Wdiag + (long long)k * 1024, lane);
     }
   }
-  // ---- write the factor back (lower part, inside N); consecutive threads take
-  //      consecutive rows of a column.  Off-diagonal tiles are stored transposed.
-  for (int sl = 0; sl < nslots; sl++) {
-    const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
-    const float* src = own + sl * kTileF;
-    for (int e = tid; e < 1024; e += blockDim.x) {
-      const int r = e & 31, c = e >> 5;
-      const int gi = ti * 32 + r, gj = tj * 32 + c;
-      if (gi < N && gj < N && gi >= gj) G[gi + (long long)gj * ld] = (ti == tj) ? src[r * 33 + c] : src[c * 32 + r];
+  // ---- write the factor back (lower part, inside N).  Off-diagonal tiles are stored
+  //      transposed (column c of the tile is contiguous): rows 4q .. 4q+3 of a column
+  //      go out as one 16-byte store where G and ld allow it; diagonal tiles (row stride
+  //      33) entry by entry, consecutive threads on consecutive rows of a column.
+  {
+    const bool v4 = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(G) & 15) == 0;
+    for (int e = tid; e < nslots * 256; e += blockDim.x) {
+      const int sl = e >> 8, q = e & 7, c = (e >> 3) & 31;
+      const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+      const int gi = ti * 32 + 4 * q, gj = tj * 32 + c;
+      if (ti == tj || gj >= N || gi >= N) continue;
+      const float4 val = *reinterpret_cast<const float4*>(own + sl * kTileF + c * 32 + 4 * q);
+      float* dst = G + gi + (long long)gj * ld;
+      if (v4 && gi + 3 < N) {
+        *reinterpret_cast<float4*>(dst) = val;
+      } else {
+        dst[0] = val.x;
+        if (gi + 1 < N) dst[1] = val.y;
+        if (gi + 2 < N) dst[2] = val.z;
+        if (gi + 3 < N) dst[3] = val.w;
+      }
+    }
+    for (int sl = 0; sl < nslots; sl++) {
+      const int ti = slot_ij[sl] >> 8, tj = slot_ij[sl] & 255;
+      if (ti != tj) continue;
+      const float* src = own + sl * kTileF;
+      for (int e = tid; e < 1024; e += blockDim.x) {
+        const int r = e & 31, c = e >> 5;
+        const int gi = ti * 32 + r, gj = tj * 32 + c;
+        if (gi < N && gj < N && gi >= gj) G[gi + (long long)gj * ld] = src[r * 33 + c];
+      }
     }
   }
 }
