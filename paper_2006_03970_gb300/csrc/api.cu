@@ -350,10 +350,13 @@ struct PhaseTimer {
 
 // The state after the work queued so far.  A kernel behind that work writes the
 // state into the host mirror and then a sequence number, which this thread
-// polls: no copy-engine transfer and no blocking wake-up on the common path.
-// The poll checks the stream for errors now and then and, after about 50 us,
-// falls back to a blocking synchronisation.  Recorded profiling events are
-// waited for before they are read.
+// polls: no copy-engine transfer and no blocking wake-up on the common path (the
+// work between two reads is a few microseconds to a few milliseconds: one Newton
+// step's prox / gather / gradient kernels, or a Newton step and a pass over A).
+// The poll checks the stream for errors now and then and, after kPollMax, falls
+// back to a blocking synchronisation.  Recorded profiling events are waited for
+// before they are read.
+constexpr std::chrono::microseconds kPollMax(20000);
 ssnal_en_status read_state(ssnal_en_ctx* c) {
   if (!c->st_flag) {
     CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
@@ -375,7 +378,7 @@ ssnal_en_status read_state(ssnal_en_ctx* c) {
         break;
       }
       if (e != cudaErrorNotReady) return SSNAL_EN_ECUDA;
-      if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(50)) {
+      if (std::chrono::steady_clock::now() - t0 > kPollMax) {
         CK(cudaStreamSynchronize(c->stream));
         if (__atomic_load_n(c->st_flag, __ATOMIC_ACQUIRE) != want) return SSNAL_EN_ECUDA;
         break;
