@@ -621,17 +621,39 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
   const long long total = ngrp * nw;
   unsigned char* wring = ring + (size_t)warp * cfg.stages * kLBoxBytes;
   unsigned long long* wbars = bars + warp * cfg.stages;
-  auto issue = [&](long long item) {
+  // item i = q nw + k of this warp: chunk warp + 8 k of group blockIdx.x + q gridDim.x, ring
+  // slot i mod stages.  Lane 0 issues the items in order.  The float-float passes
+  // (bound by the FP32 pipe) keep the issue position and the consumer's slot and phase
+  // by increments, no 64-bit division per box: 433 against 480 us per u = A^T y pass at
+  // m = 1000, n = 1e6 (BF16).  The FP32-accumulation passes (memory-bound, a few
+  // instructions per box) derive them from the item index: measured 322 against 332 us
+  // per t = A^T d pass on the same matrix with the increments (the cause is not
+  // established; both forms give the same slots).
+  auto issue_item = [&](long long item) {
     const long long q = item / nw;
     const int ch = warp + kLWarps * (int)(item % nw);
-    const int sidx = (int)(item % cfg.stages);
-    const unsigned bar = smem_u32(wbars + sidx);
+    const int sx = (int)(item % cfg.stages);
+    const unsigned bar = smem_u32(wbars + sx);
     mbar_expect_tx(bar, kLBoxBytes);
-    tma_load_2d(smem_u32(wring + (size_t)sidx * kLBoxBytes), &tmap, ch * elt_box_inner(ELT),
+    tma_load_2d(smem_u32(wring + (size_t)sx * kLBoxBytes), &tmap, ch * elt_box_inner(ELT),
                 (int)(((long long)blockIdx.x + q * gridDim.x) * kLCols), bar);
   };
+  long long iq = 0;
+  int ik = 0, islot = 0;
+  auto issue_next = [&]() {
+    const int ch = warp + kLWarps * ik;
+    const unsigned bar = smem_u32(wbars + islot);
+    mbar_expect_tx(bar, kLBoxBytes);
+    tma_load_2d(smem_u32(wring + (size_t)islot * kLBoxBytes), &tmap, ch * elt_box_inner(ELT),
+                (int)(((long long)blockIdx.x + iq * gridDim.x) * kLCols), bar);
+    if (++ik == nw) {
+      ik = 0;
+      iq++;
+    }
+    if (++islot == cfg.stages) islot = 0;
+  };
   if (lane == 0)
-    for (long long it = 0; it < total && it < cfg.stages; it++) issue(it);
+    for (long long it = 0; it < total && it < cfg.stages; it++) issue_next();
   __syncwarp();
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // the vector, scaled by a power of two and split: row pair k goes to slot pair_slot<P>(k),
@@ -677,6 +699,8 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
   double cand = 0.0, amax = 0.0;
   bool timed_out = false;
   long long it = 0;
+  int sidx = 0;         // ring slot of item it
+  unsigned rphase = 0;  // phase parity of that slot's barrier for item it
   for (long long q = 0; q < ngrp; q++) {
     // float-float: four accumulator pairs per column (row pair index mod 4) for four
     // independent dependency chains; FP32: one FMA chain per column
@@ -684,8 +708,11 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
     unsigned long long FS[4] = {0ull, 0ull, 0ull, 0ull}, FL[4] = {0ull, 0ull, 0ull, 0ull};
     unsigned long long FSb[4] = {0ull, 0ull, 0ull, 0ull}, FLb[4] = {0ull, 0ull, 0ull, 0ull};
     for (int k = 0; k < nw && !timed_out; k++, it++) {
-      const int sidx = (int)(it % cfg.stages);
-      if (!mbar_wait(smem_u32(wbars + sidx), (unsigned)((it / cfg.stages) & 1))) {
+      if constexpr (!elt_ff(ELT)) {
+        sidx = (int)(it % cfg.stages);
+        rphase = (unsigned)((it / cfg.stages) & 1);
+      }
+      if (!mbar_wait(smem_u32(wbars + sidx), rphase)) {
         timed_out = true;
         break;
       }
@@ -790,7 +817,14 @@ __global__ void __launch_bounds__(kLThreads, 1) k_stream_lane(const __grid_const
       __syncwarp();
       if (lane == 0 && it + cfg.stages < total) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(it + cfg.stages);
+        if constexpr (elt_ff(ELT))
+          issue_next();  // item it + stages
+        else
+          issue_item(it + cfg.stages);
+      }
+      if (++sidx == cfg.stages) {  // ring slot and phase of item it + 1
+        sidx = 0;
+        rphase ^= 1u;
       }
     }
     {
