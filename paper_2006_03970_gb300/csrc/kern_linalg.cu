@@ -1419,12 +1419,12 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
       }
       r = c0 + c1;
     }
-    if (live) acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
-    {
+    {  // the next link of the chain first; the FP64 accumulation (a global load) after it
       const unsigned dst = smem_u32(cbuf + J * 32 + lane), bar = smem_u32(bars + T + J);
 #pragma unroll 1
       for (int c = 0; c < kTrsvCL; c++) st_async_f32(cluster_addr(dst, c), r, cluster_addr(bar, c));
     }
+    if (live) acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
   }
   // every value sent to this CTA has landed before it exits
   for (int k = tid; k < 2 * T; k += blockDim.x)
@@ -1451,6 +1451,7 @@ __global__ void __cluster_dims__(kTrsvCL, 1, 1) __launch_bounds__(512)
 // (DevState::timeout).  With zin the forward pass is already done (z = L^{-1} h from the
 // factor): each warp starts from z_J and streams only the backward tiles.
 constexpr int kTrsvPairMaxT = 32;  // 32 tile rows: N <= 1024 (the m x m systems of m = 1000 included)
+static_assert(kTrsvPairMaxT <= 32, "the contraction test reduces one row block per lane");
 constexpr int kTrsvQ = 4;     // CTAs per cluster
 constexpr int kTrsvRing = 6;  // tiles in flight per warp
 constexpr int kTrsvMaxT0 = (kTrsvPairMaxT + kTrsvQ - 1) / kTrsvQ;
@@ -1599,6 +1600,8 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
       if (t + kTrsvRing < ntile) issue(t + kTrsvRing);
     }
     r = wr_product();  // c_J = W_JJ^T r_J: lane l takes column l of W
+    // the next link of the chain first; the FP64 accumulation (a global load) after it
+    publish(cbuf, bars + T + J);
     if (rpart) {
       // refinement step: acc += c, and this row block's ||c||^2, ||acc + c||^2 (fixed order)
       double ci = 0.0, ai = 0.0;
@@ -1615,7 +1618,6 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
     } else if (live) {
       acc[row] = first ? alpha * (double)r : acc[row] + alpha * (double)r;
     }
-    publish(cbuf, bars + T + J);
   }
   // every value sent to this CTA has landed before it exits (the ring copies of a
   // warp were all waited for: each issued tile is consumed)
@@ -1623,15 +1625,15 @@ __global__ void __cluster_dims__(kTrsvQ, 1, 1) __launch_bounds__(32 * kTrsvMaxT0
     if (ok && !mbar_wait(smem_u32(bars + k), 0u)) ok = false;
   if (!ok) st->timeout = 1;
   if (rpart && last_block(&st->counters[kCtrRefine])) {
-    // the contraction test of the refinement: the row blocks' partial norms in order
-    if (tid == 0) {
-      double c2 = 0.0, a2 = 0.0;
-      for (int j = 0; j < T; j++) {
-        c2 += ld_cg(rpart + 2 * j);
-        a2 += ld_cg(rpart + 2 * j + 1);
+    // the contraction test of the refinement: the row blocks' partial norms, one per
+    // lane of warp 0 (T <= 32: all loads in flight at once), summed in a fixed order
+    if (tid < 32) {
+      const double c2 = warp_sum(tid < T ? ld_cg(rpart + 2 * tid) : 0.0);
+      const double a2 = warp_sum(tid < T ? ld_cg(rpart + 2 * tid + 1) : 0.0);
+      if (tid == 0) {
+        st->refine_ratio = a2 > 0.0 ? sqrt(c2 / a2) : (c2 > 0.0 ? INFINITY : 0.0);
+        if (!(c2 <= tau2 * a2)) st->newton_bad = 1;
       }
-      st->refine_ratio = a2 > 0.0 ? sqrt(c2 / a2) : (c2 > 0.0 ? INFINITY : 0.0);
-      if (!(c2 <= tau2 * a2)) st->newton_bad = 1;
     }
     reset_counter(&st->counters[kCtrRefine]);
   }
