@@ -1860,6 +1860,9 @@ __global__ void __launch_bounds__(kSubThreads) k_syrk_sub(float* __restrict__ G,
       }
 }
 
+static_assert(trsm_smem(kClusterN) <= kClusterSmemLimit, "k_trsm_blocks: shared memory at the largest super-block");
+static_assert(syrk_sub_smem(kClusterN) <= kClusterSmemLimit, "k_syrk_sub: shared memory at the largest super-block");
+
 // Shared-memory limits of the super-block kernels (k_chol_cluster<8>, k_trsm_blocks,
 // k_syrk_sub), set once per device.
 static void super_block_attrs() {
